@@ -1,0 +1,347 @@
+"""Pins of the FP64 CPU oracle against what the paper and the mathematics fix.
+
+Each test targets a mistake the oracle could plausibly contain (a dropped term, a wrong
+index, a transposed operand, an off-by-one rank) and checks it against something other
+than the oracle itself: brute force, closed forms, an independent library routine, or a
+theorem of the paper.
+"""
+import numpy as np
+import pytest
+
+from paper_1805_08998_gb300 import inputs
+
+
+def _kernel(kind, X, Y):
+    if kind == 0:
+        r = np.sqrt(((X[:, None, :] - Y[None, :, :]) ** 2).sum(-1))
+        return np.exp(-r)
+    if kind == 1:
+        r2 = ((X[:, None, :] - Y[None, :, :]) ** 2).sum(-1)
+        return 1.0 / (1.0 + r2)
+    ip = X @ Y.T
+    return (1.0 + ip) ** 2
+
+
+def _bbox(P):
+    return P.min(0), P.max(0)
+
+
+# ---------------------------------------------------------------- trees (Def. 2.2, 2.3, Alg. 1)
+
+@pytest.mark.parametrize("kind,dim,n,leaf", [(0, 2, 300, 8), (1, 3, 517, 16), (0, 3, 64, 64), (0, 1, 1, 4)])
+def test_cluster_tree_definition(oracle, kind, dim, n, leaf):
+    """Def. 2.2: root = I, children partition the parent, all non-empty; leaves <= n_min;
+    depth = ceil(log2(n / leaf)); each split puts the smaller coordinates on the first child."""
+    P = inputs.points(kind, dim, n, 5)
+    T = oracle.Tree(P, leaf, 1.0)
+    assert sorted(T.perm.tolist()) == list(range(n))
+    cl = T.cl
+    assert cl[0, 1] == 0 and cl[0, 2] == n
+    D = 0
+    while -(-n // 2 ** D) > leaf:
+        D += 1
+    assert T.depth == D
+    Pp = P[T.perm]
+    for c in range(T.ncl):
+        lvl, b, s, c0, c1 = (int(x) for x in cl[c])
+        assert s >= 1
+        if c0 < 0:
+            assert lvl == D and s <= leaf
+            continue
+        assert cl[c0, 1] == b and cl[c0, 2] == s // 2
+        assert cl[c1, 1] == b + s // 2 and cl[c0, 2] + cl[c1, 2] == s
+        lo, hi = _bbox(Pp[b:b + s])
+        ax = int(np.argmax(hi - lo))
+        left, right = Pp[b:b + s // 2, ax], Pp[b + s // 2:b + s, ax]
+        if len(left) and len(right):
+            assert left.max() <= right.min()
+
+
+def _adm(Pt, Ps, eta):
+    lt, ht = _bbox(Pt)
+    ls, hs = _bbox(Ps)
+    dt, ds = np.linalg.norm(ht - lt), np.linalg.norm(hs - ls)
+    gap = np.maximum(0, np.maximum(ls - ht, lt - hs))
+    dist = np.linalg.norm(gap)
+    return dist > 0 and max(dt, ds) <= eta * dist
+
+
+@pytest.mark.parametrize("kind,dim,n,leaf,eta", [(0, 2, 400, 8, 1.0), (1, 3, 700, 16, 1.0), (0, 3, 333, 10, 2.0)])
+def test_block_tree_partition_and_admissibility(oracle, kind, dim, n, leaf, eta):
+    """Alg. 1: leaves partition I x I; far leaves admissible, near leaves and inner blocks
+    not; inner blocks have exactly the 4 children tau' x sigma'; the tree is level-conserving."""
+    P = inputs.points(kind, dim, n, 11)
+    T = oracle.Tree(P, leaf, eta)
+    Pp = P[T.perm]
+    cover = np.zeros((n, n), np.int32)
+    for b in range(T.nbl):
+        tau, sig, k, lvl, leafid, nch = (int(x) for x in T.bl[b])
+        tb, ts = T.cl[tau, 1:3]
+        sb, ss = T.cl[sig, 1:3]
+        assert T.cl[tau, 0] == lvl == T.cl[sig, 0]
+        a = _adm(Pp[tb:tb + ts], Pp[sb:sb + ss], eta)
+        if k == 1:
+            assert a and leafid >= 0
+            cover[tb:tb + ts, sb:sb + ss] += 1
+        elif k == 2:
+            assert not a and leafid >= 0 and T.cl[tau, 3] < 0
+            cover[tb:tb + ts, sb:sb + ss] += 1
+        else:
+            assert not a and nch == 4
+            kids = {(int(T.bl[c, 0]), int(T.bl[c, 1])) for c in T.bl_child[b]}
+            want = {(int(x), int(y)) for x in T.cl[tau, 3:5] for y in T.cl[sig, 3:5]}
+            assert kids == want
+    assert (cover == 1).all()
+
+
+def test_admissibility_symmetric(oracle):
+    """Def. 2.3: adm(tau, sigma) = adm(sigma, tau), so the leaf pattern is symmetric."""
+    P = inputs.points(1, 3, 900, 2)
+    T = oracle.Tree(P, 16, 1.0)
+    kinds = {(int(a), int(b)): int(k) for a, b, k in T.bl[:, :3]}
+    for (a, b), k in kinds.items():
+        assert kinds[(b, a)] == k
+
+
+# ---------------------------------------------------------------- assembly (Alg. 6)
+
+@pytest.mark.parametrize("kernel,kind,dim", [(0, 0, 2), (1, 1, 3), (0, 1, 3)])
+def test_aca_accuracy_against_brute_force(oracle, kernel, kind, dim):
+    """Far leaves by ACA match the kernel block evaluated entry by entry (eq. (ACAblockerror)
+    with a modest constant); near leaves are the kernel block exactly."""
+    P = inputs.points(kind, dim, 600, 4)
+    T = oracle.Tree(P, 16, 1.0)
+    H = oracle.HMatrix(T, kernel, 1e-8)
+    Pp = P[T.perm]
+    for l in range(T.nleaf):
+        r0, m, c0, n = T.leaf_ranges(l)
+        K = _kernel(kernel, Pp[r0:r0 + m], Pp[c0:c0 + n])
+        if H.ranks[l] < 0:
+            assert np.array_equal(H.leaf(l), K) or np.abs(H.leaf(l) - K).max() <= 1e-15 * np.abs(K).max()
+        else:
+            U, V = H.leaf(l)
+            err = np.linalg.norm(K - U @ V.T) / np.linalg.norm(K)
+            assert err <= 1e-6, (l, err)
+
+
+def test_aca_exact_on_separable_kernel(oracle):
+    """The kernel (1 + x.y)^2 in 2-D has rank <= 6 on every block: ACA reproduces the block
+    to rounding after 6 terms; the 7th (rounding-level) term is the one the stop test
+    measures and is kept, so the stored rank is at most 7."""
+    P = inputs.points(0, 2, 500, 9)
+    T = oracle.Tree(P, 16, 1.0)
+    H = oracle.HMatrix(T, oracle.KERNEL_POLY2, 1e-12)
+    Pp = P[T.perm]
+    for l in T.far_leaves():
+        U, V = H.leaf(int(l))
+        assert U.shape[1] <= 7
+        r0, m, c0, n = T.leaf_ranges(int(l))
+        K = _kernel(2, Pp[r0:r0 + m], Pp[c0:c0 + n])
+        assert np.linalg.norm(K - U @ V.T) <= 1e-12 * np.linalg.norm(K)
+
+
+def test_fp32_storage_is_exact_rounding(oracle):
+    """prec32 stores every factor entry rounded to float once."""
+    P = inputs.points(0, 2, 300, 1)
+    T = oracle.Tree(P, 16, 1.0)
+    H64 = oracle.HMatrix(T, 0, 1e-8)
+    H32 = oracle.HMatrix(T, 0, 1e-8, prec32=True)
+    for l in range(T.nleaf):
+        a, b = H64.leaf(l), H32.leaf(l)
+        if H64.ranks[l] < 0:
+            assert np.array_equal(a.astype(np.float32).astype(np.float64), b)
+        else:
+            assert np.array_equal(a[0].astype(np.float32).astype(np.float64), b[0])
+            assert np.array_equal(a[1].astype(np.float32).astype(np.float64), b[1])
+
+
+def test_dense_sub_matches_leaves(oracle):
+    """The dense view of the H-matrix places each leaf at its (tau, sigma) position."""
+    P = inputs.points(0, 2, 256, 3)
+    T = oracle.Tree(P, 16, 1.0)
+    H = oracle.HMatrix(T, 0, 1e-9)
+    D = H.dense()
+    for l in range(T.nleaf):
+        r0, m, c0, n = T.leaf_ranges(l)
+        blk = H.leaf(l) if H.ranks[l] < 0 else H.leaf(l)[0] @ H.leaf(l)[1].T
+        assert np.allclose(D[r0:r0 + m, c0:c0 + n], blk, rtol=0, atol=1e-15)
+    sub = H.dense_sub(10, 50, 100, 77)
+    assert np.array_equal(sub, D[10:60, 100:177])
+
+
+# ---------------------------------------------------------------- dense product
+
+def test_matmul_brute_force(oracle):
+    """The product against a brute-force triple loop (tiny) and an independent BLAS call."""
+    rng = np.random.default_rng(0)
+    A = rng.standard_normal((7, 5))
+    B = rng.standard_normal((5, 9))
+    C = oracle.matmul(A, B)
+    ref = np.zeros((7, 9))
+    for i in range(7):
+        for j in range(9):
+            for k in range(5):
+                ref[i, j] += A[i, k] * B[k, j]
+    assert np.abs(C - ref).max() <= 1e-14
+    A = rng.standard_normal((130, 70))
+    B = rng.standard_normal((70, 90))
+    assert np.abs(oracle.matmul(A, B) - A @ B).max() <= 1e-12
+
+
+def test_block_product_matches_dense(oracle):
+    """C|tau x sigma = A|tau x I * B|I x sigma equals the block of the full product."""
+    P = inputs.points(1, 3, 400, 6)
+    T = oracle.Tree(P, 16, 1.0)
+    A = oracle.HMatrix(T, 0, 1e-9)
+    B = oracle.HMatrix(T, 1, 1e-9)
+    DC = oracle.matmul(A.dense(), B.dense())
+    for l in list(T.far_leaves()[:5]) + list(T.near_leaves()[:3]):
+        r0, m, c0, n = T.leaf_ranges(int(l))
+        Cb = oracle.block_product(A, B, r0, m, c0, n, chunk=37)
+        assert np.abs(Cb - DC[r0:r0 + m, c0:c0 + n]).max() <= 1e-12 * np.abs(DC).max()
+
+
+def test_eta_to_zero_gives_dense_kernel(oracle):
+    """Closed form: with eta -> 0 nothing is admissible, every leaf is dense, and the H-matrix
+    and its product are the kernel matrix and its square exactly."""
+    P = inputs.points(0, 2, 128, 8)
+    T = oracle.Tree(P, 16, 1e-9)
+    assert len(T.far_leaves()) == 0
+    H = oracle.HMatrix(T, 0, 1e-9)
+    Pp = P[T.perm]
+    K = _kernel(0, Pp, Pp)
+    assert np.abs(H.dense() - K).max() <= 1e-15
+    assert np.abs(oracle.matmul(H.dense(), H.dense()) - K @ K).max() <= 1e-12
+
+
+# ---------------------------------------------------------------- SVD and eps-rank
+
+@pytest.mark.parametrize("m,n", [(1, 1), (5, 3), (3, 5), (40, 40), (64, 20), (17, 90)])
+def test_svd_against_lapack_and_identities(oracle, m, n):
+    rng = np.random.default_rng(m * 100 + n)
+    M = rng.standard_normal((m, n)) @ np.diag(np.logspace(0, -12, n))
+    s, U, V = oracle.svd(M)
+    s_ref = np.linalg.svd(M, compute_uv=False)
+    assert np.abs(s - s_ref).max() <= 1e-13 * s_ref[0]
+    p = min(m, n)
+    assert np.abs(U.T @ U - np.eye(p)).max() <= 1e-12 or s_ref[-1] < 1e-13 * s_ref[0]
+    assert np.abs(V.T @ V - np.eye(p)).max() <= 1e-12
+    assert np.abs(U * s @ V.T - M).max() <= 1e-13 * s[0]
+    # Eckart-Young: the rank-k truncation error is the tail of the singular values
+    for k in range(p + 1):
+        err = np.linalg.norm(M - (U[:, :k] * s[:k]) @ V[:, :k].T)
+        tail = np.sqrt(np.sum(s[k:] ** 2))
+        assert abs(err - tail) <= 1e-12 * s[0] + 1e-10 * tail
+
+
+def test_svd_rank_deficient_and_zero(oracle):
+    rng = np.random.default_rng(3)
+    M = rng.standard_normal((30, 4)) @ rng.standard_normal((4, 25))
+    s, _, _ = oracle.svd(M, vectors=False)
+    assert (s[4:] <= 1e-12 * s[0]).all() and s[3] > 1e-3 * s[0]
+    s, _, _ = oracle.svd(np.zeros((6, 4)), vectors=False)
+    assert (s == 0).all()
+
+
+def test_eps_rank_closed_forms(oracle):
+    s = np.array([1.0, 1e-3, 1e-7])
+    tot = np.sqrt(np.sum(s ** 2))
+    assert oracle.eps_rank(s, 1e-6) == 2          # tail 1e-7 <= 1e-6 * tot
+    assert oracle.eps_rank(s, 1e-8) == 3
+    assert oracle.eps_rank(s, 2e-3) == 1          # tail ~1e-3 <= 2e-3
+    assert oracle.eps_rank(s, 1.0) == 0
+    assert oracle.eps_rank(np.zeros(4), 1e-6) == 0
+    # boundary: tail exactly eps * norm counts as within ("<=")
+    s = np.array([3.0, 4.0])
+    assert oracle.eps_rank(s, 4.0 / 5.0) == 1
+    assert oracle.eps_rank(s, np.nextafter(4.0 / 5.0, 0)) == 2
+    _ = tot
+
+
+def test_eps_rank_monotone(oracle):
+    rng = np.random.default_rng(5)
+    s = np.sort(np.abs(rng.standard_normal(50)) * np.logspace(0, -14, 50))[::-1]
+    ks = [oracle.eps_rank(s, e) for e in np.logspace(-16, 0, 60)]
+    assert all(a >= b for a, b in zip(ks, ks[1:]))
+    assert ks[0] == 50
+
+
+# ---------------------------------------------------------------- product truth & sum-expressions
+
+def test_product_of_separable_kernels_has_low_rank(oracle):
+    """Closed form: (1 + x.y)^2 has global rank <= 6 in 2-D, so every block of the product
+    of two such H-matrices has eps-rank <= 6 even at eps = 1e-12."""
+    P = inputs.points(0, 2, 512, 2)
+    T = oracle.Tree(P, 16, 1.0)
+    A = oracle.HMatrix(T, oracle.KERNEL_POLY2, 1e-14)
+    _, truths = oracle.product_truth(A, A, 1e-12)
+    assert max(t.k_eps for t in truths.values()) <= 6
+
+
+def test_identity_factor_gives_best_approx_of_other(oracle):
+    """Closed form: with A = diag (near leaves diagonal, far leaves zero) the product's far
+    blocks are diag * B|b, whose eps-rank is that of B|b scaled by the rows."""
+    P = inputs.points(0, 2, 256, 4)
+    T = oracle.Tree(P, 16, 1.0)
+    B = oracle.HMatrix(T, 0, 1e-12)
+    DB = B.dense()
+    d = 1.0 + inputs.uniform01(77, 256)
+    DA = np.diag(d)
+    DC = oracle.matmul(DA, DB)
+    assert np.abs(DC - d[:, None] * DB).max() <= 1e-15 * np.abs(DB).max() * 2
+
+
+def test_sumexpr_reproduces_product_blocks(oracle):
+    """Alg. 3 restriction from S(I,I) = HK (Alg. 4): for every leaf, the low-rank terms plus
+    the H-pairs of its sum-expression add up to the exact product block (Sec. 3.2), and the
+    number of low-rank terms matches the symbolic count."""
+    P = inputs.points(1, 3, 700, 12)
+    T = oracle.Tree(P, 16, 1.0)
+    A = oracle.HMatrix(T, 0, 1e-10)
+    B = oracle.HMatrix(T, 1, 1e-10)
+    DC = oracle.matmul(A.dense(), B.dense())
+    lr, hp, at = T.sumexpr_counts()
+    assert np.array_equal(at.sum(1), lr)
+    for l in range(T.nleaf):
+        r0, m, c0, n = T.leaf_ranges(l)
+        S, nt = oracle.sumexpr_eval(A, B, l)
+        assert nt == lr[l]
+        blk = DC[r0:r0 + m, c0:c0 + n]
+        assert np.linalg.norm(S - blk) <= 1e-13 * max(np.linalg.norm(blk), 1e-300)
+
+
+def test_lemma_5_3_term_bound(oracle):
+    """Lemma 5.3: S(tau, sigma) holds at most C_sp * level(tau x sigma) low-rank terms, and
+    terms are only created at levels where the target's ancestor has a far neighbour."""
+    for kind, dim, n, leaf in [(0, 2, 2048, 32), (1, 3, 4096, 32)]:
+        P = inputs.points(kind, dim, n, 0)
+        T = oracle.Tree(P, leaf, 1.0)
+        lr, hp, at = T.sumexpr_counts()
+        csp = T.csp()
+        lvl = T.leaf_blocks[:, 3]
+        assert (lr <= csp * lvl).all()
+        assert (hp <= csp).all()
+        assert (at[:, 0] == 0).all()     # S(I, I) holds no low-rank terms
+        # near leaves sit on the last level; their H-pairs are leaf x leaf pairs
+        near = T.leaf_blocks[:, 2] == 2
+        assert (lvl[near] == T.depth).all()
+
+
+def test_truth_eckart_young_invariant(oracle):
+    """For the truth of a product block: err of the best rank-k_eps approximation equals the
+    SVD tail and is <= eps * ||block||; rank k_eps - 1 would exceed eps."""
+    P = inputs.points(0, 2, 512, 0)
+    T = oracle.Tree(P, 16, 1.0)
+    A = oracle.HMatrix(T, 0, 1e-10)
+    DC = oracle.matmul(A.dense(), A.dense())
+    for l in T.far_leaves()[:40]:
+        r0, m, c0, n = T.leaf_ranges(int(l))
+        blk = DC[r0:r0 + m, c0:c0 + n]
+        L, R = oracle.best_approx(blk, 1e-6)
+        k = L.shape[1]
+        err = np.linalg.norm(blk - L @ R.T)
+        nb = np.linalg.norm(blk)
+        assert err <= 1e-6 * nb * (1 + 1e-10)
+        s = np.linalg.svd(blk, compute_uv=False)
+        if k > 0:
+            assert np.sqrt(np.sum(s[k - 1:] ** 2)) > 1e-6 * nb * (1 - 1e-10)

@@ -1,0 +1,189 @@
+/*
+ * hmat.h -- C-ABI of the GB300 H-matrix product library (libhmat.so).
+ *
+ * The library computes the product of two hierarchical (H-) matrices on one block-cluster
+ * tree and compresses every admissible target block to its eps-best low-rank approximation,
+ * following Doelz, Harbrecht, Multerer, "On the best approximation of the hierarchical
+ * matrix product": the product L = HK is written as the sum-expression S(I,I) = HK
+ * (Sec. 3.1), restricted block by block (Algorithm 3) and, at every leaf, either truncated
+ * to low rank (far leaves, operator T of Algorithm 4, realised by the blocked adaptive
+ * randomized range finder of Algorithm 8 with the stop test eq. (truncaca)) or evaluated
+ * densely (near leaves, evaluate() of Algorithm 4).
+ *
+ * Conventions for every entry point:
+ *   - Every call returns an hmat_status; nothing aborts or throws across the ABI. On error an
+ *     output handle is set to NULL and no partial object leaks; hmat_last_error() returns a
+ *     thread-local message describing the last failure on the calling thread.
+ *   - Host buffers are owned by the caller. Device memory is owned by the library and is
+ *     taken from the allocator set with hmat_set_allocator (default: the CUDA stream-ordered
+ *     pool, cudaMallocAsync/cudaFreeAsync, on the given stream).
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream). Work is
+ *     enqueued on it; calls that read results back to the host synchronise it (stated per call).
+ *   - Index conventions: points are given in their ORIGINAL order; internally the library
+ *     permutes them along its cluster tree. Leaf ranges (hmat_leaf) are in PERMUTED order;
+ *     hmat_permutation gives perm[i] = original index of permuted position i.
+ *   - Matrices on the host are column-major.
+ *   - An hmat_t is immutable once created and may be read from several threads at once.
+ */
+#ifndef HMAT_H
+#define HMAT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hmat_s *hmat_t;
+
+typedef enum {
+  HMAT_OK = 0,
+  HMAT_EINVAL = 1,     /* invalid argument (bad size, NULL pointer, eps <= 0, NaN points) */
+  HMAT_ENOMEM = 2,     /* a device or host allocation failed */
+  HMAT_ECUDA = 3,      /* a CUDA runtime call or kernel launch failed */
+  HMAT_ENOTCONV = 4,   /* some far block hit max_rank / max_rounds before the stop test held;
+                          the result is complete and usable, see hmat_stats.not_converged */
+  HMAT_ETIMEOUT = 5,   /* reserved: a bounded device wait gave up */
+  HMAT_EMISMATCH = 6   /* the two factors of a product are not on the same block tree */
+} hmat_status;
+
+/* Kernel functions k(x, y) used to assemble test matrices (r = |x - y|). */
+typedef enum {
+  HMAT_K_EXP = 0,      /* exp(-r)            (Sec. 6.1 uses this kernel) */
+  HMAT_K_INVQ = 1,     /* 1 / (1 + r^2) */
+  HMAT_K_POLY2 = 2     /* (1 + x.y)^2, separable, rank <= (d+1)(d+2)/2: a closed-form check */
+} hmat_kernel;
+
+/* Seeded point distributions (splitmix64 stream; see hmat_points). */
+typedef enum {
+  HMAT_PTS_CUBE = 0,   /* uniform in [0,1]^dim, dim in {1,2,3} */
+  HMAT_PTS_SPHERE = 1  /* uniform on the unit sphere S^2, dim = 3 */
+} hmat_ptdist;
+
+typedef enum {
+  HMAT_MODE_F64 = 0,   /* every contraction in FP64 ("plain" path) */
+  HMAT_MODE_MIXED = 1  /* contractions in the factors' precision (FP32 for factor_prec = 32),
+                          orthogonalisation (Gram, Cholesky) and the core eigen-solve in FP64 */
+} hmat_mode;
+
+typedef struct {
+  int leaf_size;       /* n_min: leaf clusters hold at most this many points (>= 1) */
+  double eta;          /* admissibility: max(diam tau, diam sigma) <= eta * dist(tau, sigma) */
+  double aca_eps;      /* ACA stop tolerance for far leaves (Algorithm 6, eq. (truncaca)) */
+  int factor_prec;     /* 64: store factors in FP64; 32: store factors in FP32 */
+  int aca_kmax;        /* rank cap of ACA (0 = default 128) */
+} hmat_build_opts;
+
+typedef struct {
+  double eps;          /* relative Frobenius tolerance per far block (> 0) */
+  int mode;            /* hmat_mode */
+  int rank_proposal;   /* 0: none (first round uses block_width columns);
+                          1: learned proposal (reserved; currently treated as 0) */
+  int max_rank;        /* cap on the sampled basis per block (0 = default 96) */
+  int max_rounds;      /* cap on adaptive rounds (0 = default max_rank / block_width + 1) */
+  int block_width;     /* columns added per adaptive round (0 = default 8; <= 32) */
+  uint64_t seed;       /* seed of the Gaussian test matrices (counter-based, splitmix64) */
+} hmat_mult_opts;
+
+typedef struct {
+  int64_t row_begin, row_size;   /* permuted row range of tau */
+  int64_t col_begin, col_size;   /* permuted column range of sigma */
+  int level;                     /* level of tau x sigma in the block tree (root = 0) */
+  int far;                       /* 1: admissible leaf (low-rank U V^T), 0: near leaf (dense) */
+  int rank;                      /* far: rank of U V^T; near: -1 */
+} hmat_leaf;
+
+typedef struct {
+  int64_t n;                     /* #I */
+  int depth;                     /* depth of the cluster tree */
+  int csp;                       /* C_sp: max number of blocks sharing one row cluster */
+  int64_t n_far, n_near;         /* number of far / near leaves */
+  int64_t storage_bytes;         /* bytes of the stored factors and dense leaves */
+  int factor_prec;               /* 32 or 64 */
+  int max_rank;                  /* largest far-leaf rank */
+  /* filled by hmat_multiply on its output handle (zero elsewhere): */
+  int64_t n_terms;               /* low-rank products created by the restriction (a2) */
+  int64_t n_lr_refs;             /* sum over leaves of their low-rank term counts */
+  int64_t n_hpairs;              /* sum over leaves of their H-pair counts */
+  int rounds;                    /* adaptive rounds run */
+  int64_t not_converged;         /* far blocks that hit max_rank or max_rounds */
+  double flops_apply;            /* algorithmic flops of the sum-expression applications */
+  double flops_terms;            /* algorithmic flops of the low-rank products (a2) */
+  double flops_near;             /* algorithmic flops of the near-field evaluation */
+  double bytes_apply;            /* algorithmic bytes read by the sum-expression applications */
+  double ms_plan, ms_terms, ms_near, ms_sample, ms_final;  /* device/host phase times */
+} hmat_stats_t;
+
+/* Fill xyz (n*dim doubles, row-major, caller-owned) with the seeded points of the given
+ * distribution: splitmix64 stream of `seed`, u = (z >> 11) * 2^-53; cube: point i uses draws
+ * dim*i .. dim*i+dim-1; sphere: draws 2i, 2i+1 -> z = 2u1 - 1, phi = 2 pi u2,
+ * (sqrt(1-z^2) cos phi, sqrt(1-z^2) sin phi, z). EINVAL on a bad dim/n or NULL xyz. */
+hmat_status hmat_points(hmat_ptdist dist, int dim, int64_t n, uint64_t seed, double *xyz);
+
+/* Build the H-matrix of kernel `kernel` on the points xyz (n x dim, row-major, original
+ * order, host, caller-owned): cluster tree by cardinality-balanced bisection (Def. 2.2),
+ * block tree by Algorithm 1 with eta-admissibility (Def. 2.3), near leaves evaluated densely,
+ * far leaves by ACA (Algorithm 6) on the GPU. If tree_from is not NULL its cluster and block
+ * tree are reused (xyz must then hold the same points; only kernel and factors differ), which
+ * is how two factors of a product are put on one block tree (Sec. 3). Synchronises `stream`
+ * once (to size the far-leaf storage). EINVAL on bad sizes, NaN/Inf points or opts;
+ * EMISMATCH if tree_from was built on other points. */
+hmat_status hmat_build(const double *xyz, int64_t n, int dim, hmat_kernel kernel,
+                       const hmat_build_opts *opts, const hmat_t tree_from, void *stream,
+                       hmat_t *out);
+
+/* C ~= A B with every far block of C the eps-approximation of its sum-expression
+ * (Algorithm 4 with the truncation operator of Algorithm 8 + eq. (truncaca), then an FP64
+ * eigen-truncation of the sampled core to relative Frobenius error eps) and every near
+ * block evaluated exactly. A and B must share one block tree (EMISMATCH otherwise) and one
+ * factor precision. C lives on the same tree with A's factor precision. Synchronises
+ * `stream` at the end of every adaptive round and at the end. Returns HMAT_ENOTCONV (with a
+ * valid C) when some block hit the rank or round cap. */
+hmat_status hmat_multiply(const hmat_t A, const hmat_t B, const hmat_mult_opts *opts,
+                          void *stream, hmat_t *C);
+
+/* Dense copy of the whole matrix in ORIGINAL point order into the host buffer out
+ * (column-major, leading dimension ld >= n). Synchronises `stream` of the handle's last
+ * use. Intended for checking small problems. */
+hmat_status hmat_to_dense(const hmat_t h, double *out, int64_t ld);
+
+/* Number of leaves of the block tree (far + near), numbered in depth-first order. */
+hmat_status hmat_leaf_count(const hmat_t h, int64_t *n_leaves);
+
+/* Geometry, kind and rank of leaf i (0 <= i < leaf count). */
+hmat_status hmat_leaf_info(const hmat_t h, int64_t i, hmat_leaf *info);
+
+/* Copy leaf i to the host as FP64: far leaf -> U (row_size x rank) into U and V
+ * (col_size x rank) into V; near leaf -> the dense block (row_size x col_size) into U,
+ * V unused. Column-major, caller-owned. Synchronises. */
+hmat_status hmat_leaf_get(const hmat_t h, int64_t i, double *U, double *V);
+
+/* perm[i] = original index of permuted position i (n entries, caller-owned). */
+hmat_status hmat_permutation(const hmat_t h, int64_t *perm);
+
+/* Structure and, for products, work statistics of h. */
+hmat_status hmat_stats(const hmat_t h, hmat_stats_t *stats);
+
+/* Per leaf: number of low-rank terms and of H-pairs in the sum-expression S(leaf) that the
+ * restriction of Algorithm 3 builds from S(I,I) = AB (Algorithm 4); arrays of leaf-count
+ * entries, caller-owned. Needs only the block tree of A (B must share it). */
+hmat_status hmat_sumexpr_counts(const hmat_t A, const hmat_t B, int64_t *n_lowrank, int64_t *n_hpairs);
+
+/* Release h and its device memory (NULL is a no-op). */
+void hmat_destroy(hmat_t h);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *hmat_last_error(void);
+
+/* Route the library's device allocations through alloc/free (both non-NULL), or restore the
+ * default stream-ordered CUDA pool (both NULL). alloc(bytes, stream, ctx) returns a device
+ * pointer or NULL; free(ptr, ctx) releases it. Not thread-safe against concurrent calls. */
+hmat_status hmat_set_allocator(void *(*alloc)(size_t bytes, void *stream, void *ctx),
+                               void (*free_fn)(void *ptr, void *ctx), void *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HMAT_H */

@@ -1,0 +1,847 @@
+// hmat_api.cpp -- the C-ABI of libhmat.so: handles, allocation, and the orchestration of the
+// product (Algorithm 4 driven level-free: all far targets of the whole tree are truncated
+// together by the blocked adaptive range finder, all near targets evaluated together).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <limits>
+#include <memory>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/hmat.h"
+#include "hmat_internal.h"
+#include "hmat_tree.h"
+
+using namespace hm;
+
+// ------------------------------------------------------------------ errors
+
+namespace {
+
+thread_local std::string g_last_error;
+
+struct HErr {
+  hmat_status st;
+  std::string msg;
+};
+
+[[noreturn]] void fail(hmat_status st, const std::string &msg) { throw HErr{st, msg}; }
+
+void ck(cudaError_t e, const char *what) {
+  if (e != cudaSuccess) fail(HMAT_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+template <typename F>
+hmat_status guard(F &&f) {
+  try {
+    f();
+    g_last_error.clear();
+    return HMAT_OK;
+  } catch (const HErr &e) {
+    g_last_error = e.msg;
+    return e.st;
+  } catch (const std::bad_alloc &) {
+    g_last_error = "host allocation failed";
+    return HMAT_ENOMEM;
+  } catch (const std::exception &e) {
+    g_last_error = e.what();
+    return HMAT_EINVAL;
+  }
+}
+
+// ------------------------------------------------------------------ allocation
+
+void *(*g_alloc)(size_t, void *, void *) = nullptr;
+void (*g_free)(void *, void *) = nullptr;
+void *g_ctx = nullptr;
+bool g_pool_set = false;
+
+void *dev_alloc(size_t bytes, cudaStream_t s) {
+  if (bytes == 0) bytes = 16;
+  if (g_alloc) {
+    void *p = g_alloc(bytes, (void *)s, g_ctx);
+    if (!p) fail(HMAT_ENOMEM, "device allocation of " + std::to_string(bytes) + " bytes failed (custom allocator)");
+    return p;
+  }
+  if (!g_pool_set) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+      uint64_t thr = std::numeric_limits<uint64_t>::max();
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    g_pool_set = true;
+  }
+  void *p = nullptr;
+  cudaError_t e = cudaMallocAsync(&p, bytes, s);
+  if (e != cudaSuccess || !p) {
+    cudaGetLastError();
+    fail(HMAT_ENOMEM, "device allocation of " + std::to_string(bytes) + " bytes failed: " + cudaGetErrorString(e));
+  }
+  return p;
+}
+
+void dev_free(void *p, cudaStream_t s) {
+  if (!p) return;
+  if (g_free) g_free(p, g_ctx);
+  else cudaFreeAsync(p, s);
+}
+
+struct DevBuf {
+  void *p = nullptr;
+  size_t bytes = 0;
+  cudaStream_t s = nullptr;
+  DevBuf() = default;
+  DevBuf(size_t b, cudaStream_t st) : bytes(b), s(st) { p = dev_alloc(b, st); }
+  DevBuf(const DevBuf &) = delete;
+  DevBuf &operator=(const DevBuf &) = delete;
+  DevBuf(DevBuf &&o) noexcept : p(o.p), bytes(o.bytes), s(o.s) { o.p = nullptr; }
+  DevBuf &operator=(DevBuf &&o) noexcept {
+    if (this != &o) {
+      release();
+      p = o.p; bytes = o.bytes; s = o.s;
+      o.p = nullptr;
+    }
+    return *this;
+  }
+  ~DevBuf() { release(); }
+  void release() {
+    if (p) dev_free(p, s);
+    p = nullptr;
+  }
+  template <typename T>
+  T *as() const { return (T *)p; }
+};
+
+template <typename T>
+DevBuf upload(const std::vector<T> &v, cudaStream_t s) {
+  DevBuf b(sizeof(T) * std::max<size_t>(v.size(), 1), s);
+  if (!v.empty()) ck(cudaMemcpyAsync(b.p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, s), "upload");
+  return b;
+}
+
+double now_ms() {
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ handle
+
+struct hmat_s {
+  std::shared_ptr<Tree> tree;
+  int prec = 64;                   // element type of the factor buffer
+  int kernel = -1;                 // -1 for products
+  std::vector<LeafDev> leaves;     // host copy
+  DevBuf d_leaves;
+  DevBuf d_data;
+  int64_t data_elems = 0;
+  hmat_stats_t stats{};
+  cudaStream_t stream = nullptr;
+};
+
+namespace {
+
+size_t esize(int prec) { return prec == 64 ? sizeof(double) : sizeof(float); }
+
+// storage (elements) of every block's subtree, bottom-up
+std::vector<double> block_storage(const Tree &t, const std::vector<LeafDev> &lv) {
+  std::vector<double> st(t.bl.size(), 0.0);
+  for (int b = (int)t.bl.size() - 1; b >= 0; b--) {  // children have larger ids than parents
+    const Block &bk = t.bl[b];
+    if (bk.kind == BK_INNER) {
+      double s = 0;
+      for (int c = 0; c < bk.nchild; c++) s += st[bk.child[c]];
+      st[b] = s;
+    } else {
+      const LeafDev &l = lv[bk.leaf];
+      st[b] = l.rank < 0 ? (double)l.m * l.n : (double)l.rank * (l.m + l.n);
+    }
+  }
+  return st;
+}
+
+void ensure_tree_device(Tree &t, cudaStream_t s) {
+  if (t.d_pts) return;
+  ck(cudaMalloc(&t.d_pts, sizeof(double) * t.pts.size()), "cudaMalloc points");
+  ck(cudaMemcpyAsync(t.d_pts, t.pts.data(), sizeof(double) * t.pts.size(), cudaMemcpyHostToDevice, s), "points");
+  std::vector<BlockDev> bd(t.bl.size());
+  for (size_t b = 0; b < t.bl.size(); b++) {
+    const Block &bk = t.bl[b];
+    bd[b].row = t.cl[bk.tau].begin;
+    bd[b].col = t.cl[bk.sigma].begin;
+    bd[b].m = (int32_t)t.cl[bk.tau].size;
+    bd[b].n = (int32_t)t.cl[bk.sigma].size;
+    bd[b].leaf_lo = bk.leaf_lo;
+    bd[b].leaf_hi = bk.leaf_hi;
+  }
+  ck(cudaMalloc(&t.d_blocks, sizeof(BlockDev) * bd.size()), "cudaMalloc blocks");
+  ck(cudaMemcpyAsync(t.d_blocks, bd.data(), sizeof(BlockDev) * bd.size(), cudaMemcpyHostToDevice, s), "blocks");
+  ck(cudaStreamSynchronize(s), "tree upload");
+}
+
+std::vector<LeafDev> base_leaves(const Tree &t) {
+  std::vector<LeafDev> lv(t.leaf_block.size());
+  for (size_t l = 0; l < lv.size(); l++) {
+    const Block &bk = t.bl[t.leaf_block[l]];
+    lv[l].row = t.cl[bk.tau].begin;
+    lv[l].col = t.cl[bk.sigma].begin;
+    lv[l].m = (int32_t)t.cl[bk.tau].size;
+    lv[l].n = (int32_t)t.cl[bk.sigma].size;
+    lv[l].rank = bk.kind == BK_NEAR ? -1 : 0;
+    lv[l].level = bk.level;
+    lv[l].off_u = lv[l].off_v = 0;
+  }
+  return lv;
+}
+
+void fill_structure_stats(hmat_s *h) {
+  const Tree &t = *h->tree;
+  hmat_stats_t &s = h->stats;
+  s.n = t.n;
+  s.depth = t.depth;
+  s.csp = t.csp;
+  s.n_far = s.n_near = 0;
+  s.max_rank = 0;
+  for (const LeafDev &l : h->leaves) {
+    if (l.rank < 0) s.n_near++;
+    else {
+      s.n_far++;
+      s.max_rank = std::max(s.max_rank, (int)l.rank);
+    }
+  }
+  s.storage_bytes = h->data_elems * (int64_t)esize(h->prec);
+  s.factor_prec = h->prec;
+}
+
+bool same_points(const Tree &t, const double *xyz, int64_t n, int dim) {
+  return t.n == n && t.dim == dim && std::memcmp(t.orig.data(), xyz, sizeof(double) * n * dim) == 0;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ C-ABI
+
+extern "C" {
+
+const char *hmat_last_error(void) { return g_last_error.c_str(); }
+
+hmat_status hmat_set_allocator(void *(*alloc)(size_t, void *, void *), void (*free_fn)(void *, void *), void *ctx) {
+  return guard([&] {
+    if ((alloc == nullptr) != (free_fn == nullptr)) fail(HMAT_EINVAL, "alloc and free must both be set or both NULL");
+    g_alloc = alloc;
+    g_free = free_fn;
+    g_ctx = alloc ? ctx : nullptr;
+  });
+}
+
+hmat_status hmat_points(hmat_ptdist dist, int dim, int64_t n, uint64_t seed, double *xyz) {
+  return guard([&] {
+    if (n < 0 || (n > 0 && !xyz)) fail(HMAT_EINVAL, "bad n or NULL xyz");
+    auto draw = [&](uint64_t c) {  // c-th output of the splitmix64 stream
+      uint64_t z = seed + (c + 1) * 0x9E3779B97F4A7C15ull;
+      z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+      z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+      z = z ^ (z >> 31);
+      return (double)(z >> 11) * 0x1.0p-53;
+    };
+    if (dist == HMAT_PTS_CUBE) {
+      if (dim < 1 || dim > 3) fail(HMAT_EINVAL, "cube points need dim in 1..3");
+      for (int64_t i = 0; i < n * dim; i++) xyz[i] = draw((uint64_t)i);
+    } else if (dist == HMAT_PTS_SPHERE) {
+      if (dim != 3) fail(HMAT_EINVAL, "sphere points need dim 3");
+      const double two_pi = 2.0 * 3.14159265358979323846;
+      for (int64_t i = 0; i < n; i++) {
+        const double z = 2.0 * draw(2 * (uint64_t)i) - 1.0;
+        const double phi = two_pi * draw(2 * (uint64_t)i + 1);
+        const double s = std::sqrt(1.0 - z * z);
+        xyz[3 * i] = s * std::cos(phi);
+        xyz[3 * i + 1] = s * std::sin(phi);
+        xyz[3 * i + 2] = z;
+      }
+    } else {
+      fail(HMAT_EINVAL, "unknown point distribution");
+    }
+  });
+}
+
+hmat_status hmat_build(const double *xyz, int64_t n, int dim, hmat_kernel kernel, const hmat_build_opts *opts,
+                       const hmat_t tree_from, void *stream, hmat_t *out) {
+  if (out) *out = nullptr;
+  return guard([&] {
+    if (!out || !xyz || !opts) fail(HMAT_EINVAL, "NULL argument");
+    if (n < 1 || dim < 1 || dim > 3) fail(HMAT_EINVAL, "need n >= 1 and dim in 1..3");
+    if (kernel < HMAT_K_EXP || kernel > HMAT_K_POLY2) fail(HMAT_EINVAL, "unknown kernel");
+    if (opts->factor_prec != 32 && opts->factor_prec != 64) fail(HMAT_EINVAL, "factor_prec must be 32 or 64");
+    if (opts->leaf_size < 1 || opts->leaf_size > 128) fail(HMAT_EINVAL, "leaf_size must be in 1..128");
+    if (!(opts->eta > 0.0) || !(opts->aca_eps > 0.0)) fail(HMAT_EINVAL, "eta and aca_eps must be > 0");
+    const int kmax = opts->aca_kmax > 0 ? opts->aca_kmax : 128;
+    if (kmax > 128) fail(HMAT_EINVAL, "aca_kmax must be <= 128");
+    for (int64_t i = 0; i < n * dim; i++)
+      if (!std::isfinite(xyz[i])) fail(HMAT_EINVAL, "non-finite point coordinate");
+    cudaStream_t s = (cudaStream_t)stream;
+    auto h = std::make_unique<hmat_s>();
+    h->stream = s;
+    if (tree_from) {
+      if (!same_points(*tree_from->tree, xyz, n, dim) || tree_from->tree->leaf_size != opts->leaf_size ||
+          tree_from->tree->eta != opts->eta)
+        fail(HMAT_EMISMATCH, "tree_from was built on other points or tree options");
+      h->tree = tree_from->tree;
+    } else {
+      h->tree = build_tree(xyz, n, dim, opts->leaf_size, opts->eta);
+      if (!h->tree) fail(HMAT_EINVAL, "tree construction failed");
+    }
+    Tree &t = *h->tree;
+    ensure_tree_device(t, s);
+    h->prec = opts->factor_prec;
+    h->kernel = kernel;
+    h->leaves = base_leaves(t);
+    std::vector<LeafDev> &lv = h->leaves;
+    std::vector<int32_t> near_ids, far_ids;
+    for (size_t l = 0; l < lv.size(); l++) (lv[l].rank < 0 ? near_ids : far_ids).push_back((int32_t)l);
+    // ACA in batches of at most ~1 GiB of FP64 scratch; each batch is compacted into an
+    // exact-size buffer, and the final factor buffer [near leaves | far leaves] is assembled
+    // once every rank is known.
+    struct BatchOut {
+      DevBuf buf;
+      int64_t elems;
+      std::vector<int32_t> ids;
+    };
+    std::vector<BatchOut> batches;
+    {
+      DevBuf d_lv0 = upload(lv, s);
+      size_t pos = 0;
+      const size_t cap_elems = (size_t)1 << 27;
+      while (pos < far_ids.size()) {
+        std::vector<int64_t> soff;
+        std::vector<int32_t> ids;
+        size_t tot = 0;
+        while (pos < far_ids.size()) {
+          const LeafDev &l = lv[far_ids[pos]];
+          const size_t need = (size_t)(l.m + l.n) * kmax + l.m;
+          if (!ids.empty() && tot + need > cap_elems) break;
+          soff.push_back((int64_t)tot);
+          ids.push_back(far_ids[pos]);
+          tot += need;
+          pos++;
+        }
+        DevBuf scratch(sizeof(double) * tot, s), d_soff = upload(soff, s), d_ids = upload(ids, s);
+        DevBuf d_rk(sizeof(int32_t) * ids.size(), s);
+        ck(launch_aca(kernel, t.d_pts, dim, d_lv0.as<LeafDev>(), d_ids.as<int32_t>(), (int)ids.size(), opts->aca_eps,
+                      kmax, scratch.as<double>(), d_soff.as<int64_t>(), d_rk.as<int32_t>(), s),
+           "ACA launch");
+        std::vector<int32_t> rk(ids.size());
+        ck(cudaMemcpyAsync(rk.data(), d_rk.p, sizeof(int32_t) * ids.size(), cudaMemcpyDeviceToHost, s), "ranks");
+        ck(cudaStreamSynchronize(s), "ACA");
+        // batch-relative offsets
+        std::vector<LeafDev> blv = lv;
+        int64_t e = 0;
+        for (size_t i = 0; i < ids.size(); i++) {
+          LeafDev &l = blv[ids[i]];
+          l.rank = rk[i];
+          l.off_u = e;
+          l.off_v = e + (int64_t)l.m * l.rank;
+          e = l.off_v + (int64_t)l.n * l.rank;
+          lv[ids[i]].rank = rk[i];
+          lv[ids[i]].off_u = l.off_u;  // relative for now
+        }
+        BatchOut bo;
+        bo.elems = e;
+        bo.ids = ids;
+        bo.buf = DevBuf(esize(h->prec) * (size_t)std::max<int64_t>(e, 1), s);
+        DevBuf d_blv = upload(blv, s);
+        ck(launch_aca_compact(h->prec, d_blv.as<LeafDev>(), d_ids.as<int32_t>(), (int)ids.size(), scratch.as<double>(),
+                              d_soff.as<int64_t>(), kmax, bo.buf.p, s),
+           "ACA compaction");
+        ck(cudaStreamSynchronize(s), "ACA compaction");
+        batches.push_back(std::move(bo));
+      }
+    }
+    int64_t off = 0;
+    for (int32_t id : near_ids) {
+      lv[id].off_u = off;
+      off += (int64_t)lv[id].m * lv[id].n;
+    }
+    std::vector<int64_t> batch_base;
+    for (BatchOut &bo : batches) {
+      batch_base.push_back(off);
+      for (int32_t id : bo.ids) {
+        LeafDev &l = lv[id];
+        l.off_u += off;
+        l.off_v = l.off_u + (int64_t)l.m * l.rank;
+      }
+      off += bo.elems;
+    }
+    h->data_elems = off;
+    h->d_data = DevBuf(esize(h->prec) * (size_t)std::max<int64_t>(off, 1), s);
+    for (size_t i = 0; i < batches.size(); i++)
+      if (batches[i].elems)
+        ck(cudaMemcpyAsync((char *)h->d_data.p + esize(h->prec) * batch_base[i], batches[i].buf.p,
+                           esize(h->prec) * batches[i].elems, cudaMemcpyDeviceToDevice, s),
+           "assemble factors");
+    h->d_leaves = upload(lv, s);
+    DevBuf d_near = upload(near_ids, s);
+    ck(launch_kernel_dense(h->prec, kernel, t.d_pts, dim, h->d_leaves.as<LeafDev>(), d_near.as<int32_t>(),
+                           (int)near_ids.size(), h->d_data.p, s),
+       "dense leaves");
+    ck(cudaStreamSynchronize(s), "build");
+    fill_structure_stats(h.get());
+    *out = h.release();
+  });
+}
+
+void hmat_destroy(hmat_t h) {
+  if (!h) return;
+  delete h;
+}
+
+hmat_status hmat_leaf_count(const hmat_t h, int64_t *n_leaves) {
+  return guard([&] {
+    if (!h || !n_leaves) fail(HMAT_EINVAL, "NULL argument");
+    *n_leaves = (int64_t)h->leaves.size();
+  });
+}
+
+hmat_status hmat_leaf_info(const hmat_t h, int64_t i, hmat_leaf *info) {
+  return guard([&] {
+    if (!h || !info) fail(HMAT_EINVAL, "NULL argument");
+    if (i < 0 || i >= (int64_t)h->leaves.size()) fail(HMAT_EINVAL, "leaf index out of range");
+    const LeafDev &l = h->leaves[i];
+    info->row_begin = l.row;
+    info->row_size = l.m;
+    info->col_begin = l.col;
+    info->col_size = l.n;
+    info->level = l.level;
+    info->far = l.rank >= 0 ? 1 : 0;
+    info->rank = l.rank;
+  });
+}
+
+hmat_status hmat_leaf_get(const hmat_t h, int64_t i, double *U, double *V) {
+  return guard([&] {
+    if (!h || !U) fail(HMAT_EINVAL, "NULL argument");
+    if (i < 0 || i >= (int64_t)h->leaves.size()) fail(HMAT_EINVAL, "leaf index out of range");
+    const LeafDev &l = h->leaves[i];
+    if (l.rank >= 0 && !V && l.rank > 0) fail(HMAT_EINVAL, "V is NULL for a far leaf");
+    const int64_t nu = l.rank < 0 ? (int64_t)l.m * l.n : (int64_t)l.m * l.rank;
+    const int64_t nv = l.rank < 0 ? 0 : (int64_t)l.n * l.rank;
+    cudaStream_t s = h->stream;
+    if (nu + nv == 0) return;
+    DevBuf tmp(sizeof(double) * (nu + nv), s);
+    const char *base = (const char *)h->d_data.p;
+    ck(launch_convert(h->prec, base + esize(h->prec) * l.off_u, tmp.as<double>(), nu, s), "convert");
+    if (nv) ck(launch_convert(h->prec, base + esize(h->prec) * l.off_v, tmp.as<double>() + nu, nv, s), "convert");
+    ck(cudaMemcpyAsync(U, tmp.p, sizeof(double) * nu, cudaMemcpyDeviceToHost, s), "leaf U");
+    if (nv) ck(cudaMemcpyAsync(V, tmp.as<double>() + nu, sizeof(double) * nv, cudaMemcpyDeviceToHost, s), "leaf V");
+    ck(cudaStreamSynchronize(s), "leaf get");
+  });
+}
+
+hmat_status hmat_to_dense(const hmat_t h, double *out, int64_t ld) {
+  return guard([&] {
+    if (!h || !out) fail(HMAT_EINVAL, "NULL argument");
+    const Tree &t = *h->tree;
+    if (ld < t.n) fail(HMAT_EINVAL, "ld < n");
+    cudaStream_t s = h->stream;
+    DevBuf tmp(sizeof(double) * std::max<int64_t>(h->data_elems, 1), s);
+    ck(launch_convert(h->prec, h->d_data.p, tmp.as<double>(), h->data_elems, s), "convert");
+    std::vector<double> data(h->data_elems);
+    ck(cudaMemcpyAsync(data.data(), tmp.p, sizeof(double) * h->data_elems, cudaMemcpyDeviceToHost, s), "to host");
+    ck(cudaStreamSynchronize(s), "to dense");
+    for (const LeafDev &l : h->leaves) {
+      for (int64_t j = 0; j < l.n; j++) {
+        const int64_t oj = t.perm[l.col + j];
+        for (int64_t i = 0; i < l.m; i++) {
+          const int64_t oi = t.perm[l.row + i];
+          double v;
+          if (l.rank < 0) v = data[l.off_u + i + j * l.m];
+          else {
+            v = 0.0;
+            for (int q = 0; q < l.rank; q++) v += data[l.off_u + i + (int64_t)q * l.m] * data[l.off_v + j + (int64_t)q * l.n];
+          }
+          out[oi + oj * ld] = v;
+        }
+      }
+    }
+  });
+}
+
+hmat_status hmat_permutation(const hmat_t h, int64_t *perm) {
+  return guard([&] {
+    if (!h || !perm) fail(HMAT_EINVAL, "NULL argument");
+    std::memcpy(perm, h->tree->perm.data(), sizeof(int64_t) * h->tree->n);
+  });
+}
+
+hmat_status hmat_stats(const hmat_t h, hmat_stats_t *stats) {
+  return guard([&] {
+    if (!h || !stats) fail(HMAT_EINVAL, "NULL argument");
+    *stats = h->stats;
+  });
+}
+
+hmat_status hmat_sumexpr_counts(const hmat_t A, const hmat_t B, int64_t *n_lowrank, int64_t *n_hpairs) {
+  return guard([&] {
+    if (!A || !B || !n_lowrank || !n_hpairs) fail(HMAT_EINVAL, "NULL argument");
+    if (A->tree != B->tree && !same_points(*A->tree, B->tree->orig.data(), B->tree->n, B->tree->dim))
+      fail(HMAT_EMISMATCH, "A and B are not on one block tree");
+    const Tree &t = *A->tree;
+    std::vector<int32_t> ra(A->leaves.size()), rb(B->leaves.size());
+    for (size_t l = 0; l < ra.size(); l++) { ra[l] = A->leaves[l].rank; rb[l] = B->leaves[l].rank; }
+    Plan plan;
+    build_plan(t, ra, rb, plan);
+    for (size_t l = 0; l + 1 < plan.leaf_term_off.size(); l++) {
+      n_lowrank[l] = plan.leaf_term_off[l + 1] - plan.leaf_term_off[l];
+      n_hpairs[l] = plan.leaf_pair_off[l + 1] - plan.leaf_pair_off[l];
+    }
+  });
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ the product
+
+namespace {
+
+struct Product {
+  const hmat_s *A, *B;
+  const hmat_mult_opts *o;
+  cudaStream_t s;
+  int cprec;              // compute / output precision
+  std::unique_ptr<hmat_s> C;
+
+  void run();
+};
+
+void Product::run() {
+  const Tree &t = *A->tree;
+  const double t_plan0 = now_ms();
+  C = std::make_unique<hmat_s>();
+  C->tree = A->tree;
+  C->stream = s;
+  C->prec = cprec;
+  C->kernel = -1;
+  hmat_stats_t &S = C->stats;
+  const size_t es = esize(cprec);
+  const int p = o->block_width > 0 ? o->block_width : 8;
+  if (p > 32) fail(HMAT_EINVAL, "block_width must be <= 32");
+  int max_rank = o->max_rank > 0 ? o->max_rank : 96;
+  if (max_rank > 96) fail(HMAT_EINVAL, "max_rank must be <= 96");
+  if (max_rank < p) max_rank = p;
+  const int max_rounds = o->max_rounds > 0 ? o->max_rounds : max_rank / p + 1;
+
+  // factors in compute precision
+  DevBuf convA, convB;
+  const void *dataA = A->d_data.p, *dataB = B->d_data.p;
+  if (A->prec != cprec) {
+    convA = DevBuf(sizeof(double) * std::max<int64_t>(A->data_elems, 1), s);
+    ck(launch_convert(A->prec, A->d_data.p, convA.as<double>(), A->data_elems, s), "widen A");
+    dataA = convA.p;
+  }
+  if (B->prec != cprec) {
+    if (B == A) dataB = dataA;
+    else {
+      convB = DevBuf(sizeof(double) * std::max<int64_t>(B->data_elems, 1), s);
+      ck(launch_convert(B->prec, B->d_data.p, convB.as<double>(), B->data_elems, s), "widen B");
+      dataB = convB.p;
+    }
+  }
+
+  // ---- a1: symbolic restriction (Algorithm 3) over the tree
+  std::vector<int32_t> ra(A->leaves.size()), rb(B->leaves.size());
+  for (size_t l = 0; l < ra.size(); l++) { ra[l] = A->leaves[l].rank; rb[l] = B->leaves[l].rank; }
+  Plan plan;
+  build_plan(t, ra, rb, plan);
+  const std::vector<double> storA = block_storage(t, A->leaves), storB = block_storage(t, B->leaves);
+
+  // term storage and jobs (a2)
+  std::vector<TermJob> jobs(plan.terms.size());
+  std::vector<int64_t> term_off(plan.terms.size());
+  int64_t term_elems = 0;
+  double flops_terms = 0;
+  for (size_t i = 0; i < plan.terms.size(); i++) {
+    const PlanTerm &pt = plan.terms[i];
+    const Block &cb = t.bl[pt.block];
+    const int64_t mp = t.cl[cb.tau].size, np = t.cl[cb.sigma].size;
+    TermJob &j = jobs[i];
+    j.type = pt.type;
+    j.a = pt.a;
+    j.b = pt.b;
+    j.rank = pt.rank;
+    j.rows = (pt.type == JOB_FF_L || pt.type == JOB_HF) ? mp : np;
+    j.out = term_elems;
+    term_off[i] = term_elems;
+    term_elems += j.rows * j.rank;
+    if (pt.type == JOB_FF_R || pt.type == JOB_FF_L) {
+      const LeafDev &la = A->leaves[pt.a], &lb = B->leaves[pt.b];
+      flops_terms += 2.0 * la.n * la.rank * lb.rank + 2.0 * j.rows * la.rank * lb.rank;
+    } else if (pt.type == JOB_FH) {
+      flops_terms += 2.0 * storB[pt.b] * pt.rank;
+    } else {
+      flops_terms += 2.0 * storA[pt.a] * pt.rank;
+    }
+  }
+  S.n_terms = (int64_t)plan.terms.size();
+  S.n_lr_refs = (int64_t)plan.leaf_terms.size();
+  S.n_hpairs = (int64_t)plan.leaf_pairs.size();
+  S.flops_terms = flops_terms;
+
+  // ---- targets
+  struct Tgt {
+    int leaf;
+    double cost;
+  };
+  std::vector<Tgt> far, nearv;
+  std::vector<double> elems_b(t.leaf_block.size(), 0.0);
+  for (size_t l = 0; l < t.leaf_block.size(); l++) {
+    const LeafDev &lc = A->leaves[l];
+    double e = 0;
+    for (int64_t q = plan.leaf_term_off[l]; q < plan.leaf_term_off[l + 1]; q++)
+      e += (double)plan.terms[plan.leaf_terms[q]].rank * (lc.m + lc.n);
+    for (int64_t q = plan.leaf_pair_off[l]; q < plan.leaf_pair_off[l + 1]; q++)
+      e += storA[plan.leaf_pairs[q].blkA] + storB[plan.leaf_pairs[q].blkB];
+    elems_b[l] = e;
+    (lc.rank < 0 ? nearv : far).push_back(Tgt{(int)l, e});
+  }
+  std::stable_sort(far.begin(), far.end(), [](const Tgt &a, const Tgt &b) { return a.cost > b.cost; });
+
+  auto make_targets = [&](const std::vector<Tgt> &tv, std::vector<TargetDev> &tg, std::vector<int32_t> &tterms,
+                          std::vector<PairDev> &tpairs) {
+    tg.resize(tv.size());
+    for (size_t i = 0; i < tv.size(); i++) {
+      const int l = tv[i].leaf;
+      const LeafDev &lc = A->leaves[l];
+      TargetDev &d = tg[i];
+      std::memset(&d, 0, sizeof(d));
+      d.row = lc.row;
+      d.col = lc.col;
+      d.m = lc.m;
+      d.n = lc.n;
+      d.leaf = l;
+      d.term_lo = (int32_t)tterms.size();
+      for (int64_t q = plan.leaf_term_off[l]; q < plan.leaf_term_off[l + 1]; q++) tterms.push_back(plan.leaf_terms[q]);
+      d.term_hi = (int32_t)tterms.size();
+      d.pair_lo = (int32_t)tpairs.size();
+      for (int64_t q = plan.leaf_pair_off[l]; q < plan.leaf_pair_off[l + 1]; q++) tpairs.push_back(plan.leaf_pairs[q]);
+      d.pair_hi = (int32_t)tpairs.size();
+    }
+  };
+  std::vector<TargetDev> ftg, ntg;
+  std::vector<int32_t> fterms, nterms;
+  std::vector<PairDev> fpairs, npairs;
+  make_targets(far, ftg, fterms, fpairs);
+  make_targets(nearv, ntg, nterms, npairs);
+  // scratch offsets for far targets
+  int64_t qw_elems = 0, xy_elems = 0, z_elems = 0;
+  for (TargetDev &d : ftg) {
+    const int mn = std::min(d.m, d.n);
+    d.rmax = std::min(max_rank, ((mn + p + p - 1) / p) * p);
+    if (d.rmax < p) d.rmax = p;
+    d.q_off = qw_elems;
+    qw_elems += (int64_t)d.m * d.rmax;
+    d.w_off = qw_elems;
+    qw_elems += (int64_t)d.n * d.rmax;
+    const int64_t mx = std::max(d.m, d.n);
+    d.x_off = xy_elems;
+    d.y_off = xy_elems;  // separate buffers x and y share the same offsets
+    xy_elems += mx * p;
+    int rho_max = 0;
+    for (int q = d.pair_lo; q < d.pair_hi; q++) rho_max = std::max(rho_max, (int)t.cl[t.bl[fpairs[q].blkA].sigma].size);
+    d.z_off = z_elems;
+    z_elems += (int64_t)rho_max * p;
+  }
+  S.ms_plan = now_ms() - t_plan0;
+
+  cudaEvent_t ev[6];
+  for (auto &e : ev) ck(cudaEventCreate(&e), "event");
+  struct EvGuard {
+    cudaEvent_t *e;
+    ~EvGuard() { for (int i = 0; i < 6; i++) cudaEventDestroy(e[i]); }
+  } evg{ev};
+
+  // ---- a2: low-rank products
+  ck(cudaEventRecord(ev[0], s), "event");
+  DevBuf d_termbuf(es * std::max<int64_t>(term_elems, 1), s);
+  ck(cudaMemsetAsync(d_termbuf.p, 0, es * std::max<int64_t>(term_elems, 1), s), "memset terms");
+  DevBuf d_jobs = upload(jobs, s);
+  ck(launch_term_jobs(cprec, d_jobs.as<TermJob>(), (int)jobs.size(), A->d_leaves.as<LeafDev>(),
+                      B->d_leaves.as<LeafDev>(), t.d_blocks, dataA, dataB, d_termbuf.p, s),
+     "low-rank products");
+  std::vector<TermDev> tdev(plan.terms.size());
+  for (size_t i = 0; i < plan.terms.size(); i++) {
+    const PlanTerm &pt = plan.terms[i];
+    const Block &cb = t.bl[pt.block];
+    TermDev &d = tdev[i];
+    d.row0 = t.cl[cb.tau].begin;
+    d.col0 = t.cl[cb.sigma].begin;
+    d.ldL = t.cl[cb.tau].size;
+    d.ldR = t.cl[cb.sigma].size;
+    d.rank = pt.rank;
+    const char *tb = (const char *)d_termbuf.p + es * term_off[i];
+    const char *da = (const char *)dataA, *db = (const char *)dataB;
+    switch (pt.type) {
+      case JOB_FF_R:
+      case JOB_FH:
+        d.L = da + es * A->leaves[pt.a].off_u;
+        d.R = tb;
+        break;
+      case JOB_FF_L:
+      case JOB_HF:
+      default:
+        d.L = tb;
+        d.R = db + es * B->leaves[pt.b].off_v;
+        break;
+    }
+  }
+  DevBuf d_terms = upload(tdev, s);
+  ck(cudaEventRecord(ev[1], s), "event");
+
+  // ---- a3..a7: adaptive randomized truncation of all far targets
+  const int nf = (int)ftg.size();
+  DevBuf d_ftg = upload(ftg, s), d_fterms = upload(fterms, s), d_fpairs = upload(fpairs, s);
+  DevBuf d_qw(sizeof(double) * std::max<int64_t>(qw_elems, 1), s);
+  DevBuf d_x(es * std::max<int64_t>(xy_elems, 1), s), d_y(es * std::max<int64_t>(xy_elems, 1), s);
+  DevBuf d_z(es * std::max<int64_t>(z_elems, 1), s);
+  std::vector<TargetState> st0(nf);
+  for (auto &x : st0) {
+    std::memset(&x, 0, sizeof(x));
+    x.active = 1;
+  }
+  DevBuf d_st = upload(st0, s);
+  DevBuf d_cnt(sizeof(int32_t), s);
+  ApplyArgs aa{};
+  aa.tg = d_ftg.as<TargetDev>();
+  aa.tg_terms = d_fterms.as<int32_t>();
+  aa.terms = d_terms.as<TermDev>();
+  aa.pairs = d_fpairs.as<PairDev>();
+  aa.blocks = t.d_blocks;
+  aa.leafA = A->d_leaves.as<LeafDev>();
+  aa.leafB = B->d_leaves.as<LeafDev>();
+  aa.dataA = dataA;
+  aa.dataB = dataB;
+  aa.state = d_st.as<TargetState>();
+  aa.x_base = d_x.p;
+  aa.y_base = d_y.p;
+  aa.z_base = d_z.p;
+  aa.p = p;
+  aa.ntarget = nf;
+  const double eps = o->eps;
+  const double eps_stop = 0.5 * eps;
+  int rounds = 0;
+  for (int round = 0; round < max_rounds && nf > 0; round++) {
+    rounds++;
+    ck(launch_gaussian(cprec, aa.tg, aa.state, nf, p, o->seed, round, d_x.p, s), "gaussian");
+    ck(launch_apply(cprec, false, aa, s), "apply S");
+    ck(launch_orth(cprec, aa.tg, aa.state, nf, p, eps, d_y.p, d_qw.as<double>(), d_x.p, round, s), "orth");
+    ck(launch_apply(cprec, true, aa, s), "apply S^T");
+    ck(cudaMemsetAsync(d_cnt.p, 0, sizeof(int32_t), s), "memset");
+    ck(launch_absorb_w(cprec, aa.tg, aa.state, nf, p, eps_stop, d_y.p, d_qw.as<double>(), round, max_rounds,
+                       d_cnt.as<int32_t>(), s),
+       "stop test");
+    int32_t act = 0;
+    ck(cudaMemcpyAsync(&act, d_cnt.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s), "count");
+    ck(cudaStreamSynchronize(s), "round");
+    if (act == 0) break;
+  }
+  ck(cudaEventRecord(ev[2], s), "event");
+  ck(launch_final(aa.tg, aa.state, nf, eps, d_qw.as<double>(), s), "final truncation");
+  std::vector<TargetState> st(nf);
+  if (nf) ck(cudaMemcpyAsync(st.data(), d_st.p, sizeof(TargetState) * nf, cudaMemcpyDeviceToHost, s), "states");
+  ck(cudaStreamSynchronize(s), "final");
+  ck(cudaEventRecord(ev[3], s), "event");
+
+  // ---- C: leaves, storage, write far factors, evaluate near leaves (a8, a9)
+  C->leaves = base_leaves(t);
+  int64_t off = 0;
+  int64_t notconv = 0;
+  for (size_t i = 0; i < ftg.size(); i++) {
+    int k = st[i].rank;
+    if (k < -2) { notconv++; k = -(k + 3); }
+    LeafDev &l = C->leaves[ftg[i].leaf];
+    l.rank = k;
+    l.off_u = off;
+    l.off_v = off + (int64_t)l.m * k;
+    off = l.off_v + (int64_t)l.n * k;
+  }
+  for (const TargetDev &d : ntg) {
+    LeafDev &l = C->leaves[d.leaf];
+    l.off_u = off;
+    off += (int64_t)l.m * l.n;
+  }
+  C->data_elems = off;
+  C->d_data = DevBuf(es * std::max<int64_t>(off, 1), s);
+  C->d_leaves = upload(C->leaves, s);
+  ck(launch_write_far(cprec, aa.tg, aa.state, nf, d_qw.as<double>(), C->d_leaves.as<LeafDev>(), C->d_data.p, s),
+     "write far");
+  DevBuf d_ntg = upload(ntg, s), d_nterms = upload(nterms, s), d_npairs = upload(npairs, s);
+  ck(launch_near_eval(cprec, d_ntg.as<TargetDev>(), (int)ntg.size(), d_nterms.as<int32_t>(), d_terms.as<TermDev>(),
+                      d_npairs.as<PairDev>(), t.d_blocks, A->d_leaves.as<LeafDev>(), B->d_leaves.as<LeafDev>(), dataA,
+                      dataB, C->d_leaves.as<LeafDev>(), C->d_data.p, s),
+     "near field");
+  ck(cudaEventRecord(ev[4], s), "event");
+  ck(cudaStreamSynchronize(s), "product");
+
+  float ms = 0;
+  cudaEventElapsedTime(&ms, ev[0], ev[1]);
+  S.ms_terms = ms;
+  cudaEventElapsedTime(&ms, ev[1], ev[2]);
+  S.ms_sample = ms;
+  cudaEventElapsedTime(&ms, ev[2], ev[3]);
+  S.ms_final = ms;
+  cudaEventElapsedTime(&ms, ev[3], ev[4]);
+  S.ms_near = ms;
+  S.rounds = rounds;
+  S.not_converged = notconv;
+  double fa = 0, ba = 0, fn = 0;
+  for (size_t i = 0; i < ftg.size(); i++) {
+    const double e = elems_b[ftg[i].leaf];
+    const int cols = st[i].r;  // columns that went through both passes
+    fa += 2.0 * e * 2.0 * cols;
+    ba += e * 2.0 * ((cols + p - 1) / p) * es;
+  }
+  for (const TargetDev &d : ntg) {
+    double kk = 0;
+    for (int q = d.term_lo; q < d.term_hi; q++) kk += tdev[nterms[q]].rank;
+    double rr = 0;
+    for (int q = d.pair_lo; q < d.pair_hi; q++) rr += t.cl[t.bl[npairs[q].blkA].sigma].size;
+    fn += 2.0 * d.m * d.n * (kk + rr);
+  }
+  S.flops_apply = fa;
+  S.bytes_apply = ba;
+  S.flops_near = fn;
+  fill_structure_stats(C.get());
+}
+
+}  // namespace
+
+extern "C" hmat_status hmat_multiply(const hmat_t A, const hmat_t B, const hmat_mult_opts *opts, void *stream,
+                                     hmat_t *C) {
+  if (C) *C = nullptr;
+  return guard([&] {
+    if (!A || !B || !opts || !C) fail(HMAT_EINVAL, "NULL argument");
+    if (!(opts->eps > 0.0) || !std::isfinite(opts->eps)) fail(HMAT_EINVAL, "eps must be a positive number");
+    if (opts->mode != HMAT_MODE_F64 && opts->mode != HMAT_MODE_MIXED) fail(HMAT_EINVAL, "unknown mode");
+    if (A->tree != B->tree) {
+      const Tree &ta = *A->tree, &tb = *B->tree;
+      if (!same_points(ta, tb.orig.data(), tb.n, tb.dim) || ta.leaf_size != tb.leaf_size || ta.eta != tb.eta)
+        fail(HMAT_EMISMATCH, "A and B are not on one block tree");
+    }
+    if (A->prec != B->prec) fail(HMAT_EINVAL, "A and B must have the same factor precision");
+    Product pr;
+    pr.A = A;
+    pr.B = B;
+    pr.o = opts;
+    pr.s = (cudaStream_t)stream;
+    pr.cprec = opts->mode == HMAT_MODE_F64 ? 64 : A->prec;
+    pr.run();
+    const bool nc = pr.C->stats.not_converged > 0;
+    *C = pr.C.release();
+    if (nc) fail(HMAT_ENOTCONV, "some far blocks hit max_rank or max_rounds");
+  });
+}

@@ -1,0 +1,133 @@
+// hmat_internal.h -- data layout and launch interface shared by the library's sources.
+//
+// Layout in HBM (all device arrays owned by the library):
+//   * an H-matrix keeps ONE factor buffer of element type T (double or float). Leaves are
+//     numbered in depth-first order of the block tree; far leaf l stores U (m x k) at
+//     off_u and V (n x k) at off_v, column-major with leading dimensions m and n; near
+//     leaf l stores the dense block (m x n, column-major, ld m) at off_u.
+//   * a LeafDev table (one entry per leaf) and a BlockDev table (one entry per block of the
+//     tree, with the depth-first leaf range of its subtree) let a kernel walk any inadmissible
+//     block's subtree: the subtree of a block is a contiguous range of leaves.
+//   * the product's plan: TermDev table (low-rank products L R^T created by the restriction,
+//     Algorithm 3), per-target CSR lists of term ids and of H-pairs (block of A, block of B).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace hm {
+
+struct LeafDev {
+  int64_t row, col;     // permuted begin of tau and sigma
+  int32_t m, n, rank;   // rank < 0: dense leaf
+  int32_t level;
+  int64_t off_u, off_v; // element offsets into the factor buffer (dense: off_u)
+};
+
+struct BlockDev {
+  int64_t row, col;     // permuted begin of tau, sigma
+  int32_t m, n;
+  int32_t leaf_lo, leaf_hi;  // depth-first leaf range of the subtree
+};
+
+// A low-rank term L R^T of a sum-expression, on the block tau' x sigma' where it was created.
+// Restricted to tau x sigma (inside tau' x sigma') by index shift: L + (tau.begin - row0),
+// R + (sigma.begin - col0) (Sec. 3.2: restriction of low-rank matrices is an index shift).
+struct TermDev {
+  const void *L, *R;
+  int64_t ldL, ldR;
+  int64_t row0, col0;
+  int32_t rank, pad;
+};
+
+// Work item of the low-rank products (a2).
+enum TermJobType : int32_t {
+  JOB_FF_R = 0,   // far x far, ka <= kb: R_new = V_b (V_a^T U_b)^T   (n' x ka)
+  JOB_FF_L = 1,   // far x far, ka >  kb: L_new = U_a (V_a^T U_b)     (m' x kb)
+  JOB_FH = 2,     // far x inadmissible:  R_new = B|rho' x sigma'^T V_a (n' x ka)
+  JOB_HF = 3      // inadmissible x far:  L_new = A|tau' x rho' U_b   (m' x kb)
+};
+struct TermJob {
+  int32_t type;
+  int32_t a;      // leaf of A (FF, FH) or block of the tree (HF)
+  int32_t b;      // leaf of B (FF, HF) or block of the tree (FH)
+  int32_t rank;   // width of the new factor
+  int64_t out;    // element offset of the new factor in the term buffer
+  int64_t rows;   // rows of the new factor
+};
+
+struct PairDev {
+  int32_t blkA, blkB;   // tau x rho (in A) and rho x sigma (in B), same level as the target
+};
+
+struct TargetDev {
+  int64_t row, col;     // permuted begin of tau, sigma
+  int32_t m, n;
+  int32_t term_lo, term_hi;
+  int32_t pair_lo, pair_hi;
+  int32_t leaf;         // leaf id in the block tree
+  int32_t rmax;         // basis capacity (columns of Q and W)
+  int64_t q_off, w_off; // FP64 basis Q (m x rmax) and W (n x rmax)
+  int64_t y_off, x_off; // per-round sample buffers (m x p) and (n x p), element type T
+  int64_t z_off;        // H-pair intermediate (m x p), element type T
+};
+
+// Per-target state of the adaptive range finder.
+struct TargetState {
+  int32_t r;            // columns in Q so far
+  int32_t active;       // 1 while sampling continues
+  int32_t p_new;        // columns kept in the current round
+  int32_t rank;         // final rank
+  double nrm2;          // ||W||_F^2 over all columns so far (= ||Q Q^T S||_F^2)
+  double est2;          // ||Y||_F^2 / p of the first round (scale for dropping)
+  double tail2;         // discarded energy in the final truncation
+};
+
+struct ApplyArgs {
+  const TargetDev *tg;
+  const int32_t *tg_terms;
+  const TermDev *terms;
+  const PairDev *pairs;
+  const BlockDev *blocks;
+  const LeafDev *leafA, *leafB;
+  const void *dataA, *dataB;
+  TargetState *state;
+  void *y_base;          // per-target In/Out regions (element type T), offsets in TargetDev
+  void *x_base;
+  void *z_base;
+  int p;                 // columns this round
+  int ntarget;
+};
+
+// ---- launch wrappers (hmat_kernels.cu); all return cudaError_t of the launch ----
+cudaError_t launch_kernel_dense(int prec, int kernel, const double *pts, int dim,
+                                const LeafDev *leaves, const int32_t *near_ids, int nnear,
+                                void *data, cudaStream_t s);
+cudaError_t launch_aca(int kernel, const double *pts, int dim, const LeafDev *leaves,
+                       const int32_t *far_ids, int nfar, double eps, int kmax,
+                       double *scratch, const int64_t *scratch_off, int32_t *ranks,
+                       cudaStream_t s);
+cudaError_t launch_aca_compact(int prec, const LeafDev *leaves, const int32_t *far_ids, int nfar,
+                               const double *scratch, const int64_t *scratch_off, int kmax,
+                               void *data, cudaStream_t s);
+cudaError_t launch_term_jobs(int prec, const TermJob *jobs, int njobs, const LeafDev *leafA,
+                             const LeafDev *leafB, const BlockDev *blocks, const void *dataA,
+                             const void *dataB, void *terms, cudaStream_t s);
+cudaError_t launch_near_eval(int prec, const TargetDev *tg, int ntg, const int32_t *tg_terms,
+                             const TermDev *terms, const PairDev *pairs, const BlockDev *blocks,
+                             const LeafDev *leafA, const LeafDev *leafB, const void *dataA,
+                             const void *dataB, const LeafDev *leafC, void *dataC, cudaStream_t s);
+cudaError_t launch_gaussian(int prec, const TargetDev *tg, const TargetState *st, int ntg, int p,
+                            uint64_t seed, int round, void *x_base, cudaStream_t s);
+cudaError_t launch_apply(int prec, bool trans, const ApplyArgs &a, cudaStream_t s);
+cudaError_t launch_orth(int prec, const TargetDev *tg, TargetState *st, int ntg, int p, double eps,
+                        void *y_base, double *qw, void *x_base, int round, cudaStream_t s);
+cudaError_t launch_absorb_w(int prec, const TargetDev *tg, TargetState *st, int ntg, int p,
+                            double eps_stop, void *y_base, double *qw, int round, int max_rounds,
+                            int32_t *active_count, cudaStream_t s);
+cudaError_t launch_final(const TargetDev *tg, TargetState *st, int ntg, double eps, double *qw,
+                         cudaStream_t s);
+cudaError_t launch_write_far(int prec, const TargetDev *tg, const TargetState *st, int ntg,
+                             const double *qw, const LeafDev *leafC, void *dataC, cudaStream_t s);
+cudaError_t launch_convert(int prec, const void *src, double *dst, int64_t count, cudaStream_t s);
+
+}  // namespace hm

@@ -1,0 +1,1068 @@
+// hmat_kernels.cu -- device kernels of the H-matrix product (sm_103a).
+//
+// Kernels, in the order the product runs them (paper references are to Doelz, Harbrecht,
+// Multerer, "On the best approximation of the hierarchical matrix product"):
+//   k_kernel_dense  near leaves of an input matrix, evaluated entry by entry
+//   k_aca           far leaves of an input matrix by adaptive cross approximation (Alg. 6)
+//   k_term_jobs     the low-rank products A|tau' x rho' * B|rho' x sigma' that the restriction
+//                   of Algorithm 3 creates when one factor is far (cost: Lemma 5.1)
+//   k_near_eval     evaluate() of Algorithm 4 for near leaves: S(b) applied to the identity
+//   k_gaussian      Gaussian test matrices Omega (counter-based, splitmix64 + Box-Muller)
+//   k_apply         S(b) Omega or S(b)^T Q for every far target b in one launch: all low-rank
+//                   terms and all H-pairs of b fused in one pass (the formula for S v in
+//                   Sec. 3.3, H-pairs applied by the recursion of Algorithm 2 over leaves)
+//   k_orth          project the new samples against the basis twice and orthonormalise them by
+//                   Gram-Schmidt twice with dropping, all in FP64 (the projection step of Alg. 8)
+//   k_absorb_w      append W_new = S^T Q_new and apply the blocked stop test eq. (truncaca)
+//   k_final         core truncation: eigen-decomposition of W^T W (Jacobi, FP64), eps-rank,
+//                   U = Q V_k, V = W V_k (the small SVD of Algorithm 5 on the sampled core)
+//   k_write_far     copy the truncated factors into the output H-matrix
+//
+// Block size is 256 threads everywhere; every block-level helper must be reached by all
+// threads of the block (they contain __syncthreads()).
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "hmat_internal.h"
+
+namespace hm {
+
+constexpr int NT = 256;     // threads per block
+constexpr int KC = 32;      // rows staged per chunk in the SIMT contractions
+constexpr int PMAX = 32;    // max right-hand-side columns per contraction call
+constexpr int RMAX = 128;   // max rank / leaf size handled by one contraction call
+
+// ---------------------------------------------------------------------------------------
+// small block-level SIMT contractions
+// ---------------------------------------------------------------------------------------
+
+// Out[i + c*ldo] += sum_k M[i + k*ldm] * X[k + c*ldx] for i < mr, c < p, k < kc.
+// X is staged through xs[KC * PMAX]. All threads of the block must call.
+template <typename T>
+__device__ void gemm_nn_acc(T *Out, int64_t ldo, const T *M, int64_t ldm, const T *X, int64_t ldx,
+                            int mr, int kc, int p, T *xs) {
+  constexpr int OPT = 2;
+  const int tid = threadIdx.x;
+  const int p4 = (p + 3) >> 2;
+  const int nout = mr * p4;
+  for (int ob = 0; ob < nout; ob += NT * OPT) {
+    T acc[OPT][4];
+#pragma unroll
+    for (int j = 0; j < OPT; j++)
+#pragma unroll
+      for (int q = 0; q < 4; q++) acc[j][q] = T(0);
+    for (int k0 = 0; k0 < kc; k0 += KC) {
+      const int kk = min(KC, kc - k0);
+      __syncthreads();
+      for (int e = tid; e < kk * p; e += NT) {
+        const int k = e % kk, c = e / kk;
+        xs[k * PMAX + c] = X[(k0 + k) + (int64_t)c * ldx];
+      }
+      __syncthreads();
+#pragma unroll
+      for (int j = 0; j < OPT; j++) {
+        const int o = ob + tid + j * NT;
+        if (o < nout) {
+          const int i = o % mr, cg = o / mr;
+          const T *mp = M + i + (int64_t)k0 * ldm;
+          const T *xp = xs + 4 * cg;
+          for (int k = 0; k < kk; k++) {
+            const T a = mp[(int64_t)k * ldm];
+#pragma unroll
+            for (int q = 0; q < 4; q++) acc[j][q] += a * xp[k * PMAX + q];
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < OPT; j++) {
+      const int o = ob + tid + j * NT;
+      if (o < nout) {
+        const int i = o % mr, cg = o / mr;
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+          const int c = 4 * cg + q;
+          if (c < p) Out[i + (int64_t)c * ldo] += acc[j][q];
+        }
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// Cs[q + c*r] = sum_k M[k + q*ldm] * X[k + c*ldx] for q < r (<= RMAX), c < p (<= PMAX),
+// k < kc. Cs lives in shared memory (r*p entries). ms[KC*RMAX], xs[KC*PMAX] are staging.
+template <typename T>
+__device__ void gemm_tn(T *Cs, const T *M, int64_t ldm, const T *X, int64_t ldx, int kc, int r, int p,
+                        T *ms, T *xs) {
+  constexpr int OPT = (RMAX * PMAX + NT - 1) / NT;
+  const int tid = threadIdx.x;
+  const int nout = r * p;
+  T acc[OPT];
+#pragma unroll
+  for (int j = 0; j < OPT; j++) acc[j] = T(0);
+  for (int k0 = 0; k0 < kc; k0 += KC) {
+    const int kk = min(KC, kc - k0);
+    __syncthreads();
+    for (int e = tid; e < kk * r; e += NT) {
+      const int k = e % kk, q = e / kk;
+      ms[k * RMAX + q] = M[(k0 + k) + (int64_t)q * ldm];
+    }
+    for (int e = tid; e < kk * p; e += NT) {
+      const int k = e % kk, c = e / kk;
+      xs[k * PMAX + c] = X[(k0 + k) + (int64_t)c * ldx];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < OPT; j++) {
+      const int o = tid + j * NT;
+      if (o < nout) {
+        const int q = o % r, c = o / r;
+        T s = T(0);
+        for (int k = 0; k < kk; k++) s += ms[k * RMAX + q] * xs[k * PMAX + c];
+        acc[j] += s;
+      }
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < OPT; j++) {
+    const int o = tid + j * NT;
+    if (o < nout) Cs[o] = acc[j];
+  }
+  __syncthreads();
+}
+
+// Out[q + c*ldo] += Cs[q + c*r]
+template <typename T>
+__device__ void add_small(T *Out, int64_t ldo, const T *Cs, int r, int p) {
+  for (int o = threadIdx.x; o < r * p; o += NT) {
+    const int q = o % r, c = o / r;
+    Out[q + (int64_t)c * ldo] += Cs[o];
+  }
+  __syncthreads();
+}
+
+template <typename T>
+__device__ void zero_mat(T *Out, int64_t ld, int rows, int cols) {
+  for (int64_t o = threadIdx.x; o < (int64_t)rows * cols; o += NT) {
+    const int64_t i = o % rows, c = o / rows;
+    Out[i + c * ld] = T(0);
+  }
+  __syncthreads();
+}
+
+struct Smem {
+  // carve-up of the dynamic shared memory used by the apply-type kernels
+  template <typename T>
+  __device__ static void get(T *base, T *&cs, T *&ms, T *&xs) {
+    cs = base;
+    ms = cs + RMAX * PMAX;
+    xs = ms + KC * RMAX;
+  }
+  template <typename T>
+  static constexpr size_t bytes() { return sizeof(T) * (RMAX * PMAX + KC * RMAX + KC * PMAX); }
+};
+
+// Apply the H-matrix block whose subtree holds leaves [lo, hi) (origin row0, col0) to X:
+//   trans = false:  Out[rows of leaf] += leaf * X[cols of leaf]      (Algorithm 2)
+//   trans = true:   Out[cols of leaf] += leaf^T * X[rows of leaf]
+// X has p <= PMAX columns. Leaves are taken one at a time by the whole block.
+template <typename T>
+__device__ void hblock_apply(const LeafDev *leaves, const T *data, int lo, int hi, int64_t row0, int64_t col0,
+                             bool trans, const T *X, int64_t ldx, int p, T *Out, int64_t ldo, T *cs, T *ms,
+                             T *xs) {
+  for (int l = lo; l < hi; l++) {
+    const LeafDev lf = leaves[l];
+    const int64_t ro = lf.row - row0, co = lf.col - col0;
+    if (lf.rank < 0) {
+      const T *D = data + lf.off_u;
+      if (!trans) {
+        gemm_nn_acc(Out + ro, ldo, D, lf.m, X + co, ldx, lf.m, lf.n, p, xs);
+      } else {
+        gemm_tn(cs, D, lf.m, X + ro, ldx, lf.m, lf.n, p, ms, xs);
+        add_small(Out + co, ldo, cs, lf.n, p);
+      }
+    } else if (lf.rank > 0) {
+      const T *U = data + lf.off_u, *V = data + lf.off_v;
+      if (!trans) {
+        gemm_tn(cs, V, lf.n, X + co, ldx, lf.n, lf.rank, p, ms, xs);
+        gemm_nn_acc(Out + ro, ldo, U, lf.m, cs, lf.rank, lf.m, lf.rank, p, xs);
+      } else {
+        gemm_tn(cs, U, lf.m, X + ro, ldx, lf.m, lf.rank, p, ms, xs);
+        gemm_nn_acc(Out + co, ldo, V, lf.n, cs, lf.rank, lf.n, lf.rank, p, xs);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// input assembly: dense near leaves and ACA far leaves
+// ---------------------------------------------------------------------------------------
+
+__device__ __forceinline__ double kernel_eval(int kernel, const double *x, const double *y, int dim) {
+  if (kernel == 2) {
+    double ip = 0.0;
+    for (int d = 0; d < dim; d++) ip += x[d] * y[d];
+    return (1.0 + ip) * (1.0 + ip);
+  }
+  double r2 = 0.0;
+  for (int d = 0; d < dim; d++) {
+    const double e = x[d] - y[d];
+    r2 += e * e;
+  }
+  if (kernel == 0) return exp(-sqrt(r2));
+  return 1.0 / (1.0 + r2);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NT) k_kernel_dense(int kernel, const double *pts, int dim,
+                                                     const LeafDev *leaves, const int32_t *ids, T *data) {
+  const LeafDev lf = leaves[ids[blockIdx.x]];
+  T *D = data + lf.off_u;
+  for (int64_t o = threadIdx.x; o < (int64_t)lf.m * lf.n; o += NT) {
+    const int64_t i = o % lf.m, j = o / lf.m;
+    D[o] = T(kernel_eval(kernel, pts + (lf.row + i) * dim, pts + (lf.col + j) * dim, dim));
+  }
+}
+
+// block-wide reductions (NT threads)
+__device__ double block_sum(double v, double *red) {
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    v = lane < NT / 32 ? red[lane] : 0.0;
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    if (lane == 0) red[0] = v;
+  }
+  __syncthreads();
+  const double r = red[0];
+  __syncthreads();
+  return r;
+}
+
+// argmax of |v| with the smallest index on ties; returns index (or -1 if every v < 0 marker)
+__device__ int64_t block_argmax(double v, int64_t idx, double *redv, int64_t *redi) {
+  for (int off = 16; off > 0; off >>= 1) {
+    const double ov = __shfl_down_sync(0xffffffffu, v, off);
+    const int64_t oi = __shfl_down_sync(0xffffffffu, idx, off);
+    if (ov > v || (ov == v && oi >= 0 && (idx < 0 || oi < idx))) { v = ov; idx = oi; }
+  }
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) { redv[w] = v; redi[w] = idx; }
+  __syncthreads();
+  if (w == 0) {
+    v = lane < NT / 32 ? redv[lane] : -1.0;
+    idx = lane < NT / 32 ? redi[lane] : -1;
+    for (int off = 16; off > 0; off >>= 1) {
+      const double ov = __shfl_down_sync(0xffffffffu, v, off);
+      const int64_t oi = __shfl_down_sync(0xffffffffu, idx, off);
+      if (ov > v || (ov == v && oi >= 0 && (idx < 0 || oi < idx))) { v = ov; idx = oi; }
+    }
+    if (lane == 0) { redv[0] = v; redi[0] = idx; }
+  }
+  __syncthreads();
+  const int64_t r = redi[0];
+  __syncthreads();
+  return r;
+}
+
+// Algorithm 6 with partial pivoting, one block per far leaf, FP64. Same reading as the
+// oracle: first pivot row = first row; column pivot = argmax |u_hat_r| (first on ties);
+// next pivot row = argmax |l_r| over unused rows; all-zero residual rows are skipped; stop
+// when ||l_{k+1}|| ||u_{k+1}|| <= eps ||L_k U_k||_F (eq. (truncaca)), keeping that term.
+// L (m x kmax) and R (n x kmax) live in scratch; `used` flags live after them.
+__global__ void __launch_bounds__(NT) k_aca(int kernel, const double *pts, int dim, const LeafDev *leaves,
+                                            const int32_t *ids, double eps, int kmax, double *scratch,
+                                            const int64_t *soff, int32_t *ranks) {
+  __shared__ double redv[NT / 32];
+  __shared__ int64_t redi[NT / 32];
+  __shared__ double red[NT / 32];
+  const int f = blockIdx.x;
+  const LeafDev lf = leaves[ids[f]];
+  const int64_t m = lf.m, n = lf.n;
+  double *L = scratch + soff[f];
+  double *R = L + m * kmax;
+  double *usedf = R + n * kmax;  // m flags stored as doubles (0 / 1)
+  const int cap = (int)min((int64_t)kmax, min(m, n));
+  for (int64_t i = threadIdx.x; i < m; i += NT) usedf[i] = 0.0;
+  __syncthreads();
+  double norm2 = 0.0;
+  int k = 0;
+  int64_t ipiv = 0;
+  while (k < cap) {
+    // pivot row with a nonzero residual row
+    int64_t jpiv = -1;
+    while (true) {
+      if (ipiv < 0 || usedf[ipiv] != 0.0) {
+        int64_t cand = m;
+        for (int64_t i = threadIdx.x; i < m; i += NT)
+          if (usedf[i] == 0.0) { cand = i; break; }
+        // min over threads
+        double cv = -(double)cand;
+        int64_t best = block_argmax(cv, cand < m ? cand : -1, redv, redi);
+        ipiv = best;
+        if (ipiv < 0) break;
+      }
+      const double *x = pts + (lf.row + ipiv) * dim;
+      double bv = -1.0;
+      int64_t bi = -1;
+      for (int64_t j = threadIdx.x; j < n; j += NT) {
+        double v = kernel_eval(kernel, x, pts + (lf.col + j) * dim, dim);
+        for (int q = 0; q < k; q++) v -= L[q * m + ipiv] * R[q * n + j];
+        R[k * n + j] = v;
+        const double a = fabs(v);
+        if (a > bv) { bv = a; bi = j; }
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) usedf[ipiv] = 1.0;
+      jpiv = block_argmax(bv, bi, redv, redi);
+      const double best = jpiv >= 0 ? fabs(R[k * n + jpiv]) : 0.0;
+      if (best > 0.0) break;
+      ipiv = -1;
+      jpiv = -1;
+    }
+    if (ipiv < 0 || jpiv < 0) break;
+    const double piv = R[k * n + jpiv];
+    __syncthreads();
+    for (int64_t j = threadIdx.x; j < n; j += NT) R[k * n + j] = R[k * n + j] / piv;
+    __syncthreads();
+    const double *y = pts + (lf.col + jpiv) * dim;
+    for (int64_t i = threadIdx.x; i < m; i += NT) {
+      double v = kernel_eval(kernel, pts + (lf.row + i) * dim, y, dim);
+      for (int q = 0; q < k; q++) v -= R[q * n + jpiv] * L[q * m + i];
+      L[k * m + i] = v;
+    }
+    __syncthreads();
+    double pl = 0.0, pu = 0.0;
+    for (int64_t i = threadIdx.x; i < m; i += NT) pl += L[k * m + i] * L[k * m + i];
+    for (int64_t j = threadIdx.x; j < n; j += NT) pu += R[k * n + j] * R[k * n + j];
+    const double nl = block_sum(pl, red), nu = block_sum(pu, red);
+    double cross = 0.0;
+    for (int q = 0; q < k; q++) {
+      double a = 0.0, b = 0.0;
+      for (int64_t i = threadIdx.x; i < m; i += NT) a += L[q * m + i] * L[k * m + i];
+      for (int64_t j = threadIdx.x; j < n; j += NT) b += R[q * n + j] * R[k * n + j];
+      a = block_sum(a, red);
+      b = block_sum(b, red);
+      cross += a * b;
+    }
+    const double prev = norm2;
+    norm2 = prev + 2.0 * cross + nl * nu;
+    k++;
+    if (sqrt(nl) * sqrt(nu) <= eps * sqrt(prev)) break;
+    double bv = -1.0;
+    int64_t bi = -1;
+    for (int64_t i = threadIdx.x; i < m; i += NT)
+      if (usedf[i] == 0.0) {
+        const double a = fabs(L[(k - 1) * m + i]);
+        if (a > bv) { bv = a; bi = i; }
+      }
+    ipiv = block_argmax(bv, bi, redv, redi);
+    if (ipiv < 0) break;
+  }
+  if (threadIdx.x == 0) ranks[f] = k;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NT) k_aca_compact(const LeafDev *leaves, const int32_t *ids,
+                                                    const double *scratch, const int64_t *soff, int kmax,
+                                                    T *data) {
+  const LeafDev lf = leaves[ids[blockIdx.x]];
+  const double *L = scratch + soff[blockIdx.x];
+  const double *R = L + (int64_t)lf.m * kmax;
+  for (int64_t o = threadIdx.x; o < (int64_t)lf.m * lf.rank; o += NT) data[lf.off_u + o] = T(L[o]);
+  for (int64_t o = threadIdx.x; o < (int64_t)lf.n * lf.rank; o += NT) data[lf.off_v + o] = T(R[o]);
+}
+
+// ---------------------------------------------------------------------------------------
+// a2: low-rank products created by the restriction (Algorithm 3)
+// ---------------------------------------------------------------------------------------
+
+template <typename T>
+__global__ void __launch_bounds__(NT) k_term_jobs(const TermJob *jobs, const LeafDev *leafA, const LeafDev *leafB,
+                                                  const BlockDev *blocks, const T *dataA, const T *dataB,
+                                                  T *terms) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *cs, *ms, *xs;
+  Smem::get((T *)smem_raw, cs, ms, xs);
+  const TermJob jb = jobs[blockIdx.x];
+  T *out = terms + jb.out;
+  if (jb.type == JOB_FF_R || jb.type == JOB_FF_L) {
+    const LeafDev a = leafA[jb.a], b = leafB[jb.b];
+    const T *Ua = dataA + a.off_u, *Va = dataA + a.off_v;
+    const T *Ub = dataB + b.off_u, *Vb = dataB + b.off_v;
+    const int rho = a.n;  // = b.m
+    if (jb.type == JOB_FF_R) {
+      // R_new (n' x ka) = V_b M^T, M = V_a^T U_b; chunk over columns q of M^T: U_b^T V_a[:, q]
+      for (int c0 = 0; c0 < a.rank; c0 += PMAX) {
+        const int pc = min(PMAX, a.rank - c0);
+        gemm_tn(cs, Ub, rho, Va + (int64_t)c0 * rho, rho, rho, b.rank, pc, ms, xs);  // (kb x pc)
+        gemm_nn_acc(out + (int64_t)c0 * b.n, b.n, Vb, b.n, cs, b.rank, b.n, b.rank, pc, xs);
+      }
+    } else {
+      // L_new (m' x kb) = U_a M, M = V_a^T U_b (ka x kb)
+      for (int c0 = 0; c0 < b.rank; c0 += PMAX) {
+        const int pc = min(PMAX, b.rank - c0);
+        gemm_tn(cs, Va, rho, Ub + (int64_t)c0 * rho, rho, rho, a.rank, pc, ms, xs);  // (ka x pc)
+        gemm_nn_acc(out + (int64_t)c0 * a.m, a.m, Ua, a.m, cs, a.rank, a.m, a.rank, pc, xs);
+      }
+    }
+  } else if (jb.type == JOB_FH) {
+    // R_new (n' x ka) = B|rho' x sigma'^T V_a
+    const LeafDev a = leafA[jb.a];
+    const BlockDev bb = blocks[jb.b];
+    const T *Va = dataA + a.off_v;
+    for (int c0 = 0; c0 < a.rank; c0 += PMAX) {
+      const int pc = min(PMAX, a.rank - c0);
+      hblock_apply(leafB, dataB, bb.leaf_lo, bb.leaf_hi, bb.row, bb.col, true, Va + (int64_t)c0 * a.n, a.n, pc,
+                   out + (int64_t)c0 * bb.n, bb.n, cs, ms, xs);
+    }
+  } else {
+    // L_new (m' x kb) = A|tau' x rho' U_b
+    const LeafDev b = leafB[jb.b];
+    const BlockDev ba = blocks[jb.a];
+    const T *Ub = dataB + b.off_u;
+    for (int c0 = 0; c0 < b.rank; c0 += PMAX) {
+      const int pc = min(PMAX, b.rank - c0);
+      hblock_apply(leafA, dataA, ba.leaf_lo, ba.leaf_hi, ba.row, ba.col, false, Ub + (int64_t)c0 * b.m, b.m, pc,
+                   out + (int64_t)c0 * ba.m, ba.m, cs, ms, xs);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// a8: near leaves, C|b = S(b) applied to the identity (Algorithm 4, evaluate())
+// ---------------------------------------------------------------------------------------
+
+// Accumulate C (m x n, column-major in shared memory, m, n <= 64 per tile) += L R^T where L is
+// m x K and R is n x K; L(i,q) = Lp[i*sl_i + q*sl_q], R(j,q) = Rp[j*sr_j + q*sr_q].
+template <typename T>
+__device__ void acc_outer(T (&acc)[4][4], const T *Lp, int64_t sl_i, int64_t sl_q, const T *Rp, int64_t sr_j,
+                          int64_t sr_q, int m, int n, int K, T *ls, T *rs) {
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;  // 16 x 16 threads, 4 x 4 outputs each
+  for (int q0 = 0; q0 < K; q0 += KC) {
+    const int kk = min(KC, K - q0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < kk * 64; e += NT) {
+      const int i = e & 63, q = e >> 6;
+      ls[q * 64 + i] = i < m ? Lp[i * sl_i + (int64_t)(q0 + q) * sl_q] : T(0);
+      rs[q * 64 + i] = i < n ? Rp[i * sr_j + (int64_t)(q0 + q) * sr_q] : T(0);
+    }
+    __syncthreads();
+    for (int q = 0; q < kk; q++) {
+      T a[4], b[4];
+#pragma unroll
+      for (int u = 0; u < 4; u++) { a[u] = ls[q * 64 + tx + 16 * u]; b[u] = rs[q * 64 + ty + 16 * u]; }
+#pragma unroll
+      for (int u = 0; u < 4; u++)
+#pragma unroll
+        for (int v = 0; v < 4; v++) acc[u][v] += a[u] * b[v];
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NT) k_near_eval(const TargetDev *tg, const int32_t *tg_terms, const TermDev *terms,
+                                                  const PairDev *pairs, const BlockDev *blocks, const LeafDev *leafA,
+                                                  const LeafDev *leafB, const T *dataA, const T *dataB,
+                                                  const LeafDev *leafC, T *dataC) {
+  __shared__ T ls[KC * 64], rs[KC * 64];
+  const TargetDev t = tg[blockIdx.x];
+  const LeafDev lc = leafC[t.leaf];
+  T *C = dataC + lc.off_u;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  for (int i0 = 0; i0 < t.m; i0 += 64)
+    for (int j0 = 0; j0 < t.n; j0 += 64) {
+      const int mt = min(64, t.m - i0), nt = min(64, t.n - j0);
+      T acc[4][4];
+#pragma unroll
+      for (int u = 0; u < 4; u++)
+#pragma unroll
+        for (int v = 0; v < 4; v++) acc[u][v] = T(0);
+      for (int ti = t.term_lo; ti < t.term_hi; ti++) {
+        const TermDev tm = terms[tg_terms[ti]];
+        const T *L = (const T *)tm.L + (t.row - tm.row0) + i0;
+        const T *R = (const T *)tm.R + (t.col - tm.col0) + j0;
+        acc_outer(acc, L, 1, tm.ldL, R, 1, tm.ldR, mt, nt, tm.rank, ls, rs);
+      }
+      for (int pi = t.pair_lo; pi < t.pair_hi; pi++) {
+        const PairDev pr = pairs[pi];
+        const BlockDev ba = blocks[pr.blkA], bb = blocks[pr.blkB];
+        // near x near at the leaf level: both blocks are dense leaves
+        const LeafDev la = leafA[ba.leaf_lo], lb = leafB[bb.leaf_lo];
+        const T *DA = dataA + la.off_u + i0;                  // m x rho, ld m
+        const T *DB = dataB + lb.off_u + (int64_t)j0 * lb.m;  // rho x n, ld rho; R(j, q) = DB[q + j*rho]
+        acc_outer(acc, DA, 1, la.m, DB, lb.m, 1, mt, nt, la.n, ls, rs);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; u++)
+#pragma unroll
+        for (int v = 0; v < 4; v++) {
+          const int i = tx + 16 * u, j = ty + 16 * v;
+          if (i < mt && j < nt) C[(i0 + i) + (int64_t)(j0 + j) * t.m] = acc[u][v];
+        }
+      __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// a3 / a6: sum-expression applications for all far targets
+// ---------------------------------------------------------------------------------------
+
+template <typename T, bool TRANS>
+__global__ void __launch_bounds__(NT) k_apply(ApplyArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *cs, *ms, *xs;
+  Smem::get((T *)smem_raw, cs, ms, xs);
+  const int b = blockIdx.x;
+  if (a.state[b].active == 0) return;  // uniform over the block
+  const TargetDev t = a.tg[b];
+  const int p = a.p;
+  const T *X = (const T *)a.x_base + t.x_off;
+  T *Out = (T *)a.y_base + t.y_off;
+  T *Z = (T *)a.z_base + t.z_off;
+  const int64_t ldx = TRANS ? t.m : t.n;
+  const int64_t ldo = TRANS ? t.n : t.m;
+  zero_mat(Out, ldo, (int)ldo, p);
+  // low-rank terms: Out += L (R^T X)   or   Out += R (L^T X)
+  for (int ti = t.term_lo; ti < t.term_hi; ti++) {
+    const TermDev tm = a.terms[a.tg_terms[ti]];
+    const T *L = (const T *)tm.L + (t.row - tm.row0);
+    const T *R = (const T *)tm.R + (t.col - tm.col0);
+    if (!TRANS) {
+      gemm_tn(cs, R, tm.ldR, X, ldx, t.n, tm.rank, p, ms, xs);
+      gemm_nn_acc(Out, ldo, L, tm.ldL, cs, tm.rank, t.m, tm.rank, p, xs);
+    } else {
+      gemm_tn(cs, L, tm.ldL, X, ldx, t.m, tm.rank, p, ms, xs);
+      gemm_nn_acc(Out, ldo, R, tm.ldR, cs, tm.rank, t.n, tm.rank, p, xs);
+    }
+  }
+  // H-pairs: Out += A|tau x rho (B|rho x sigma X)   or   Out += B^T (A^T X)
+  for (int pi = t.pair_lo; pi < t.pair_hi; pi++) {
+    const PairDev pr = a.pairs[pi];
+    const BlockDev ba = a.blocks[pr.blkA], bb = a.blocks[pr.blkB];
+    const int rho = ba.n;
+    zero_mat(Z, rho, rho, p);
+    if (!TRANS) {
+      hblock_apply(a.leafB, (const T *)a.dataB, bb.leaf_lo, bb.leaf_hi, bb.row, bb.col, false, X, ldx, p, Z, rho,
+                   cs, ms, xs);
+      hblock_apply(a.leafA, (const T *)a.dataA, ba.leaf_lo, ba.leaf_hi, ba.row, ba.col, false, Z, rho, p, Out, ldo,
+                   cs, ms, xs);
+    } else {
+      hblock_apply(a.leafA, (const T *)a.dataA, ba.leaf_lo, ba.leaf_hi, ba.row, ba.col, true, X, ldx, p, Z, rho,
+                   cs, ms, xs);
+      hblock_apply(a.leafB, (const T *)a.dataB, bb.leaf_lo, bb.leaf_hi, bb.row, bb.col, true, Z, rho, p, Out, ldo,
+                   cs, ms, xs);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Gaussian test matrices
+// ---------------------------------------------------------------------------------------
+
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// Omega(i, c) for target leaf L in round rd: two splitmix64 draws of the counter
+// ((L * 64 + rd) * 64 + c) * 2^24 + i, then Box-Muller.
+template <typename T>
+__global__ void __launch_bounds__(NT) k_gaussian(const TargetDev *tg, const TargetState *st, int p, uint64_t seed,
+                                                 int round, T *x_base) {
+  const int b = blockIdx.x;
+  if (st[b].active == 0) return;
+  const TargetDev t = tg[b];
+  T *X = x_base + t.x_off;
+  for (int64_t o = threadIdx.x; o < (int64_t)t.n * p; o += NT) {
+    const int64_t i = o % t.n, c = o / t.n;
+    const uint64_t ctr = ((((uint64_t)t.leaf * 64u + (uint64_t)round) * 64u + (uint64_t)c) << 24) + (uint64_t)i;
+    const uint64_t z1 = mix64(seed + (2 * ctr + 1) * 0x9E3779B97F4A7C15ull);
+    const uint64_t z2 = mix64(seed + (2 * ctr + 2) * 0x9E3779B97F4A7C15ull);
+    const double u1 = ((z1 >> 11) + 1) * 0x1.0p-53;  // (0, 1]
+    const double u2 = (z2 >> 11) * 0x1.0p-53;
+    X[o] = T(sqrt(-2.0 * log(u1)) * cospi(2.0 * u2));
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// a4: orthogonalisation of the new samples (FP64)
+// ---------------------------------------------------------------------------------------
+
+// Q buffer of target b: qw + q_off, m x rmax FP64; the new columns are built in place at
+// columns r .. r+p-1. Also writes Q_new in T precision into x_base (input of the S^T pass).
+template <typename T>
+__global__ void __launch_bounds__(NT) k_orth(const TargetDev *tg, TargetState *st, int p, double eps,
+                                             const T *y_base, double *qw, T *x_base, int round) {
+  __shared__ double G[PMAX];
+  constexpr int QCH = 64;  // basis columns projected per chunk
+  __shared__ double Cm[QCH * PMAX];
+  __shared__ double red[NT / 32];
+  const int b = blockIdx.x;
+  if (st[b].active == 0) return;
+  const TargetDev t = tg[b];
+  const int64_t m = t.m;
+  const int r = st[b].r;
+  double *Q = qw + t.q_off;
+  double *Y = Q + (int64_t)r * m;  // m x p workspace inside Q
+  const T *Ys = y_base + t.y_off;
+  double part = 0.0;
+  for (int64_t o = threadIdx.x; o < m * p; o += NT) {
+    const double v = (double)Ys[o];
+    Y[o] = v;
+    part += v * v;
+  }
+  const double ny2 = block_sum(part, red);
+  if (round == 0 && threadIdx.x == 0) st[b].est2 = ny2 / p;
+  __syncthreads();
+  const double est2 = st[b].est2;
+  // project against the basis, twice: Y -= Q (Q^T Y)
+  for (int pass = 0; pass < 2 && r > 0; pass++) {
+    for (int c0 = 0; c0 < r; c0 += QCH) {
+      const int rc = min(QCH, r - c0);
+      // Cm (rc x p) = Q[:, c0:c0+rc]^T Y, one warp per output, lanes over rows
+      const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+      for (int o = w; o < rc * p; o += NT / 32) {
+        const int q = o % rc, c = o / rc;
+        const double *qc = Q + (int64_t)(c0 + q) * m, *yc = Y + (int64_t)c * m;
+        double s = 0.0;
+        for (int64_t i = lane; i < m; i += 32) s += qc[i] * yc[i];
+        for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+        if (lane == 0) Cm[o] = s;
+      }
+      __syncthreads();
+      for (int64_t o = threadIdx.x; o < m * p; o += NT) {
+        const int64_t i = o % m, c = o / m;
+        double s = 0.0;
+        for (int q = 0; q < rc; q++) s += Q[(int64_t)(c0 + q) * m + i] * Cm[q + c * rc];
+        Y[o] -= s;
+      }
+      __syncthreads();
+    }
+  }
+  // Orthonormalise the projected block column by column by classical Gram-Schmidt applied
+  // twice against the columns already accepted in this round (stable while a column keeps more
+  // than ~u of its norm; no Gram squaring). A column whose remaining norm is at most
+  // drop = 0.1 * eps * sqrt(est2) carries negligible energy for the eps target and is dropped;
+  // the block's kept columns are compacted to the front.
+  const double drop2 = (0.1 * eps) * (0.1 * eps) * est2;
+  int kept = 0;
+  for (int j = 0; j < p; j++) {
+    double *y = Y + (int64_t)j * m;
+    for (int pass = 0; pass < 2 && kept > 0; pass++) {
+      const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+      for (int l = w; l < kept; l += NT / 32) {
+        const double *ql = Y + (int64_t)l * m;
+        double s = 0.0;
+        for (int64_t i = lane; i < m; i += 32) s += ql[i] * y[i];
+        for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+        if (lane == 0) G[l] = s;
+      }
+      __syncthreads();
+      for (int64_t i = threadIdx.x; i < m; i += NT) {
+        double s = 0.0;
+        for (int l = 0; l < kept; l++) s += Y[i + (int64_t)l * m] * G[l];
+        y[i] -= s;
+      }
+      __syncthreads();
+    }
+    double part2 = 0.0;
+    for (int64_t i = threadIdx.x; i < m; i += NT) part2 += y[i] * y[i];
+    const double nrm2 = block_sum(part2, red);
+    if (nrm2 > drop2) {
+      const double inv = 1.0 / sqrt(nrm2);
+      double *dst = Y + (int64_t)kept * m;
+      for (int64_t i = threadIdx.x; i < m; i += NT) dst[i] = y[i] * inv;
+      kept++;
+    }
+    __syncthreads();
+  }
+  for (int64_t o = threadIdx.x; o < m * (p - kept); o += NT) Y[(int64_t)kept * m + o] = 0.0;
+  __syncthreads();
+  // Q_new in T precision for the transpose pass (zero padded to p columns)
+  T *Xo = x_base + t.x_off;
+  for (int64_t o = threadIdx.x; o < m * p; o += NT) {
+    const int64_t c = o / m;
+    Xo[o] = c < kept ? T(Y[o]) : T(0);
+  }
+  if (threadIdx.x == 0) {
+    st[b].p_new = kept;
+    if (kept == 0) st[b].active = 0;
+  }
+}
+
+// a5 + append: W_new = S^T Q_new arrives in y_base (n x p, T). Copy into W (FP64) at columns
+// r .. r+p_new-1, update ||W||_F^2 and apply the blocked stop test eq. (truncaca):
+// stop when ||W_new||_F <= eps_stop * ||W_old||_F.
+template <typename T>
+__global__ void __launch_bounds__(NT) k_absorb_w(const TargetDev *tg, TargetState *st, int p, double eps_stop,
+                                                 const T *y_base, double *qw, int round, int max_rounds,
+                                                 int32_t *active_count) {
+  __shared__ double red[NT / 32];
+  const int b = blockIdx.x;
+  const int was_active = st[b].active;
+  const int pn = st[b].p_new;
+  if (was_active == 0 || pn == 0) return;
+  const TargetDev t = tg[b];
+  const int r = st[b].r;
+  double *W = qw + t.w_off + (int64_t)r * t.n;
+  const T *Ws = y_base + t.y_off;
+  double part = 0.0;
+  for (int64_t o = threadIdx.x; o < (int64_t)t.n * pn; o += NT) {
+    const double v = (double)Ws[o];
+    W[o] = v;
+    part += v * v;
+  }
+  const double nw2 = block_sum(part, red);
+  if (threadIdx.x == 0) {
+    const double old = st[b].nrm2;
+    st[b].nrm2 = old + nw2;
+    const int rn = r + pn;
+    st[b].r = rn;
+    int act = 1;
+    if (nw2 <= eps_stop * eps_stop * old) act = 0;
+    if (rn >= min(t.m, t.n)) act = 0;                       // range exhausted: exact
+    if (rn + p > t.rmax || round + 1 >= max_rounds) {
+      if (act) st[b].rank = -2;                              // marks "hit a cap"
+      act = 0;
+    }
+    st[b].active = act;
+    if (act) atomicAdd(active_count, 1);
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// a7: core truncation (FP64)
+// ---------------------------------------------------------------------------------------
+
+constexpr int JMAX = 96;  // max basis size handled by the Jacobi core solver (even)
+
+// Eigen-decomposition of G = W^T W (r x r) by cyclic Jacobi with a round-robin ordering
+// (r/2 disjoint rotations per step, all applied at once), then the eps-rank: the smallest k
+// with sum_{i >= k} lambda_i <= eps^2 sum_i lambda_i; finally Q <- Q V_k and W <- W V_k in place.
+__global__ void __launch_bounds__(NT) k_final(const TargetDev *tg, TargetState *st, double eps, double *qw) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double *G = (double *)smem_raw;          // JMAX x JMAX
+  double *V = G + JMAX * JMAX;             // JMAX x JMAX
+  double *cs = V + JMAX * JMAX;            // JMAX/2 cos, JMAX/2 sin
+  int *pr = (int *)(cs + JMAX);            // JMAX pairing
+  int *order = pr + JMAX;                  // JMAX
+  __shared__ int rank_s, changed_s;
+  const int b = blockIdx.x;
+  const TargetDev t = tg[b];
+  const int r = st[b].r;
+  const int64_t m = t.m, n = t.n;
+  double *Q = qw + t.q_off, *W = qw + t.w_off;
+  if (r == 0) {
+    if (threadIdx.x == 0) { st[b].rank = 0; st[b].tail2 = 0.0; }
+    return;
+  }
+  const int rr = r + (r & 1);  // padded to even
+  // G = W^T W
+  {
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int o = w; o < rr * rr; o += NT / 32) {
+      const int i = o % rr, j = o / rr;
+      if (i > j) continue;
+      double s = 0.0;
+      if (i < r && j < r) {
+        const double *wi = W + (int64_t)i * n, *wj = W + (int64_t)j * n;
+        for (int64_t k = lane; k < n; k += 32) s += wi[k] * wj[k];
+        for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+      }
+      if (lane == 0) { G[i + j * JMAX] = s; G[j + i * JMAX] = s; }
+    }
+  }
+  for (int o = threadIdx.x; o < rr * rr; o += NT) {
+    const int i = o % rr, j = o / rr;
+    V[i + j * JMAX] = (i == j) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  const int npair = rr / 2;
+  for (int sweep = 0; sweep < 40; sweep++) {
+    if (threadIdx.x == 0) changed_s = 0;
+    __syncthreads();
+    for (int step = 0; step < rr - 1; step++) {
+      // round-robin pairing: position 0 fixed, others rotate
+      for (int k = threadIdx.x; k < npair; k += NT) {
+        int a = (k == 0) ? 0 : 1 + ((k - 1 + step) % (rr - 1));
+        int c = 1 + ((rr - 2 - k + step) % (rr - 1));
+        if (a > c) { const int tmp = a; a = c; c = tmp; }
+        pr[2 * k] = a;
+        pr[2 * k + 1] = c;
+        const double app = G[a + a * JMAX], aqq = G[c + c * JMAX], apq = G[a + c * JMAX];
+        double co = 1.0, si = 0.0;
+        if (apq != 0.0 && fabs(apq) > 1e-15 * sqrt(fabs(app * aqq)) && fabs(apq) > 1e-300) {
+          const double zeta = (aqq - app) / (2.0 * apq);
+          const double tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+          co = 1.0 / sqrt(1.0 + tt * tt);
+          si = co * tt;
+          changed_s = 1;
+        }
+        cs[k] = co;
+        cs[JMAX / 2 + k] = si;
+      }
+      __syncthreads();
+      // columns: G <- G J   (for each pair (a, c): col_a' = co col_a - si col_c, col_c' = si col_a + co col_c)
+      for (int o = threadIdx.x; o < npair * rr; o += NT) {
+        const int k = o / rr, i = o % rr;
+        const int a = pr[2 * k], c = pr[2 * k + 1];
+        const double co = cs[k], si = cs[JMAX / 2 + k];
+        const double ga = G[i + a * JMAX], gc = G[i + c * JMAX];
+        G[i + a * JMAX] = co * ga - si * gc;
+        G[i + c * JMAX] = si * ga + co * gc;
+        const double va = V[i + a * JMAX], vc = V[i + c * JMAX];
+        V[i + a * JMAX] = co * va - si * vc;
+        V[i + c * JMAX] = si * va + co * vc;
+      }
+      __syncthreads();
+      // rows: G <- J^T G
+      for (int o = threadIdx.x; o < npair * rr; o += NT) {
+        const int k = o / rr, j = o % rr;
+        const int a = pr[2 * k], c = pr[2 * k + 1];
+        const double co = cs[k], si = cs[JMAX / 2 + k];
+        const double ga = G[a + j * JMAX], gc = G[c + j * JMAX];
+        G[a + j * JMAX] = co * ga - si * gc;
+        G[c + j * JMAX] = si * ga + co * gc;
+      }
+      __syncthreads();
+    }
+    const int ch = changed_s;
+    __syncthreads();
+    if (!ch) break;
+  }
+  // order eigenvalues descending, eps-rank
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < rr; i++) order[i] = i;
+    for (int i = 1; i < rr; i++) {
+      const int x = order[i];
+      const double lx = G[x + x * JMAX];
+      int j = i - 1;
+      while (j >= 0 && G[order[j] + order[j] * JMAX] < lx) { order[j + 1] = order[j]; j--; }
+      order[j + 1] = x;
+    }
+    double tot = 0.0;
+    for (int i = 0; i < rr; i++) tot += fmax(G[i + i * JMAX], 0.0);
+    double tail = 0.0;
+    int k = rr;
+    for (int i = rr - 1; i >= 0; i--) {
+      const double nt = tail + fmax(G[order[i] + order[i] * JMAX], 0.0);
+      if (nt <= eps * eps * tot) { tail = nt; k = i; }
+      else break;
+    }
+    if (k > r) k = r;
+    rank_s = k;
+    st[b].tail2 = tail;
+  }
+  __syncthreads();
+  const int k = rank_s;
+  // in-place Q <- Q V(:, order[0:k]), W <- W V(:, order[0:k]); rows are independent
+  double *Vk = G;  // reuse G storage: r x k, column-major ld JMAX
+  for (int o = threadIdx.x; o < r * k; o += NT) {
+    const int i = o % r, j = o / r;
+    Vk[i + j * JMAX] = V[i + order[j] * JMAX];
+  }
+  __syncthreads();
+  for (int mat = 0; mat < 2; mat++) {
+    double *M = mat == 0 ? Q : W;
+    const int64_t rows = mat == 0 ? m : n;
+    for (int64_t i = threadIdx.x; i < rows; i += NT) {
+      double row[JMAX];
+      for (int q = 0; q < r; q++) row[q] = M[i + (int64_t)q * rows];
+      for (int j = 0; j < k; j++) {
+        double s = 0.0;
+        for (int q = 0; q < r; q++) s += row[q] * Vk[q + j * JMAX];
+        M[i + (int64_t)j * rows] = s;
+      }
+    }
+  }
+  if (threadIdx.x == 0) {
+    if (st[b].rank != -2) st[b].rank = k;
+    else st[b].rank = -(k + 3);  // cap hit: encode rank as -(k+3)
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NT) k_write_far(const TargetDev *tg, const TargetState *st, const double *qw,
+                                                  const LeafDev *leafC, T *dataC) {
+  const TargetDev t = tg[blockIdx.x];
+  const LeafDev lc = leafC[t.leaf];
+  const int k = lc.rank;
+  const double *Q = qw + t.q_off, *W = qw + t.w_off;
+  for (int64_t o = threadIdx.x; o < (int64_t)t.m * k; o += NT) dataC[lc.off_u + o] = T(Q[o]);
+  for (int64_t o = threadIdx.x; o < (int64_t)t.n * k; o += NT) dataC[lc.off_v + o] = T(W[o]);
+  (void)st;
+}
+
+template <typename T>
+__global__ void k_convert(const T *src, double *dst, int64_t count) {
+  for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < count; o += (int64_t)gridDim.x * blockDim.x)
+    dst[o] = (double)src[o];
+}
+
+// ---------------------------------------------------------------------------------------
+// launch wrappers
+// ---------------------------------------------------------------------------------------
+
+template <typename K>
+static cudaError_t set_smem(K kern, size_t bytes) {
+  return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+cudaError_t launch_kernel_dense(int prec, int kernel, const double *pts, int dim, const LeafDev *leaves,
+                                const int32_t *near_ids, int nnear, void *data, cudaStream_t s) {
+  if (nnear == 0) return cudaSuccess;
+  if (prec == 64)
+    k_kernel_dense<double><<<nnear, NT, 0, s>>>(kernel, pts, dim, leaves, near_ids, (double *)data);
+  else
+    k_kernel_dense<float><<<nnear, NT, 0, s>>>(kernel, pts, dim, leaves, near_ids, (float *)data);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_aca(int kernel, const double *pts, int dim, const LeafDev *leaves, const int32_t *far_ids,
+                       int nfar, double eps, int kmax, double *scratch, const int64_t *scratch_off, int32_t *ranks,
+                       cudaStream_t s) {
+  if (nfar == 0) return cudaSuccess;
+  k_aca<<<nfar, NT, 0, s>>>(kernel, pts, dim, leaves, far_ids, eps, kmax, scratch, scratch_off, ranks);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_aca_compact(int prec, const LeafDev *leaves, const int32_t *far_ids, int nfar,
+                               const double *scratch, const int64_t *scratch_off, int kmax, void *data,
+                               cudaStream_t s) {
+  if (nfar == 0) return cudaSuccess;
+  if (prec == 64)
+    k_aca_compact<double><<<nfar, NT, 0, s>>>(leaves, far_ids, scratch, scratch_off, kmax, (double *)data);
+  else
+    k_aca_compact<float><<<nfar, NT, 0, s>>>(leaves, far_ids, scratch, scratch_off, kmax, (float *)data);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_term_jobs(int prec, const TermJob *jobs, int njobs, const LeafDev *leafA, const LeafDev *leafB,
+                             const BlockDev *blocks, const void *dataA, const void *dataB, void *terms,
+                             cudaStream_t s) {
+  if (njobs == 0) return cudaSuccess;
+  cudaError_t e;
+  if (prec == 64) {
+    const size_t sm = Smem::bytes<double>();
+    if ((e = set_smem(k_term_jobs<double>, sm)) != cudaSuccess) return e;
+    k_term_jobs<double><<<njobs, NT, sm, s>>>(jobs, leafA, leafB, blocks, (const double *)dataA,
+                                              (const double *)dataB, (double *)terms);
+  } else {
+    const size_t sm = Smem::bytes<float>();
+    if ((e = set_smem(k_term_jobs<float>, sm)) != cudaSuccess) return e;
+    k_term_jobs<float><<<njobs, NT, sm, s>>>(jobs, leafA, leafB, blocks, (const float *)dataA,
+                                             (const float *)dataB, (float *)terms);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_near_eval(int prec, const TargetDev *tg, int ntg, const int32_t *tg_terms, const TermDev *terms,
+                             const PairDev *pairs, const BlockDev *blocks, const LeafDev *leafA,
+                             const LeafDev *leafB, const void *dataA, const void *dataB, const LeafDev *leafC,
+                             void *dataC, cudaStream_t s) {
+  if (ntg == 0) return cudaSuccess;
+  if (prec == 64)
+    k_near_eval<double><<<ntg, NT, 0, s>>>(tg, tg_terms, terms, pairs, blocks, leafA, leafB, (const double *)dataA,
+                                           (const double *)dataB, leafC, (double *)dataC);
+  else
+    k_near_eval<float><<<ntg, NT, 0, s>>>(tg, tg_terms, terms, pairs, blocks, leafA, leafB, (const float *)dataA,
+                                          (const float *)dataB, leafC, (float *)dataC);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gaussian(int prec, const TargetDev *tg, const TargetState *st, int ntg, int p, uint64_t seed,
+                            int round, void *x_base, cudaStream_t s) {
+  if (ntg == 0) return cudaSuccess;
+  if (prec == 64)
+    k_gaussian<double><<<ntg, NT, 0, s>>>(tg, st, p, seed, round, (double *)x_base);
+  else
+    k_gaussian<float><<<ntg, NT, 0, s>>>(tg, st, p, seed, round, (float *)x_base);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_apply(int prec, bool trans, const ApplyArgs &a, cudaStream_t s) {
+  if (a.ntarget == 0) return cudaSuccess;
+  cudaError_t e;
+  if (prec == 64) {
+    const size_t sm = Smem::bytes<double>();
+    if (!trans) {
+      if ((e = set_smem(k_apply<double, false>, sm)) != cudaSuccess) return e;
+      k_apply<double, false><<<a.ntarget, NT, sm, s>>>(a);
+    } else {
+      if ((e = set_smem(k_apply<double, true>, sm)) != cudaSuccess) return e;
+      k_apply<double, true><<<a.ntarget, NT, sm, s>>>(a);
+    }
+  } else {
+    const size_t sm = Smem::bytes<float>();
+    if (!trans) {
+      if ((e = set_smem(k_apply<float, false>, sm)) != cudaSuccess) return e;
+      k_apply<float, false><<<a.ntarget, NT, sm, s>>>(a);
+    } else {
+      if ((e = set_smem(k_apply<float, true>, sm)) != cudaSuccess) return e;
+      k_apply<float, true><<<a.ntarget, NT, sm, s>>>(a);
+    }
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_orth(int prec, const TargetDev *tg, TargetState *st, int ntg, int p, double eps, void *y_base,
+                        double *qw, void *x_base, int round, cudaStream_t s) {
+  if (ntg == 0) return cudaSuccess;
+  if (prec == 64)
+    k_orth<double><<<ntg, NT, 0, s>>>(tg, st, p, eps, (const double *)y_base, qw, (double *)x_base, round);
+  else
+    k_orth<float><<<ntg, NT, 0, s>>>(tg, st, p, eps, (const float *)y_base, qw, (float *)x_base, round);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_absorb_w(int prec, const TargetDev *tg, TargetState *st, int ntg, int p, double eps_stop,
+                            void *y_base, double *qw, int round, int max_rounds, int32_t *active_count,
+                            cudaStream_t s) {
+  if (ntg == 0) return cudaSuccess;
+  if (prec == 64)
+    k_absorb_w<double><<<ntg, NT, 0, s>>>(tg, st, p, eps_stop, (const double *)y_base, qw, round, max_rounds,
+                                          active_count);
+  else
+    k_absorb_w<float><<<ntg, NT, 0, s>>>(tg, st, p, eps_stop, (const float *)y_base, qw, round, max_rounds,
+                                         active_count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_final(const TargetDev *tg, TargetState *st, int ntg, double eps, double *qw, cudaStream_t s) {
+  if (ntg == 0) return cudaSuccess;
+  const size_t sm = sizeof(double) * (2 * JMAX * JMAX + JMAX) + sizeof(int) * 2 * JMAX;
+  cudaError_t e;
+  if ((e = set_smem(k_final, sm)) != cudaSuccess) return e;
+  k_final<<<ntg, NT, sm, s>>>(tg, st, eps, qw);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_write_far(int prec, const TargetDev *tg, const TargetState *st, int ntg, const double *qw,
+                             const LeafDev *leafC, void *dataC, cudaStream_t s) {
+  if (ntg == 0) return cudaSuccess;
+  if (prec == 64)
+    k_write_far<double><<<ntg, NT, 0, s>>>(tg, st, qw, leafC, (double *)dataC);
+  else
+    k_write_far<float><<<ntg, NT, 0, s>>>(tg, st, qw, leafC, (float *)dataC);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_convert(int prec, const void *src, double *dst, int64_t count, cudaStream_t s) {
+  if (count == 0) return cudaSuccess;
+  const int blocks = (int)std::min<int64_t>((count + NT - 1) / NT, 152 * 16);
+  if (prec == 64)
+    k_convert<double><<<blocks, NT, 0, s>>>((const double *)src, dst, count);
+  else
+    k_convert<float><<<blocks, NT, 0, s>>>((const float *)src, dst, count);
+  return cudaGetLastError();
+}
+
+}  // namespace hm

@@ -1,0 +1,248 @@
+// hmat_tree.cpp -- cluster tree (Def. 2.2), admissibility (Def. 2.3), block-cluster tree
+// (Algorithm 1) and the symbolic sum-expression plan (Algorithm 3 applied from S(I,I) = HK,
+// Algorithm 4). Host code; compiled without floating-point contraction so the tree decisions
+// are the plain IEEE values of their formulas.
+#include "hmat_tree.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cuda_runtime.h>
+
+namespace hm {
+
+Tree::~Tree() {
+  if (d_pts) cudaFree(d_pts);
+  if (d_blocks) cudaFree(d_blocks);
+}
+
+namespace {
+
+struct Builder {
+  Tree &t;
+  void bbox(int64_t begin, int64_t size, double *lo, double *hi) {
+    for (int d = 0; d < t.dim; d++) { lo[d] = INFINITY; hi[d] = -INFINITY; }
+    for (int64_t i = begin; i < begin + size; i++) {
+      const double *p = &t.orig[t.perm[i] * t.dim];
+      for (int d = 0; d < t.dim; d++) {
+        if (p[d] < lo[d]) lo[d] = p[d];
+        if (p[d] > hi[d]) hi[d] = p[d];
+      }
+    }
+  }
+  // Every cluster above depth D splits in two (D = smallest d with ceil(n/2^d) <= leaf_size):
+  // axis = longest bounding-box side (first on ties), points ordered by (coordinate, original
+  // index), first child = the first floor(size/2) of them.
+  int cluster(int64_t begin, int64_t size, int level) {
+    const int id = (int)t.cl.size();
+    t.cl.emplace_back();
+    Cluster c;
+    c.level = level;
+    c.begin = begin;
+    c.size = size;
+    bbox(begin, size, c.lo, c.hi);
+    t.cl[id] = c;
+    if (level < t.depth) {
+      int axis = 0;
+      double best = c.hi[0] - c.lo[0];
+      for (int d = 1; d < t.dim; d++) {
+        const double e = c.hi[d] - c.lo[d];
+        if (e > best) { best = e; axis = d; }
+      }
+      const double *P = t.orig.data();
+      const int dim = t.dim;
+      std::sort(t.perm.begin() + begin, t.perm.begin() + begin + size, [&](int64_t a, int64_t b) {
+        const double xa = P[a * dim + axis], xb = P[b * dim + axis];
+        if (xa < xb) return true;
+        if (xa > xb) return false;
+        return a < b;
+      });
+      const int64_t h = size / 2;
+      const int c0 = cluster(begin, h, level + 1);
+      const int c1 = cluster(begin + h, size - h, level + 1);
+      t.cl[id].child[0] = c0;
+      t.cl[id].child[1] = c1;
+    }
+    return id;
+  }
+  // eta-admissibility: max(diam tau, diam sigma) <= eta * dist(tau, sigma) with bounding-box
+  // diagonals and the Euclidean distance of the boxes; distance zero is never admissible.
+  bool admissible(const Cluster &a, const Cluster &b) const {
+    double da = 0.0, db = 0.0, dd = 0.0;
+    for (int d = 0; d < t.dim; d++) {
+      const double ea = a.hi[d] - a.lo[d];
+      const double eb = b.hi[d] - b.lo[d];
+      da += ea * ea;
+      db += eb * eb;
+      const double g1 = b.lo[d] - a.hi[d];
+      const double g2 = a.lo[d] - b.hi[d];
+      double g = g1 > g2 ? g1 : g2;
+      if (g < 0.0) g = 0.0;
+      dd += g * g;
+    }
+    da = std::sqrt(da);
+    db = std::sqrt(db);
+    dd = std::sqrt(dd);
+    if (!(dd > 0.0)) return false;
+    const double mx = da > db ? da : db;
+    return mx <= t.eta * dd;
+  }
+  int nleaf = 0;
+  // Algorithm 1; children tau'-major; leaves numbered depth-first.
+  int block(int tau, int sigma) {
+    const int id = (int)t.bl.size();
+    t.bl.emplace_back();
+    Block b;
+    b.tau = tau;
+    b.sigma = sigma;
+    b.level = t.cl[tau].level;
+    b.leaf_lo = nleaf;
+    const Cluster &ct = t.cl[tau], &cs = t.cl[sigma];
+    if (admissible(ct, cs)) {
+      b.kind = BK_FAR;
+      b.leaf = nleaf++;
+    } else if (ct.child[0] >= 0 && cs.child[0] >= 0) {
+      b.kind = BK_INNER;
+      t.bl[id] = b;
+      int k = 0;
+      for (int i = 0; i < 2; i++)
+        for (int j = 0; j < 2; j++) {
+          const int c = block(t.cl[tau].child[i], t.cl[sigma].child[j]);
+          t.bl[id].child[k++] = c;
+        }
+      t.bl[id].nchild = 4;
+      t.bl[id].leaf_hi = nleaf;
+      return id;
+    } else {
+      b.kind = BK_NEAR;
+      b.leaf = nleaf++;
+    }
+    b.leaf_hi = nleaf;
+    t.bl[id] = b;
+    return id;
+  }
+};
+
+}  // namespace
+
+std::shared_ptr<Tree> build_tree(const double *xyz, int64_t n, int dim, int leaf_size, double eta) {
+  if (!xyz || n < 1 || dim < 1 || dim > 3 || leaf_size < 1 || !(eta > 0.0)) return nullptr;
+  auto t = std::make_shared<Tree>();
+  t->n = n;
+  t->dim = dim;
+  t->leaf_size = leaf_size;
+  t->eta = eta;
+  t->orig.assign(xyz, xyz + n * dim);
+  int depth = 0;
+  while ((n + ((int64_t)1 << depth) - 1) / ((int64_t)1 << depth) > leaf_size) depth++;
+  t->depth = depth;
+  t->perm.resize(n);
+  for (int64_t i = 0; i < n; i++) t->perm[i] = i;
+  t->cl.reserve(((size_t)2 << depth));
+  Builder bd{*t};
+  bd.cluster(0, n, 0);
+  t->pts.resize(n * dim);
+  for (int64_t i = 0; i < n; i++)
+    for (int d = 0; d < dim; d++) t->pts[i * dim + d] = t->orig[t->perm[i] * dim + d];
+  bd.block(0, 0);
+  t->leaf_block.assign(bd.nleaf, -1);
+  std::vector<int> per_row(t->cl.size(), 0);
+  for (size_t b = 0; b < t->bl.size(); b++) {
+    if (t->bl[b].leaf >= 0) t->leaf_block[t->bl[b].leaf] = (int)b;
+    per_row[t->bl[b].tau]++;
+  }
+  t->csp = *std::max_element(per_row.begin(), per_row.end());
+  return t;
+}
+
+// ----------------------------------------------------------------------------------------
+// Plan: Algorithm 3 from S(I,I) = S_H(I,I) = {(A|IxI, B|IxI)} down the whole block tree.
+// A pair is carried as the two block ids (tau x rho in A, rho x sigma in B); since the tree is
+// level-conserving, the blocks tau' x rho' and rho' x sigma' of a child are children of these.
+// ----------------------------------------------------------------------------------------
+
+namespace {
+
+struct Planner {
+  const Tree &t;
+  const std::vector<int32_t> &rA, &rB;
+  Plan &plan;
+  std::vector<int32_t> stack;  // low-rank terms of the current block (ids)
+
+  static int child_index(const Tree &t, int parent_cluster, int child_cluster) {
+    return t.cl[parent_cluster].child[0] == child_cluster ? 0 : 1;
+  }
+
+  void visit(int b, const std::vector<PairDev> &pairs) {
+    const Block &bk = t.bl[b];
+    if (bk.kind != BK_INNER) {
+      const int leaf = bk.leaf;
+      plan.leaf_term_off[leaf] = (int64_t)plan.leaf_terms.size();
+      plan.leaf_terms.insert(plan.leaf_terms.end(), stack.begin(), stack.end());
+      plan.leaf_pair_off[leaf] = (int64_t)plan.leaf_pairs.size();
+      plan.leaf_pairs.insert(plan.leaf_pairs.end(), pairs.begin(), pairs.end());
+      return;
+    }
+    for (int c = 0; c < bk.nchild; c++) {
+      const int cb = bk.child[c];
+      const int ti = child_index(t, bk.tau, t.bl[cb].tau);
+      const int si = child_index(t, bk.sigma, t.bl[cb].sigma);
+      const size_t mark = stack.size();
+      std::vector<PairDev> np;
+      np.reserve(pairs.size() * 2);
+      for (const PairDev &pr : pairs) {
+        const Block &ba = t.bl[pr.blkA], &bb = t.bl[pr.blkB];
+        // tau x rho and rho x sigma are inner blocks (pairs of inner blocks only reach here)
+        for (int ri = 0; ri < 2; ri++) {
+          const int a2 = ba.child[ti * 2 + ri];   // tau' x rho'
+          const int b2 = bb.child[ri * 2 + si];   // rho' x sigma'
+          const Block &x = t.bl[a2], &y = t.bl[b2];
+          if (x.kind == BK_FAR || y.kind == BK_FAR) {
+            PlanTerm tm;
+            tm.block = cb;
+            if (x.kind == BK_FAR && y.kind == BK_FAR) {
+              const int ka = rA[x.leaf], kb = rB[y.leaf];
+              tm.type = ka <= kb ? JOB_FF_R : JOB_FF_L;
+              tm.a = x.leaf;
+              tm.b = y.leaf;
+              tm.rank = ka <= kb ? ka : kb;
+            } else if (x.kind == BK_FAR) {
+              tm.type = JOB_FH;
+              tm.a = x.leaf;
+              tm.b = b2;
+              tm.rank = rA[x.leaf];
+            } else {
+              tm.type = JOB_HF;
+              tm.a = a2;
+              tm.b = y.leaf;
+              tm.rank = rB[y.leaf];
+            }
+            stack.push_back((int32_t)plan.terms.size());
+            plan.terms.push_back(tm);
+          } else {
+            np.push_back(PairDev{a2, b2});
+          }
+        }
+      }
+      visit(cb, np);
+      stack.resize(mark);
+    }
+  }
+};
+
+}  // namespace
+
+void build_plan(const Tree &t, const std::vector<int32_t> &rankA, const std::vector<int32_t> &rankB, Plan &plan) {
+  const size_t nleaf = t.leaf_block.size();
+  plan.terms.clear();
+  plan.leaf_terms.clear();
+  plan.leaf_pairs.clear();
+  plan.leaf_term_off.assign(nleaf + 1, 0);
+  plan.leaf_pair_off.assign(nleaf + 1, 0);
+  Planner pl{t, rankA, rankB, plan, {}};
+  std::vector<PairDev> root{PairDev{0, 0}};
+  pl.visit(0, root);
+  plan.leaf_term_off[nleaf] = (int64_t)plan.leaf_terms.size();
+  plan.leaf_pair_off[nleaf] = (int64_t)plan.leaf_pairs.size();
+}
+
+}  // namespace hm

@@ -1,0 +1,68 @@
+// hmat_tree.h -- host-side cluster tree, block-cluster tree and sum-expression plan.
+#pragma once
+#include <cstdint>
+#include <memory>
+#include <vector>
+
+#include "hmat_internal.h"
+
+namespace hm {
+
+struct Cluster {
+  int level = 0;
+  int64_t begin = 0, size = 0;
+  int child[2] = {-1, -1};
+  double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+};
+
+enum BlockKind : int { BK_INNER = 0, BK_FAR = 1, BK_NEAR = 2 };
+
+struct Block {
+  int tau = -1, sigma = -1, kind = BK_INNER, level = 0;
+  int child[4] = {-1, -1, -1, -1};
+  int nchild = 0;
+  int leaf = -1;               // depth-first leaf number (leaves only)
+  int32_t leaf_lo = 0, leaf_hi = 0;
+};
+
+struct Tree {
+  int64_t n = 0;
+  int dim = 0, leaf_size = 0, depth = 0;
+  double eta = 0;
+  std::vector<double> orig;    // points in original order (n x dim)
+  std::vector<double> pts;     // points in permuted order
+  std::vector<int64_t> perm;   // perm[i] = original index of permuted position i
+  std::vector<Cluster> cl;
+  std::vector<Block> bl;
+  std::vector<int> leaf_block; // leaf -> block
+  int csp = 0;
+  // device copies (owned)
+  double *d_pts = nullptr;
+  BlockDev *d_blocks = nullptr;
+  ~Tree();
+};
+
+// Def. 2.2 / Def. 2.3 / Algorithm 1. Returns nullptr on invalid input.
+std::shared_ptr<Tree> build_tree(const double *xyz, int64_t n, int dim, int leaf_size, double eta);
+
+// Symbolic restriction (Algorithm 3) over the whole block tree, from S(I,I) = HK.
+struct PlanTerm {
+  int32_t type;        // TermJobType
+  int32_t a, b;        // see TermJob
+  int32_t rank;
+  int block;           // block tau' x sigma' where the term was created
+};
+
+struct Plan {
+  std::vector<PlanTerm> terms;
+  // per leaf: term ids and pairs (CSR)
+  std::vector<int64_t> leaf_term_off;   // nleaf + 1
+  std::vector<int32_t> leaf_terms;
+  std::vector<int64_t> leaf_pair_off;   // nleaf + 1
+  std::vector<PairDev> leaf_pairs;
+};
+
+// rankA/rankB: per leaf ranks of the two factors (-1 for dense leaves).
+void build_plan(const Tree &t, const std::vector<int32_t> &rankA, const std::vector<int32_t> &rankB, Plan &plan);
+
+}  // namespace hm

@@ -1,0 +1,238 @@
+"""Thin ctypes binding of libhmat.so: the same names as the C-ABI in include/hmat.h.
+
+Argument marshalling only; every step of the product runs in the library's CUDA kernels.
+Loading fails loudly (ImportError) when the library has not been built, and every call that
+fails raises HmatError with the library's status and message -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhmat.so")
+
+HMAT_OK, HMAT_EINVAL, HMAT_ENOMEM, HMAT_ECUDA, HMAT_ENOTCONV, HMAT_ETIMEOUT, HMAT_EMISMATCH = range(7)
+STATUS_NAMES = {0: "HMAT_OK", 1: "HMAT_EINVAL", 2: "HMAT_ENOMEM", 3: "HMAT_ECUDA", 4: "HMAT_ENOTCONV",
+                5: "HMAT_ETIMEOUT", 6: "HMAT_EMISMATCH"}
+
+K_EXP, K_INVQ, K_POLY2 = 0, 1, 2
+PTS_CUBE, PTS_SPHERE = 0, 1
+MODE_F64, MODE_MIXED = 0, 1
+
+# every symbol include/hmat.h declares
+EXPORTS = ["hmat_points", "hmat_build", "hmat_multiply", "hmat_to_dense", "hmat_leaf_count", "hmat_leaf_info",
+           "hmat_leaf_get", "hmat_permutation", "hmat_stats", "hmat_sumexpr_counts", "hmat_destroy",
+           "hmat_last_error", "hmat_set_allocator"]
+
+
+class HmatError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class BuildOpts(ctypes.Structure):
+    _fields_ = [("leaf_size", ctypes.c_int), ("eta", ctypes.c_double), ("aca_eps", ctypes.c_double),
+                ("factor_prec", ctypes.c_int), ("aca_kmax", ctypes.c_int)]
+
+
+class MultOpts(ctypes.Structure):
+    _fields_ = [("eps", ctypes.c_double), ("mode", ctypes.c_int), ("rank_proposal", ctypes.c_int),
+                ("max_rank", ctypes.c_int), ("max_rounds", ctypes.c_int), ("block_width", ctypes.c_int),
+                ("seed", ctypes.c_uint64)]
+
+
+class Leaf(ctypes.Structure):
+    _fields_ = [("row_begin", ctypes.c_int64), ("row_size", ctypes.c_int64), ("col_begin", ctypes.c_int64),
+                ("col_size", ctypes.c_int64), ("level", ctypes.c_int), ("far", ctypes.c_int),
+                ("rank", ctypes.c_int)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("depth", ctypes.c_int), ("csp", ctypes.c_int),
+                ("n_far", ctypes.c_int64), ("n_near", ctypes.c_int64), ("storage_bytes", ctypes.c_int64),
+                ("factor_prec", ctypes.c_int), ("max_rank", ctypes.c_int),
+                ("n_terms", ctypes.c_int64), ("n_lr_refs", ctypes.c_int64), ("n_hpairs", ctypes.c_int64),
+                ("rounds", ctypes.c_int), ("not_converged", ctypes.c_int64),
+                ("flops_apply", ctypes.c_double), ("flops_terms", ctypes.c_double),
+                ("flops_near", ctypes.c_double), ("bytes_apply", ctypes.c_double),
+                ("ms_plan", ctypes.c_double), ("ms_terms", ctypes.c_double), ("ms_near", ctypes.c_double),
+                ("ms_sample", ctypes.c_double), ("ms_final", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_PD = ctypes.POINTER(ctypes.c_double)
+_PI64 = ctypes.POINTER(ctypes.c_int64)
+_lib = None
+
+
+def lib():
+    """Load libhmat.so (built by __graft_entry__.build() / build_lib.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build the CUDA library first (paper_1805_08998_gb300.build_lib)")
+    L = ctypes.CDLL(LIB_PATH)
+    L.hmat_points.argtypes = [ctypes.c_int, ctypes.c_int, _I64, ctypes.c_uint64, _PD]
+    L.hmat_build.argtypes = [_PD, _I64, ctypes.c_int, ctypes.c_int, ctypes.POINTER(BuildOpts), _P, _P,
+                             ctypes.POINTER(_P)]
+    L.hmat_multiply.argtypes = [_P, _P, ctypes.POINTER(MultOpts), _P, ctypes.POINTER(_P)]
+    L.hmat_to_dense.argtypes = [_P, _PD, _I64]
+    L.hmat_leaf_count.argtypes = [_P, _PI64]
+    L.hmat_leaf_info.argtypes = [_P, _I64, ctypes.POINTER(Leaf)]
+    L.hmat_leaf_get.argtypes = [_P, _I64, _PD, _PD]
+    L.hmat_permutation.argtypes = [_P, _PI64]
+    L.hmat_stats.argtypes = [_P, ctypes.POINTER(Stats)]
+    L.hmat_sumexpr_counts.argtypes = [_P, _P, _PI64, _PI64]
+    L.hmat_destroy.argtypes = [_P]
+    L.hmat_destroy.restype = None
+    L.hmat_last_error.restype = ctypes.c_char_p
+    for name in ["hmat_points", "hmat_build", "hmat_multiply", "hmat_to_dense", "hmat_leaf_count",
+                 "hmat_leaf_info", "hmat_leaf_get", "hmat_permutation", "hmat_stats", "hmat_sumexpr_counts",
+                 "hmat_set_allocator"]:
+        getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _check(status: int, allow=()):
+    if status != HMAT_OK and status not in allow:
+        raise HmatError(status, lib().hmat_last_error().decode())
+    return status
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)  # torch.cuda.Stream
+
+
+class HMatrix:
+    """Owner of an hmat_t; released with hmat_destroy."""
+
+    def __init__(self, handle: int):
+        self._h = handle
+        self.last_status = HMAT_OK
+
+    def __del__(self):
+        self.close()
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().hmat_destroy(self._h)
+            self._h = None
+
+    @property
+    def handle(self):
+        return self._h
+
+    def leaf_count(self) -> int:
+        n = ctypes.c_int64()
+        _check(lib().hmat_leaf_count(self._h, ctypes.byref(n)))
+        return n.value
+
+    def leaf_info(self, i: int) -> Leaf:
+        info = Leaf()
+        _check(lib().hmat_leaf_info(self._h, i, ctypes.byref(info)))
+        return info
+
+    def leaf_get(self, i: int):
+        info = self.leaf_info(i)
+        m, n = info.row_size, info.col_size
+        if not info.far:
+            D = np.zeros((n, m), np.float64)
+            _check(lib().hmat_leaf_get(self._h, i, D.ctypes.data_as(_PD), None))
+            return D.T.copy()
+        k = info.rank
+        U = np.zeros((k, m), np.float64)
+        V = np.zeros((k, n), np.float64)
+        if k > 0:
+            _check(lib().hmat_leaf_get(self._h, i, U.ctypes.data_as(_PD), V.ctypes.data_as(_PD)))
+        return U.T.copy(), V.T.copy()
+
+    def leaves(self):
+        return [self.leaf_info(i) for i in range(self.leaf_count())]
+
+    def to_dense(self) -> np.ndarray:
+        n = self.stats()["n"]
+        out = np.zeros((n, n), np.float64)  # filled column-major -> transpose view
+        _check(lib().hmat_to_dense(self._h, out.ctypes.data_as(_PD), n))
+        return out.T.copy()
+
+    def permutation(self) -> np.ndarray:
+        n = self.stats()["n"]
+        perm = np.zeros(n, np.int64)
+        _check(lib().hmat_permutation(self._h, perm.ctypes.data_as(_PI64)))
+        return perm
+
+    def stats(self) -> dict:
+        s = Stats()
+        _check(lib().hmat_stats(self._h, ctypes.byref(s)))
+        return s.as_dict()
+
+
+def hmat_points(dist: int, dim: int, n: int, seed: int) -> np.ndarray:
+    out = np.zeros((n, dim), np.float64)
+    _check(lib().hmat_points(dist, dim, n, seed, out.ctypes.data_as(_PD)))
+    return out
+
+
+def hmat_build(xyz: np.ndarray, kernel: int, leaf_size: int = 32, eta: float = 1.0, aca_eps: float = 1e-10,
+               factor_prec: int = 64, aca_kmax: int = 0, tree_from: HMatrix | None = None, stream=None) -> HMatrix:
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+    n, dim = xyz.shape
+    opts = BuildOpts(leaf_size, eta, aca_eps, factor_prec, aca_kmax)
+    h = _P()
+    _check(lib().hmat_build(xyz.ctypes.data_as(_PD), n, dim, kernel, ctypes.byref(opts),
+                            tree_from.handle if tree_from is not None else None, _stream_ptr(stream),
+                            ctypes.byref(h)))
+    return HMatrix(h.value)
+
+
+def hmat_multiply(A: HMatrix, B: HMatrix, eps: float, mode: int = MODE_F64, rank_proposal: int = 0,
+                  max_rank: int = 0, max_rounds: int = 0, block_width: int = 0, seed: int = 0,
+                  stream=None, allow_notconv: bool = True) -> HMatrix:
+    opts = MultOpts(eps, mode, rank_proposal, max_rank, max_rounds, block_width, seed)
+    h = _P()
+    st = lib().hmat_multiply(A.handle, B.handle, ctypes.byref(opts), _stream_ptr(stream), ctypes.byref(h))
+    _check(st, allow=(HMAT_ENOTCONV,) if allow_notconv else ())
+    C = HMatrix(h.value)
+    C.last_status = st
+    return C
+
+
+def hmat_sumexpr_counts(A: HMatrix, B: HMatrix):
+    L = A.leaf_count()
+    lr = np.zeros(L, np.int64)
+    hp = np.zeros(L, np.int64)
+    _check(lib().hmat_sumexpr_counts(A.handle, B.handle, lr.ctypes.data_as(_PI64), hp.ctypes.data_as(_PI64)))
+    return lr, hp
+
+
+@dataclass
+class LeafArrays:
+    """Leaf geometry of an H-matrix as numpy arrays (permuted ranges)."""
+    row_begin: np.ndarray
+    row_size: np.ndarray
+    col_begin: np.ndarray
+    col_size: np.ndarray
+    far: np.ndarray
+    rank: np.ndarray
+    level: np.ndarray
+
+
+def leaf_arrays(H: HMatrix) -> LeafArrays:
+    infos = H.leaves()
+    f = lambda k: np.array([getattr(x, k) for x in infos], np.int64)
+    return LeafArrays(f("row_begin"), f("row_size"), f("col_begin"), f("col_size"), f("far"), f("rank"), f("level"))

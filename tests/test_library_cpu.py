@@ -1,0 +1,96 @@
+"""Host-side checks of the C-ABI library that need no GPU: it builds, loads, exports every
+symbol include/hmat.h declares, validates its arguments, and its point generator matches
+the shared seeded generator."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1805_08998_gb300 import inputs
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def H():
+    from paper_1805_08998_gb300 import build_lib
+    build_lib.build()
+    from paper_1805_08998_gb300 import hmat
+    hmat.lib()
+    return hmat
+
+
+def _declared_symbols():
+    src = open(os.path.join(ROOT, "include", "hmat.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(hmat_[a-z_]+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol(H):
+    declared = _declared_symbols()
+    assert "hmat_multiply" in declared and "hmat_build" in declared
+    L = H.lib()
+    for name in declared:
+        assert hasattr(L, name), name
+        assert ctypes.cast(getattr(L, name), ctypes.c_void_p).value
+    assert sorted(H.EXPORTS) == declared
+
+
+@pytest.mark.parametrize("dist,dim,n,seed", [(0, 1, 17, 3), (0, 2, 1000, 0), (0, 3, 333, 9), (1, 3, 500, 0)])
+def test_points_match_shared_generator(H, dist, dim, n, seed):
+    a = H.hmat_points(dist, dim, n, seed)
+    b = inputs.points(dist, dim, n, seed)
+    if dist == 0:
+        assert np.array_equal(a, b)
+    else:  # cos/sin of two math libraries may differ in the last bit
+        assert np.abs(a - b).max() <= 4e-16
+
+
+def test_argument_validation(H):
+    xyz = inputs.points(0, 2, 100, 0)
+    with pytest.raises(H.HmatError) as e:
+        H.hmat_build(xyz, 0, leaf_size=0)
+    assert e.value.status == H.HMAT_EINVAL
+    with pytest.raises(H.HmatError) as e:
+        H.hmat_build(xyz, 0, leaf_size=16, eta=-1.0)
+    assert e.value.status == H.HMAT_EINVAL
+    with pytest.raises(H.HmatError) as e:
+        H.hmat_build(xyz, 0, leaf_size=16, factor_prec=16)
+    assert e.value.status == H.HMAT_EINVAL
+    with pytest.raises(H.HmatError) as e:
+        H.hmat_build(xyz, 7, leaf_size=16)
+    assert e.value.status == H.HMAT_EINVAL
+    bad = xyz.copy()
+    bad[3, 1] = np.nan
+    with pytest.raises(H.HmatError) as e:
+        H.hmat_build(bad, 0, leaf_size=16)
+    assert e.value.status == H.HMAT_EINVAL
+    assert "non-finite" in str(e.value)
+    # NULL handles
+    L = H.lib()
+    out = ctypes.c_void_p()
+    opts = H.MultOpts(1e-6, 0, 0, 0, 0, 0, 0)
+    assert L.hmat_multiply(None, None, ctypes.byref(opts), None, ctypes.byref(out)) == H.HMAT_EINVAL
+    assert out.value is None
+    assert L.hmat_leaf_count(None, None) == H.HMAT_EINVAL
+    assert L.hmat_set_allocator(ctypes.c_void_p(1), None, None) == H.HMAT_EINVAL
+    with pytest.raises(H.HmatError):
+        H.hmat_points(1, 2, 10, 0)
+
+
+def test_last_error_is_thread_local(H):
+    import threading
+    L = H.lib()
+    assert L.hmat_leaf_count(None, None) == H.HMAT_EINVAL
+    msg_main = L.hmat_last_error().decode()
+    seen = {}
+
+    def worker():
+        seen["t"] = L.hmat_last_error().decode()
+
+    th = threading.Thread(target=worker)
+    th.start()
+    th.join()
+    assert msg_main and seen["t"] == ""

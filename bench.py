@@ -1,0 +1,388 @@
+#!/usr/bin/env python
+"""Benchmark of the H x H product with blockwise eps-best truncation on one GB300.
+
+Workload (the paper's setting, Sec. 6.1, with synthetic stand-ins for its Galerkin sphere
+matrices): N = 32768 points uniform on the unit sphere (seed 0), A with k = exp(-r), B with
+k = 1/(1+r^2), cardinality-balanced bisection with leaf size 64, eta = 1, far leaves by ACA
+to 1e-8 stored in FP32, C = A B truncated to relative Frobenius error eps = 1e-6 per block.
+
+One step = one hmat_multiply (all of the hot path: symbolic restriction, low-rank products,
+adaptive randomized sampling + FP64 orthogonalisation, core truncation, near field). The
+"chosen form" is MODE_MIXED (FP32 contractions, FP64 orthogonalisation and core SVD); the
+plain FP64 GPU path (MODE_F64) is timed beside it.
+
+value = degrees of freedom per second (N / product time; the paper reports seconds per
+degree of freedom), summed over ranks. Inputs (A, B: ~0.7 GB of FP32 factors) exceed the
+129 MB L2, so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1805_08998_gb300 import inputs  # noqa: E402
+
+METRIC = "H×H product time & GFLOP/s at ε=1e-6: chosen form vs plain FP64 GPU; %roofline"
+WORKLOAD = {
+    "workload": "hxh_sphere_n32768_exp_x_invq_leaf64_eta1_fp32factors_eps1e-6",
+    "n": 32768, "points": "uniform on unit sphere S^2, seed 0", "kernel_A": "exp(-r)",
+    "kernel_B": "1/(1+r^2)", "leaf_size": 64, "eta": 1.0, "aca_eps": 1e-8, "factor_prec": 32,
+    "eps": 1e-6, "block_width": 8, "inputs_exceed_l2": True,
+}
+UNIT = "DOF/s"
+
+
+def _rank_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
+            int(os.environ.get("WORLD_SIZE", "1")))
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _traffic_from_profile():
+    """DRAM bytes per k_apply launch from the committed ncu summary, if it was taken on the
+    current kernel source (the summary records the source's sha256)."""
+    prof = os.path.join(ROOT, "profiles", "k_apply_sphere_n32768.md")
+    src = os.path.join(ROOT, "paper_1805_08998_gb300", "csrc", "hmat_kernels.cu")
+    if not (os.path.exists(prof) and os.path.exists(src)):
+        return None
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    txt = open(prof).read()
+    if f"kernel source sha256: {sha}" not in txt:
+        return None
+    for line in txt.splitlines():
+        if line.startswith("dram_bytes_per_launch:"):
+            return float(line.split(":")[1])
+    return None
+
+
+# ------------------------------------------------------------------------------------ CPU oracle
+
+def oracle_sample(n_blocks_per_level=2, seed=0, threads=None, budget_s=25.0, setup=None):
+    """Time the oracle on a stratified sample of target blocks of the workload and extrapolate
+    to the whole product: exact block C|b = A|tau x I * B|I x sigma (cost ~ m n N) plus the
+    SVD truncation of far blocks (cost ~ m n min(m, n)). Returns (estimated seconds for the full
+    product, description, threads used, setup)."""
+    from oracle import oracle as O
+    if threads:
+        O.set_threads(threads)
+    W = WORKLOAD
+    if setup is None:
+        P = inputs.points(inputs.PTS_SPHERE, 3, W["n"], 0)
+        T = O.Tree(P, W["leaf_size"], W["eta"])
+        A = O.HMatrix(T, O.KERNEL_EXP, W["aca_eps"], prec32=True)
+        B = O.HMatrix(T, O.KERNEL_INVQ, W["aca_eps"], prec32=True)
+        setup = (T, A, B)
+    T, A, B = setup
+    N = T.n
+    rng = np.random.default_rng(seed)
+    lv = T.leaf_blocks[:, 3]
+    far = T.leaf_blocks[:, 2] == 1
+    sizes = np.array([T.leaf_ranges(l) for l in range(T.nleaf)])
+    mn = sizes[:, 1] * sizes[:, 3]
+    c_prod, c_svd = [], []
+    t_start = time.perf_counter()
+    done = 0
+    for level in sorted(set(lv.tolist()), reverse=True):
+        cand = np.nonzero((lv == level) & (mn <= 256 * 256))[0]
+        if len(cand) == 0:
+            continue
+        for l in rng.choice(cand, size=min(n_blocks_per_level, len(cand)), replace=False):
+            if time.perf_counter() - t_start > budget_s:
+                break
+            r0, m, c0, n = sizes[l]
+            t0 = time.perf_counter()
+            blk = O.block_product(A, B, r0, m, c0, n)
+            t1 = time.perf_counter()
+            c_prod.append((t1 - t0) / (m * n * N))
+            if far[l]:
+                O.truth_for_block(blk, W["eps"])
+                c_svd.append((time.perf_counter() - t1) / (m * n * min(m, n)))
+            done += 1
+    cp = float(np.mean(c_prod))
+    cs = float(np.mean(c_svd)) if c_svd else 0.0
+    svd_work = float(np.sum((mn * np.minimum(sizes[:, 1], sizes[:, 3]))[far]))
+    t_est = cp * float(np.sum(mn)) * N + cs * svd_work
+    desc = (f"{done} blocks (stratified by level, m*n <= 256^2) of the N={N} product: exact block products "
+            f"and SVD truncations timed, extrapolated to all {T.nleaf} leaves by cost ~ m*n*N (+ m*n*min(m,n) "
+            f"for the far-block SVDs)")
+    return t_est, desc, O.num_threads(), setup
+
+
+# ------------------------------------------------------------------------------------ reference arm
+
+def run_reference(args):
+    rank, _, world = _rank_env()
+    if world > 1 and rank != 0:
+        return
+    setup = None
+    for w in range(args.warmup):
+        _, _, _, setup = oracle_sample(n_blocks_per_level=1, seed=100 + w, budget_s=10.0, setup=setup)
+    vals = []
+    t0 = time.perf_counter()
+    desc, thr = "", 0
+    for k in range(args.steps):
+        t_est, desc, thr, setup = oracle_sample(n_blocks_per_level=1, seed=k, budget_s=10.0, setup=setup)
+        vals.append(WORKLOAD["n"] / t_est)
+    wall = time.perf_counter() - t0
+    v = float(np.median(vals))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * WORKLOAD["n"] / v, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": WORKLOAD,
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": thr, "kind": "oracle",
+                         "sample": desc + "; one stratified sample per step"},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "wall_s": wall,
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------------ GPU arm
+
+def run_ours(args):
+    import torch
+    from paper_1805_08998_gb300 import build_lib
+    build_lib.build()
+    from paper_1805_08998_gb300 import hmat as H
+
+    rank, local_rank, world = _rank_env()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream(dev)
+    W = WORKLOAD
+    P = inputs.points(inputs.PTS_SPHERE, 3, W["n"], 0)
+    A = H.hmat_build(P, H.K_EXP, leaf_size=W["leaf_size"], eta=W["eta"], aca_eps=W["aca_eps"],
+                     factor_prec=W["factor_prec"], stream=stream)
+    B = H.hmat_build(P, H.K_INVQ, leaf_size=W["leaf_size"], eta=W["eta"], aca_eps=W["aca_eps"],
+                     factor_prec=W["factor_prec"], tree_from=A, stream=stream)
+
+    def mult(mode, seed):
+        return H.hmat_multiply(A, B, W["eps"], mode=mode, block_width=W["block_width"], seed=seed, stream=stream)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    # ---- warm-up (chosen form and plain FP64)
+    for w in range(max(args.warmup, 3)):
+        C = mult(H.MODE_MIXED, 1000 + w)
+    del C
+    C = mult(H.MODE_F64, 999)
+    del C
+    torch.cuda.synchronize()
+
+    # ---- timed: chosen form
+    stats = []
+    barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local_rank) as clk:
+        ev0.record(stream)
+        for k in range(args.steps):
+            C = mult(H.MODE_MIXED, k)
+            stats.append(C.stats())
+            last_status = C.last_status
+            del C
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps)
+
+    # ---- timed: plain FP64 GPU path (same workload)
+    k64 = max(1, min(args.steps, 3))
+    s64 = []
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(k64):
+        C = mult(H.MODE_F64, k)
+        s64.append(C.stats())
+        del C
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms64 = max_over_ranks(e0.elapsed_time(e1) / k64)
+
+    # ---- end to end through the public API with host buffers: H2D of the points from pinned
+    # memory, both builds (GPU ACA), the product, and D2H of C's packed factors to pinned memory
+    pts_pinned = torch.from_numpy(P.copy()).pin_memory()
+    C = mult(H.MODE_MIXED, 0)
+    out_bytes = C.data_bytes()
+    del C
+    # C's packed size varies slightly with the test matrices (ranks differ by one here and
+    # there): size the pinned buffer with a margin
+    host_out = torch.empty(int(out_bytes * 1.5) + (1 << 20), dtype=torch.uint8).pin_memory()
+    e2e_steps = max(1, min(args.steps, 3))
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    h2d = d2h = 0
+    xyz = pts_pinned.numpy()  # pinned host buffer; hmat_build copies it to the device itself
+    for k in range(e2e_steps):
+        h2d += pts_pinned.numel() * 8
+        Ae = H.hmat_build(xyz, H.K_EXP, leaf_size=W["leaf_size"], eta=W["eta"], aca_eps=W["aca_eps"],
+                          factor_prec=W["factor_prec"], stream=stream)
+        Be = H.hmat_build(xyz, H.K_INVQ, leaf_size=W["leaf_size"], eta=W["eta"], aca_eps=W["aca_eps"],
+                          factor_prec=W["factor_prec"], tree_from=Ae, stream=stream)
+        Ce = H.hmat_multiply(Ae, Be, W["eps"], mode=H.MODE_MIXED, block_width=W["block_width"], seed=k,
+                             stream=stream)
+        nb = Ce.data_bytes()
+        Ce.data_get((host_out.data_ptr(), host_out.numel()))
+        d2h += nb
+        del Ae, Be, Ce
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps)
+
+    st = stats[-1]
+    flops = st["flops_terms"] + st["flops_near"] + st["flops_apply"]
+    gflops = flops / (ms * 1e-3) / 1e9
+    st64 = s64[-1]
+    flops64 = st64["flops_terms"] + st64["flops_near"] + st64["flops_apply"]
+    # dominant kernel: the sum-expression application (k_apply), timed by CUDA events on the
+    # call's stream inside the library
+    apply_ms = np.mean([s["ms_apply"] for s in stats])
+    apply_launches = np.mean([s["apply_launches"] for s in stats])
+    apply_bytes = np.mean([s["bytes_apply_use"] for s in stats])
+    per_launch_ms = apply_ms / max(apply_launches, 1)
+    achieved = (apply_bytes / max(apply_launches, 1)) / (per_launch_ms * 1e-3) / 1e9
+    peak, peak_kind = _peaks()
+    traffic = _traffic_from_profile()
+    launches = int(sum(s["launches"] for s in stats))
+    value = world * W["n"] / (ms * 1e-3)
+
+    if rank == 0:
+        # CPU oracle baseline on the host cores (bounded sample)
+        t_est, desc, thr, _ = oracle_sample(n_blocks_per_level=2, budget_s=20.0)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": dict(W, parallelism="replicas" if world > 1 else "single"),
+            "gflops": gflops,
+            "plain_f64": {"ms_per_step": ms64, "value": world * W["n"] / (ms64 * 1e-3),
+                          "gflops": flops64 / (ms64 * 1e-3) / 1e9, "steps": k64},
+            "speedup_vs_plain_f64": ms64 / ms,
+            "status": int(last_status),
+            "phases_ms": {k: st[k] for k in ("ms_plan", "ms_terms", "ms_sample", "ms_final", "ms_near", "ms_apply")},
+            "max_rank": st["max_rank"], "rounds": st["rounds"],
+            "roofline": {"kernel": "k_apply (sum-expression application)", "bound": "hbm",
+                         "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "peak_source": peak_kind, "traffic": traffic,
+                         "per_launch_ms": per_launch_ms, "launches_per_step": apply_launches,
+                         "algorithmic_bytes_per_launch": apply_bytes / max(apply_launches, 1)},
+            "cpu_baseline": {"value": W["n"] / t_est, "unit": UNIT, "cores": thr, "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": world * W["n"] / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d // e2e_steps,
+                    "d2h_bytes_per_step": d2h // e2e_steps, "ms_per_step": e2e_s * 1e3,
+                    "includes": "points H2D (pinned), hmat_build x2 (GPU ACA), hmat_multiply, C factors D2H (pinned)"},
+            "gpu_launches": launches,
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

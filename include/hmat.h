@@ -113,6 +113,15 @@ typedef struct {
   double flops_near;             /* algorithmic flops of the near-field evaluation */
   double bytes_apply;            /* algorithmic bytes read by the sum-expression applications */
   double ms_plan, ms_terms, ms_near, ms_sample, ms_final;  /* device/host phase times */
+  double ms_apply;               /* summed device time of the sum-expression application kernels
+                                    (CUDA events on the call's stream around each launch) */
+  int64_t apply_launches;        /* number of those launches */
+  double bytes_apply_use;        /* algorithmic bytes of those launches: every factor element of
+                                    every target's sum-expression read once per launch, plus the
+                                    In/Out panels ((m + n) * p elements per target) */
+  int64_t launches;              /* kernels this call launched (all of them are the library's) */
+  int64_t n_ff_jobs;             /* low-rank products with two far factors */
+  int64_t n_panels;              /* panels of products with one inadmissible factor */
 } hmat_stats_t;
 
 /* Fill xyz (n*dim doubles, row-major, caller-owned) with the seeded points of the given
@@ -161,6 +170,15 @@ hmat_status hmat_leaf_get(const hmat_t h, int64_t i, double *U, double *V);
 
 /* perm[i] = original index of permuted position i (n entries, caller-owned). */
 hmat_status hmat_permutation(const hmat_t h, int64_t *perm);
+
+/* Size in bytes of h's packed factor buffer (all leaves; element type float or double as
+ * hmat_stats.factor_prec says; leaf offsets follow the depth-first leaf order: for each leaf,
+ * far: U (row_size x rank) then V (col_size x rank); near: the dense block). */
+hmat_status hmat_data_bytes(const hmat_t h, int64_t *bytes);
+
+/* Copy h's packed factor buffer to the host buffer out (capacity `bytes`, caller-owned;
+ * EINVAL if smaller than hmat_data_bytes). Pinned host memory makes it one DMA. Synchronises. */
+hmat_status hmat_data_get(const hmat_t h, void *out, int64_t bytes);
 
 /* Structure and, for products, work statistics of h. */
 hmat_status hmat_stats(const hmat_t h, hmat_stats_t *stats);

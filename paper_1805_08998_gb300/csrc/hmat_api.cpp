@@ -180,6 +180,8 @@ void ensure_tree_device(Tree &t, cudaStream_t s) {
     bd[b].n = (int32_t)t.cl[bk.sigma].size;
     bd[b].leaf_lo = bk.leaf_lo;
     bd[b].leaf_hi = bk.leaf_hi;
+    bd[b].parent = bk.parent;
+    bd[b].pad = 0;
   }
   ck(cudaMalloc(&t.d_blocks, sizeof(BlockDev) * bd.size()), "cudaMalloc blocks");
   ck(cudaMemcpyAsync(t.d_blocks, bd.data(), sizeof(BlockDev) * bd.size(), cudaMemcpyHostToDevice, s), "blocks");
@@ -479,6 +481,24 @@ hmat_status hmat_permutation(const hmat_t h, int64_t *perm) {
   });
 }
 
+hmat_status hmat_data_bytes(const hmat_t h, int64_t *bytes) {
+  return guard([&] {
+    if (!h || !bytes) fail(HMAT_EINVAL, "NULL argument");
+    *bytes = h->data_elems * (int64_t)esize(h->prec);
+  });
+}
+
+hmat_status hmat_data_get(const hmat_t h, void *out, int64_t bytes) {
+  return guard([&] {
+    if (!h || !out) fail(HMAT_EINVAL, "NULL argument");
+    const int64_t need = h->data_elems * (int64_t)esize(h->prec);
+    if (bytes < need) fail(HMAT_EINVAL, "output buffer smaller than hmat_data_bytes");
+    if (need == 0) return;
+    ck(cudaMemcpyAsync(out, h->d_data.p, (size_t)need, cudaMemcpyDeviceToHost, h->stream), "data get");
+    ck(cudaStreamSynchronize(h->stream), "data get");
+  });
+}
+
 hmat_status hmat_stats(const hmat_t h, hmat_stats_t *stats) {
   return guard([&] {
     if (!h || !stats) fail(HMAT_EINVAL, "NULL argument");
@@ -496,8 +516,8 @@ hmat_status hmat_sumexpr_counts(const hmat_t A, const hmat_t B, int64_t *n_lowra
     for (size_t l = 0; l < ra.size(); l++) { ra[l] = A->leaves[l].rank; rb[l] = B->leaves[l].rank; }
     Plan plan;
     build_plan(t, ra, rb, plan);
-    for (size_t l = 0; l + 1 < plan.leaf_term_off.size(); l++) {
-      n_lowrank[l] = plan.leaf_term_off[l + 1] - plan.leaf_term_off[l];
+    for (size_t l = 0; l + 1 < plan.leaf_pair_off.size(); l++) {
+      n_lowrank[l] = plan.nterm_cum[t.leaf_block[l]];
       n_hpairs[l] = plan.leaf_pair_off[l + 1] - plan.leaf_pair_off[l];
     }
   });
@@ -559,13 +579,24 @@ void Product::run() {
   Plan plan;
   build_plan(t, ra, rb, plan);
   const std::vector<double> storA = block_storage(t, A->leaves), storB = block_storage(t, B->leaves);
+  const size_t smem_cap = 200 * 1024;  // shared memory a launch may ask for per block
 
-  // term storage and jobs (a2)
-  std::vector<TermJob> jobs(plan.terms.size());
-  std::vector<int64_t> term_off(plan.terms.size());
+  // jobs of the low-rank products (a2), their storage, and the panels of products with an
+  // inadmissible factor: 0 = the H-block is one dense leaf (warp per panel), 1 = inner block with
+  // shared-memory staging, 2 = inner block with global staging
+  const int PW = panel_width();
+  int pcw_rows = 1;
+  for (const LeafDev &l : A->leaves) pcw_rows = std::max(pcw_rows, (int)l.rank);
+  for (const LeafDev &l : B->leaves) pcw_rows = std::max(pcw_rows, (int)l.rank);
+  const size_t pcw_bytes = (size_t)8 * pcw_rows * PW * es;
+  const size_t nterm = plan.terms.size();
+  std::vector<TermJob> jobs(nterm);
+  std::vector<int32_t> ff_ids;
+  std::vector<PanelDev> pk[3];
+  int pdim[3] = {0, 0, 0};
   int64_t term_elems = 0;
   double flops_terms = 0;
-  for (size_t i = 0; i < plan.terms.size(); i++) {
+  for (size_t i = 0; i < nterm; i++) {
     const PlanTerm &pt = plan.terms[i];
     const Block &cb = t.bl[pt.block];
     const int64_t mp = t.cl[cb.tau].size, np = t.cl[cb.sigma].size;
@@ -576,21 +607,31 @@ void Product::run() {
     j.rank = pt.rank;
     j.rows = (pt.type == JOB_FF_L || pt.type == JOB_HF) ? mp : np;
     j.out = term_elems;
-    term_off[i] = term_elems;
+    j.blk = pt.block;
+    j.pad = 0;
     term_elems += j.rows * j.rank;
     if (pt.type == JOB_FF_R || pt.type == JOB_FF_L) {
       const LeafDev &la = A->leaves[pt.a], &lb = B->leaves[pt.b];
       flops_terms += 2.0 * la.n * la.rank * lb.rank + 2.0 * j.rows * la.rank * lb.rank;
-    } else if (pt.type == JOB_FH) {
-      flops_terms += 2.0 * storB[pt.b] * pt.rank;
+      ff_ids.push_back((int32_t)i);
     } else {
-      flops_terms += 2.0 * storA[pt.a] * pt.rank;
+      const int hb = pt.type == JOB_HF ? pt.a : pt.b;  // the inadmissible H-block
+      flops_terms += 2.0 * (pt.type == JOB_HF ? storA[hb] : storB[hb]) * pt.rank;
+      const Block &bk = t.bl[hb];
+      const int dm = (int)t.cl[bk.tau].size, dn = (int)t.cl[bk.sigma].size;
+      int kind;
+      if (bk.kind == BK_NEAR) kind = 0;
+      else if ((size_t)(dm + dn) * PW * es + pcw_bytes <= smem_cap) kind = 1;
+      else kind = 2;
+      for (int q0 = 0; q0 < pt.rank; q0 += PW) pk[kind].push_back(PanelDev{(int32_t)i, q0});
+      pdim[kind] = std::max(pdim[kind], std::max(dm, dn));
     }
   }
-  S.n_terms = (int64_t)plan.terms.size();
-  S.n_lr_refs = (int64_t)plan.leaf_terms.size();
+  S.n_terms = (int64_t)nterm;
   S.n_hpairs = (int64_t)plan.leaf_pairs.size();
   S.flops_terms = flops_terms;
+  std::vector<int2> blk_terms(t.bl.size());
+  for (size_t b = 0; b < t.bl.size(); b++) blk_terms[b] = make_int2(plan.blk_term_lo[b], plan.blk_term_hi[b]);
 
   // ---- targets
   struct Tgt {
@@ -599,20 +640,49 @@ void Product::run() {
   };
   std::vector<Tgt> far, nearv;
   std::vector<double> elems_b(t.leaf_block.size(), 0.0);
+  int64_t lr_refs = 0;
   for (size_t l = 0; l < t.leaf_block.size(); l++) {
     const LeafDev &lc = A->leaves[l];
-    double e = 0;
-    for (int64_t q = plan.leaf_term_off[l]; q < plan.leaf_term_off[l + 1]; q++)
-      e += (double)plan.terms[plan.leaf_terms[q]].rank * (lc.m + lc.n);
+    const int b = t.leaf_block[l];
+    double e = (double)plan.rank_cum[b] * (lc.m + lc.n);
+    lr_refs += plan.nterm_cum[b];
     for (int64_t q = plan.leaf_pair_off[l]; q < plan.leaf_pair_off[l + 1]; q++)
       e += storA[plan.leaf_pairs[q].blkA] + storB[plan.leaf_pairs[q].blkB];
     elems_b[l] = e;
     (lc.rank < 0 ? nearv : far).push_back(Tgt{(int)l, e});
   }
-  std::stable_sort(far.begin(), far.end(), [](const Tgt &a, const Tgt &b) { return a.cost > b.cost; });
+  S.n_lr_refs = lr_refs;
+  // Size classes of the application kernel: 0 = panels staged in global memory (targets too
+  // large for shared memory), 1 = large targets staged in shared memory, 2 = targets of at most
+  // 128 rows and columns (small shared footprint, full occupancy). Far targets are ordered by
+  // class, then by decreasing cost, so every class is one contiguous launch.
+  const int P = apply_panel_width(p);
+  int cw_rows = std::max(t.leaf_size, pcw_rows);
+  for (const PlanTerm &pt : plan.terms) cw_rows = std::max(cw_rows, (int)pt.rank);
+  const size_t cw_bytes = (size_t)8 * cw_rows * P * es;
+  std::vector<int> rho_inner(t.leaf_block.size(), 0), klass(t.leaf_block.size(), 2);
+  auto is_leaf_pair = [&](const PairDev &pr) {
+    return t.bl[pr.blkA].kind == BK_NEAR && t.bl[pr.blkB].kind == BK_NEAR;
+  };
+  for (const Tgt &g : far) {
+    const int l = g.leaf;
+    int rho = 0;
+    for (int64_t q = plan.leaf_pair_off[l]; q < plan.leaf_pair_off[l + 1]; q++)
+      if (!is_leaf_pair(plan.leaf_pairs[q]))
+        rho = std::max(rho, (int)t.cl[t.bl[plan.leaf_pairs[q].blkA].sigma].size);
+    rho_inner[l] = rho;
+    const LeafDev &lc = A->leaves[l];
+    const int dmax = std::max(std::max((int)lc.m, (int)lc.n), rho);
+    if (dmax <= 128) klass[l] = 2;
+    else if ((size_t)3 * dmax * P * es + cw_bytes <= smem_cap) klass[l] = 1;
+    else klass[l] = 0;
+  }
+  std::stable_sort(far.begin(), far.end(), [&](const Tgt &a, const Tgt &b) {
+    if (klass[a.leaf] != klass[b.leaf]) return klass[a.leaf] < klass[b.leaf];
+    return a.cost > b.cost;
+  });
 
-  auto make_targets = [&](const std::vector<Tgt> &tv, std::vector<TargetDev> &tg, std::vector<int32_t> &tterms,
-                          std::vector<PairDev> &tpairs) {
+  auto make_targets = [&](const std::vector<Tgt> &tv, std::vector<TargetDev> &tg, std::vector<PairDev> &tpairs) {
     tg.resize(tv.size());
     for (size_t i = 0; i < tv.size(); i++) {
       const int l = tv[i].leaf;
@@ -624,22 +694,29 @@ void Product::run() {
       d.m = lc.m;
       d.n = lc.n;
       d.leaf = l;
-      d.term_lo = (int32_t)tterms.size();
-      for (int64_t q = plan.leaf_term_off[l]; q < plan.leaf_term_off[l + 1]; q++) tterms.push_back(plan.leaf_terms[q]);
-      d.term_hi = (int32_t)tterms.size();
+      d.blk = t.leaf_block[l];
+      d.nterms = plan.nterm_cum[d.blk];
       d.pair_lo = (int32_t)tpairs.size();
-      for (int64_t q = plan.leaf_pair_off[l]; q < plan.leaf_pair_off[l + 1]; q++) tpairs.push_back(plan.leaf_pairs[q]);
+      for (int64_t q = plan.leaf_pair_off[l]; q < plan.leaf_pair_off[l + 1]; q++)
+        if (is_leaf_pair(plan.leaf_pairs[q])) tpairs.push_back(plan.leaf_pairs[q]);
+      d.pair_mid = (int32_t)tpairs.size();
+      for (int64_t q = plan.leaf_pair_off[l]; q < plan.leaf_pair_off[l + 1]; q++)
+        if (!is_leaf_pair(plan.leaf_pairs[q])) tpairs.push_back(plan.leaf_pairs[q]);
       d.pair_hi = (int32_t)tpairs.size();
     }
   };
   std::vector<TargetDev> ftg, ntg;
-  std::vector<int32_t> fterms, nterms;
   std::vector<PairDev> fpairs, npairs;
-  make_targets(far, ftg, fterms, fpairs);
-  make_targets(nearv, ntg, nterms, npairs);
-  // scratch offsets for far targets
-  int64_t qw_elems = 0, xy_elems = 0, z_elems = 0;
-  for (TargetDev &d : ftg) {
+  make_targets(far, ftg, fpairs);
+  make_targets(nearv, ntg, npairs);
+  // scratch offsets for far targets and the per-class launch parameters
+  int64_t qw_elems = 0, xy_elems = 0, stage_elems = 0;
+  struct ClassLaunch {
+    int first = 0, count = 0, dmax = 0, rho = 0;
+  } cls[3];
+  for (int c = 0; c < 3; c++) cls[c].first = -1;
+  for (size_t i = 0; i < ftg.size(); i++) {
+    TargetDev &d = ftg[i];
     const int mn = std::min(d.m, d.n);
     d.rmax = std::min(max_rank, ((mn + p + p - 1) / p) * p);
     if (d.rmax < p) d.rmax = p;
@@ -651,10 +728,22 @@ void Product::run() {
     d.x_off = xy_elems;
     d.y_off = xy_elems;  // separate buffers x and y share the same offsets
     xy_elems += mx * p;
-    int rho_max = 0;
-    for (int q = d.pair_lo; q < d.pair_hi; q++) rho_max = std::max(rho_max, (int)t.cl[t.bl[fpairs[q].blkA].sigma].size);
-    d.z_off = z_elems;
-    z_elems += (int64_t)rho_max * p;
+    const int c = klass[d.leaf];
+    ClassLaunch &cl = cls[c];
+    if (cl.first < 0) cl.first = (int)i;
+    cl.count++;
+    cl.dmax = std::max(cl.dmax, (int)mx);
+    cl.rho = std::max(cl.rho, rho_inner[d.leaf]);
+    if (c == 0) {
+      d.stage_off = stage_elems;
+      stage_elems += ((int64_t)d.m + d.n + rho_inner[d.leaf]) * P;
+    }
+  }
+  std::vector<PanelDev> panels;
+  int pfirst[3];
+  for (int k = 0; k < 3; k++) {
+    pfirst[k] = (int)panels.size();
+    panels.insert(panels.end(), pk[k].begin(), pk[k].end());
   }
   S.ms_plan = now_ms() - t_plan0;
 
@@ -665,49 +754,53 @@ void Product::run() {
     ~EvGuard() { for (int i = 0; i < 6; i++) cudaEventDestroy(e[i]); }
   } evg{ev};
 
-  // ---- a2: low-rank products
+  // ---- a2: low-rank products. Far x far products (small) run one job per block; products with
+  // an inadmissible factor run as panels of up to panel_width() columns.
   ck(cudaEventRecord(ev[0], s), "event");
   DevBuf d_termbuf(es * std::max<int64_t>(term_elems, 1), s);
-  ck(cudaMemsetAsync(d_termbuf.p, 0, es * std::max<int64_t>(term_elems, 1), s), "memset terms");
-  DevBuf d_jobs = upload(jobs, s);
-  ck(launch_term_jobs(cprec, d_jobs.as<TermJob>(), (int)jobs.size(), A->d_leaves.as<LeafDev>(),
-                      B->d_leaves.as<LeafDev>(), t.d_blocks, dataA, dataB, d_termbuf.p, s),
-     "low-rank products");
-  std::vector<TermDev> tdev(plan.terms.size());
-  for (size_t i = 0; i < plan.terms.size(); i++) {
-    const PlanTerm &pt = plan.terms[i];
-    const Block &cb = t.bl[pt.block];
-    TermDev &d = tdev[i];
-    d.row0 = t.cl[cb.tau].begin;
-    d.col0 = t.cl[cb.sigma].begin;
-    d.ldL = t.cl[cb.tau].size;
-    d.ldR = t.cl[cb.sigma].size;
-    d.rank = pt.rank;
-    const char *tb = (const char *)d_termbuf.p + es * term_off[i];
-    const char *da = (const char *)dataA, *db = (const char *)dataB;
-    switch (pt.type) {
-      case JOB_FF_R:
-      case JOB_FH:
-        d.L = da + es * A->leaves[pt.a].off_u;
-        d.R = tb;
-        break;
-      case JOB_FF_L:
-      case JOB_HF:
-      default:
-        d.L = tb;
-        d.R = db + es * B->leaves[pt.b].off_v;
-        break;
-    }
+  DevBuf d_jobs = upload(jobs, s), d_ffids = upload(ff_ids, s), d_panels = upload(panels, s);
+  DevBuf d_blkterms = upload(blk_terms, s);
+  DevBuf d_terms(sizeof(TermDev) * std::max<size_t>(nterm, 1), s);
+  ck(launch_make_terms(cprec, d_jobs.as<TermJob>(), (int)nterm, t.d_blocks, A->d_leaves.as<LeafDev>(),
+                       B->d_leaves.as<LeafDev>(), dataA, dataB, d_termbuf.p, d_terms.as<TermDev>(), s),
+     "term table");
+  ck(launch_term_jobs(cprec, d_jobs.as<TermJob>(), d_ffids.as<int32_t>(), (int)ff_ids.size(),
+                      A->d_leaves.as<LeafDev>(), B->d_leaves.as<LeafDev>(), t.d_blocks, dataA, dataB, d_termbuf.p, s),
+     "far x far products");
+  int64_t launches = 1 + (ff_ids.empty() ? 0 : 1);
+  const int64_t pstride = (int64_t)2 * pdim[2] * PW;
+  DevBuf d_pstage(es * std::max<int64_t>(pstride * (int64_t)pk[2].size(), 1), s);
+  for (int k = 0; k < 3; k++) {
+    if (pk[k].empty()) continue;
+    PanelArgs pa{};
+    pa.first = pfirst[k];
+    pa.count = (int)pk[k].size();
+    pa.smem_in = pa.smem_out = pdim[k];
+    pa.smem_cw = pcw_rows;
+    pa.gstage = k == 2 ? 1 : 0;
+    pa.stage_stride = pstride;
+    pa.stage_base = d_pstage.p;
+    pa.panels = d_panels.as<PanelDev>();
+    pa.jobs = d_jobs.as<TermJob>();
+    pa.blocks = t.d_blocks;
+    pa.leafA = A->d_leaves.as<LeafDev>();
+    pa.leafB = B->d_leaves.as<LeafDev>();
+    pa.dataA = dataA;
+    pa.dataB = dataB;
+    pa.terms = d_termbuf.p;
+    ck(launch_panels(cprec, pa, k == 0, s), "low-rank products (panels)");
+    launches++;
   }
-  DevBuf d_terms = upload(tdev, s);
+  S.n_ff_jobs = (int64_t)ff_ids.size();
+  S.n_panels = (int64_t)panels.size();
   ck(cudaEventRecord(ev[1], s), "event");
 
   // ---- a3..a7: adaptive randomized truncation of all far targets
   const int nf = (int)ftg.size();
-  DevBuf d_ftg = upload(ftg, s), d_fterms = upload(fterms, s), d_fpairs = upload(fpairs, s);
+  DevBuf d_ftg = upload(ftg, s), d_fpairs = upload(fpairs, s);
   DevBuf d_qw(sizeof(double) * std::max<int64_t>(qw_elems, 1), s);
   DevBuf d_x(es * std::max<int64_t>(xy_elems, 1), s), d_y(es * std::max<int64_t>(xy_elems, 1), s);
-  DevBuf d_z(es * std::max<int64_t>(z_elems, 1), s);
+  DevBuf d_stage(es * std::max<int64_t>(stage_elems, 1), s);
   std::vector<TargetState> st0(nf);
   for (auto &x : st0) {
     std::memset(&x, 0, sizeof(x));
@@ -717,7 +810,7 @@ void Product::run() {
   DevBuf d_cnt(sizeof(int32_t), s);
   ApplyArgs aa{};
   aa.tg = d_ftg.as<TargetDev>();
-  aa.tg_terms = d_fterms.as<int32_t>();
+  aa.blk_terms = d_blkterms.as<int2>();
   aa.terms = d_terms.as<TermDev>();
   aa.pairs = d_fpairs.as<PairDev>();
   aa.blocks = t.d_blocks;
@@ -728,18 +821,45 @@ void Product::run() {
   aa.state = d_st.as<TargetState>();
   aa.x_base = d_x.p;
   aa.y_base = d_y.p;
-  aa.z_base = d_z.p;
+  aa.stage_base = d_stage.p;
   aa.p = p;
-  aa.ntarget = nf;
   const double eps = o->eps;
   const double eps_stop = 0.5 * eps;
   int rounds = 0;
+  // events around every application pass (S and S^T), read after the stream synchronises
+  std::vector<cudaEvent_t> aev;
+  struct AevGuard {
+    std::vector<cudaEvent_t> &v;
+    ~AevGuard() { for (auto e : v) cudaEventDestroy(e); }
+  } aevg{aev};
+  auto timed_apply = [&](bool trans) {
+    cudaEvent_t e0, e1;
+    ck(cudaEventCreate(&e0), "event");
+    aev.push_back(e0);
+    ck(cudaEventCreate(&e1), "event");
+    aev.push_back(e1);
+    ck(cudaEventRecord(e0, s), "event");
+    for (int c = 0; c < 3; c++) {
+      if (cls[c].count == 0) continue;
+      ApplyArgs ac = aa;
+      ac.first = cls[c].first;
+      ac.count = cls[c].count;
+      ac.smem_in = ac.smem_out = cls[c].dmax;
+      ac.smem_rho = cls[c].rho;
+      ac.smem_cw = cw_rows;
+      ac.gstage = c == 0 ? 1 : 0;
+      ck(launch_apply(cprec, trans, ac, s), trans ? "apply S^T" : "apply S");
+      launches++;
+    }
+    ck(cudaEventRecord(e1, s), "event");
+  };
   for (int round = 0; round < max_rounds && nf > 0; round++) {
     rounds++;
     ck(launch_gaussian(cprec, aa.tg, aa.state, nf, p, o->seed, round, d_x.p, s), "gaussian");
-    ck(launch_apply(cprec, false, aa, s), "apply S");
+    timed_apply(false);
     ck(launch_orth(cprec, aa.tg, aa.state, nf, p, eps, d_y.p, d_qw.as<double>(), d_x.p, round, s), "orth");
-    ck(launch_apply(cprec, true, aa, s), "apply S^T");
+    timed_apply(true);
+    launches += 3;
     ck(cudaMemsetAsync(d_cnt.p, 0, sizeof(int32_t), s), "memset");
     ck(launch_absorb_w(cprec, aa.tg, aa.state, nf, p, eps_stop, d_y.p, d_qw.as<double>(), round, max_rounds,
                        d_cnt.as<int32_t>(), s),
@@ -750,10 +870,22 @@ void Product::run() {
     if (act == 0) break;
   }
   ck(cudaEventRecord(ev[2], s), "event");
-  ck(launch_final(aa.tg, aa.state, nf, eps, d_qw.as<double>(), s), "final truncation");
   std::vector<TargetState> st(nf);
   if (nf) ck(cudaMemcpyAsync(st.data(), d_st.p, sizeof(TargetState) * nf, cudaMemcpyDeviceToHost, s), "states");
-  ck(cudaStreamSynchronize(s), "final");
+  ck(cudaStreamSynchronize(s), "states");
+  {
+    std::vector<int32_t> ids_small, ids_big;
+    for (int i = 0; i < nf; i++) (st[i].r <= 32 ? ids_small : ids_big).push_back(i);
+    DevBuf d_ids_small = upload(ids_small, s), d_ids_big = upload(ids_big, s);
+    ck(launch_final(aa.tg, aa.state, d_ids_small.as<int32_t>(), (int)ids_small.size(), true, eps, d_qw.as<double>(),
+                    s),
+       "final truncation (warp)");
+    ck(launch_final(aa.tg, aa.state, d_ids_big.as<int32_t>(), (int)ids_big.size(), false, eps, d_qw.as<double>(), s),
+       "final truncation (block)");
+    launches += (ids_small.empty() ? 0 : 1) + (ids_big.empty() ? 0 : 1);
+    if (nf) ck(cudaMemcpyAsync(st.data(), d_st.p, sizeof(TargetState) * nf, cudaMemcpyDeviceToHost, s), "states");
+    ck(cudaStreamSynchronize(s), "final");
+  }
   ck(cudaEventRecord(ev[3], s), "event");
 
   // ---- C: leaves, storage, write far factors, evaluate near leaves (a8, a9)
@@ -779,13 +911,23 @@ void Product::run() {
   C->d_leaves = upload(C->leaves, s);
   ck(launch_write_far(cprec, aa.tg, aa.state, nf, d_qw.as<double>(), C->d_leaves.as<LeafDev>(), C->d_data.p, s),
      "write far");
-  DevBuf d_ntg = upload(ntg, s), d_nterms = upload(nterms, s), d_npairs = upload(npairs, s);
-  ck(launch_near_eval(cprec, d_ntg.as<TargetDev>(), (int)ntg.size(), d_nterms.as<int32_t>(), d_terms.as<TermDev>(),
+  DevBuf d_ntg = upload(ntg, s), d_npairs = upload(npairs, s);
+  ck(launch_near_eval(cprec, d_ntg.as<TargetDev>(), (int)ntg.size(), d_blkterms.as<int2>(), d_terms.as<TermDev>(),
                       d_npairs.as<PairDev>(), t.d_blocks, A->d_leaves.as<LeafDev>(), B->d_leaves.as<LeafDev>(), dataA,
                       dataB, C->d_leaves.as<LeafDev>(), C->d_data.p, s),
      "near field");
+  launches += (nf > 0 ? 1 : 0) + (ntg.empty() ? 0 : 1);
   ck(cudaEventRecord(ev[4], s), "event");
   ck(cudaStreamSynchronize(s), "product");
+  double ms_apply = 0;
+  for (size_t i = 0; i + 1 < aev.size(); i += 2) {
+    float x = 0;
+    cudaEventElapsedTime(&x, aev[i], aev[i + 1]);
+    ms_apply += x;
+  }
+  S.ms_apply = ms_apply;
+  S.apply_launches = (int64_t)aev.size() / 2;
+  S.launches = launches;
 
   float ms = 0;
   cudaEventElapsedTime(&ms, ev[0], ev[1]);
@@ -798,20 +940,22 @@ void Product::run() {
   S.ms_near = ms;
   S.rounds = rounds;
   S.not_converged = notconv;
-  double fa = 0, ba = 0, fn = 0;
+  double fa = 0, ba = 0, fn = 0, bu = 0;
   for (size_t i = 0; i < ftg.size(); i++) {
     const double e = elems_b[ftg[i].leaf];
     const int cols = st[i].r;  // columns that went through both passes
     fa += 2.0 * e * 2.0 * cols;
     ba += e * 2.0 * ((cols + p - 1) / p) * es;
+    const double launches_b = 2.0 * std::max(1, st[i].nfwd);
+    bu += launches_b * (e + (double)(ftg[i].m + ftg[i].n) * p) * es;
   }
   for (const TargetDev &d : ntg) {
-    double kk = 0;
-    for (int q = d.term_lo; q < d.term_hi; q++) kk += tdev[nterms[q]].rank;
+    const double kk = (double)plan.rank_cum[d.blk];
     double rr = 0;
     for (int q = d.pair_lo; q < d.pair_hi; q++) rr += t.cl[t.bl[npairs[q].blkA].sigma].size;
     fn += 2.0 * d.m * d.n * (kk + rr);
   }
+  S.bytes_apply_use = bu;
   S.flops_apply = fa;
   S.bytes_apply = ba;
   S.flops_near = fn;

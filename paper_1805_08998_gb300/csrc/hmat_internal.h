@@ -27,6 +27,7 @@ struct BlockDev {
   int64_t row, col;     // permuted begin of tau, sigma
   int32_t m, n;
   int32_t leaf_lo, leaf_hi;  // depth-first leaf range of the subtree
+  int32_t parent, pad;       // parent block (-1 at the root)
 };
 
 // A low-rank term L R^T of a sum-expression, on the block tau' x sigma' where it was created.
@@ -53,6 +54,28 @@ struct TermJob {
   int32_t rank;   // width of the new factor
   int64_t out;    // element offset of the new factor in the term buffer
   int64_t rows;   // rows of the new factor
+  int32_t blk;    // block tau' x sigma' where the term was created
+  int32_t pad;
+};
+
+// a2 panels: up to panel_width() columns of one product with an inadmissible factor:
+// HF jobs: Out = A|tau' x rho' U_b (columns of U_b), FH jobs: Out = B|rho' x sigma'^T V_a.
+struct PanelDev {
+  int32_t job;           // index into the TermJob table
+  int32_t q0;            // first column of the job's new factor in this panel
+};
+struct PanelArgs {
+  int first, count;
+  int smem_in, smem_out, smem_cw;
+  int gstage;
+  int64_t stage_stride;  // elements of global staging per panel (gstage)
+  void *stage_base;
+  const PanelDev *panels;
+  const TermJob *jobs;
+  const BlockDev *blocks;
+  const LeafDev *leafA, *leafB;
+  const void *dataA, *dataB;
+  void *terms;
 };
 
 struct PairDev {
@@ -62,13 +85,15 @@ struct PairDev {
 struct TargetDev {
   int64_t row, col;     // permuted begin of tau, sigma
   int32_t m, n;
-  int32_t term_lo, term_hi;
-  int32_t pair_lo, pair_hi;
+  int32_t blk, nterms;  // the target's block; its low-rank terms are those created at blk and
+                        // its ancestors (ranges blk_terms[.] along the parent links)
+  int32_t pair_lo, pair_mid, pair_hi;  // [lo, mid): pairs of two dense leaves; [mid, hi): inner blocks
   int32_t leaf;         // leaf id in the block tree
   int32_t rmax;         // basis capacity (columns of Q and W)
+  int32_t pad;
   int64_t q_off, w_off; // FP64 basis Q (m x rmax) and W (n x rmax)
-  int64_t y_off, x_off; // per-round sample buffers (m x p) and (n x p), element type T
-  int64_t z_off;        // H-pair intermediate (m x p), element type T
+  int64_t y_off, x_off; // per-round sample buffers (max(m,n) x p each), element type T
+  int64_t stage_off;    // global staging panels (targets too large for shared memory)
 };
 
 // Per-target state of the adaptive range finder.
@@ -77,14 +102,21 @@ struct TargetState {
   int32_t active;       // 1 while sampling continues
   int32_t p_new;        // columns kept in the current round
   int32_t rank;         // final rank
+  int32_t nfwd;         // rounds in which the target was sampled
+  int32_t pad;
   double nrm2;          // ||W||_F^2 over all columns so far (= ||Q Q^T S||_F^2)
   double est2;          // ||Y||_F^2 / p of the first round (scale for dropping)
   double tail2;         // discarded energy in the final truncation
 };
 
 struct ApplyArgs {
+  int first, count;      // targets [first, first + count) of tg form this launch
+  int smem_in, smem_out, smem_rho, smem_cw;  // staged rows: input, output, H-pair intermediate,
+                                             // per-warp scratch
+  int gstage;            // 1: stage panels in global memory (stage_base + stage_off)
+  void *stage_base;
   const TargetDev *tg;
-  const int32_t *tg_terms;
+  const int2 *blk_terms;  // per block: [lo, hi) of the terms created at it
   const TermDev *terms;
   const PairDev *pairs;
   const BlockDev *blocks;
@@ -93,9 +125,7 @@ struct ApplyArgs {
   TargetState *state;
   void *y_base;          // per-target In/Out regions (element type T), offsets in TargetDev
   void *x_base;
-  void *z_base;
   int p;                 // columns this round
-  int ntarget;
 };
 
 // ---- launch wrappers (hmat_kernels.cu); all return cudaError_t of the launch ----
@@ -109,23 +139,32 @@ cudaError_t launch_aca(int kernel, const double *pts, int dim, const LeafDev *le
 cudaError_t launch_aca_compact(int prec, const LeafDev *leaves, const int32_t *far_ids, int nfar,
                                const double *scratch, const int64_t *scratch_off, int kmax,
                                void *data, cudaStream_t s);
-cudaError_t launch_term_jobs(int prec, const TermJob *jobs, int njobs, const LeafDev *leafA,
+cudaError_t launch_term_jobs(int prec, const TermJob *jobs, const int32_t *ids, int njobs, const LeafDev *leafA,
                              const LeafDev *leafB, const BlockDev *blocks, const void *dataA,
                              const void *dataB, void *terms, cudaStream_t s);
-cudaError_t launch_near_eval(int prec, const TargetDev *tg, int ntg, const int32_t *tg_terms,
+cudaError_t launch_make_terms(int prec, const TermJob *jobs, int njobs, const BlockDev *blocks,
+                              const LeafDev *leafA, const LeafDev *leafB, const void *dataA,
+                              const void *dataB, const void *termbuf, TermDev *terms, cudaStream_t s);
+cudaError_t launch_near_eval(int prec, const TargetDev *tg, int ntg, const int2 *blk_terms,
                              const TermDev *terms, const PairDev *pairs, const BlockDev *blocks,
                              const LeafDev *leafA, const LeafDev *leafB, const void *dataA,
                              const void *dataB, const LeafDev *leafC, void *dataC, cudaStream_t s);
 cudaError_t launch_gaussian(int prec, const TargetDev *tg, const TargetState *st, int ntg, int p,
                             uint64_t seed, int round, void *x_base, cudaStream_t s);
 cudaError_t launch_apply(int prec, bool trans, const ApplyArgs &a, cudaStream_t s);
+size_t apply_smem_bytes(int prec, int P, const ApplyArgs &a);
+cudaError_t launch_panels(int prec, const PanelArgs &a, bool leaf_kind, cudaStream_t s);
+int panel_width();
+int apply_panel_width(int p);
 cudaError_t launch_orth(int prec, const TargetDev *tg, TargetState *st, int ntg, int p, double eps,
                         void *y_base, double *qw, void *x_base, int round, cudaStream_t s);
 cudaError_t launch_absorb_w(int prec, const TargetDev *tg, TargetState *st, int ntg, int p,
                             double eps_stop, void *y_base, double *qw, int round, int max_rounds,
                             int32_t *active_count, cudaStream_t s);
-cudaError_t launch_final(const TargetDev *tg, TargetState *st, int ntg, double eps, double *qw,
-                         cudaStream_t s);
+// core truncation of the targets listed in ids: one warp per target (bases of at most 32
+// columns) or one block per target (up to 96 columns)
+cudaError_t launch_final(const TargetDev *tg, TargetState *st, const int32_t *ids, int nids, bool warp_kernel,
+                         double eps, double *qw, cudaStream_t s);
 cudaError_t launch_write_far(int prec, const TargetDev *tg, const TargetState *st, int ntg,
                              const double *qw, const LeafDev *leafC, void *dataC, cudaStream_t s);
 cudaError_t launch_convert(int prec, const void *src, double *dst, int64_t count, cudaStream_t s);

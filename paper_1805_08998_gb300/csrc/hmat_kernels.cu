@@ -8,9 +8,7 @@
 //                   of Algorithm 3 creates when one factor is far (cost: Lemma 5.1)
 //   k_near_eval     evaluate() of Algorithm 4 for near leaves: S(b) applied to the identity
 //   k_gaussian      Gaussian test matrices Omega (counter-based, splitmix64 + Box-Muller)
-//   k_apply         S(b) Omega or S(b)^T Q for every far target b in one launch: all low-rank
-//                   terms and all H-pairs of b fused in one pass (the formula for S v in
-//                   Sec. 3.3, H-pairs applied by the recursion of Algorithm 2 over leaves)
+//   k_apply         (hmat_apply.cu) S(b) Omega or S(b)^T Q for every far target b
 //   k_orth          project the new samples against the basis twice and orthonormalise them by
 //                   Gram-Schmidt twice with dropping, all in FP64 (the projection step of Alg. 8)
 //   k_absorb_w      append W_new = S^T Q_new and apply the blocked stop test eq. (truncaca)
@@ -384,14 +382,16 @@ __global__ void __launch_bounds__(NT) k_aca_compact(const LeafDev *leaves, const
 // ---------------------------------------------------------------------------------------
 
 template <typename T>
-__global__ void __launch_bounds__(NT) k_term_jobs(const TermJob *jobs, const LeafDev *leafA, const LeafDev *leafB,
-                                                  const BlockDev *blocks, const T *dataA, const T *dataB,
-                                                  T *terms) {
+__global__ void __launch_bounds__(NT) k_term_jobs(const TermJob *jobs, const int32_t *ids, const LeafDev *leafA,
+                                                  const LeafDev *leafB, const BlockDev *blocks, const T *dataA,
+                                                  const T *dataB, T *terms) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *cs, *ms, *xs;
   Smem::get((T *)smem_raw, cs, ms, xs);
-  const TermJob jb = jobs[blockIdx.x];
+  const TermJob jb = jobs[ids[blockIdx.x]];
   T *out = terms + jb.out;
+  for (int64_t o = threadIdx.x; o < jb.rows * jb.rank; o += NT) out[o] = T(0);  // outputs accumulate
+  __syncthreads();
   if (jb.type == JOB_FF_R || jb.type == JOB_FF_L) {
     const LeafDev a = leafA[jb.a], b = leafB[jb.b];
     const T *Ua = dataA + a.off_u, *Va = dataA + a.off_v;
@@ -467,7 +467,7 @@ __device__ void acc_outer(T (&acc)[4][4], const T *Lp, int64_t sl_i, int64_t sl_
 }
 
 template <typename T>
-__global__ void __launch_bounds__(NT) k_near_eval(const TargetDev *tg, const int32_t *tg_terms, const TermDev *terms,
+__global__ void __launch_bounds__(NT) k_near_eval(const TargetDev *tg, const int2 *blk_terms, const TermDev *terms,
                                                   const PairDev *pairs, const BlockDev *blocks, const LeafDev *leafA,
                                                   const LeafDev *leafB, const T *dataA, const T *dataB,
                                                   const LeafDev *leafC, T *dataC) {
@@ -484,11 +484,14 @@ __global__ void __launch_bounds__(NT) k_near_eval(const TargetDev *tg, const int
       for (int u = 0; u < 4; u++)
 #pragma unroll
         for (int v = 0; v < 4; v++) acc[u][v] = T(0);
-      for (int ti = t.term_lo; ti < t.term_hi; ti++) {
-        const TermDev tm = terms[tg_terms[ti]];
-        const T *L = (const T *)tm.L + (t.row - tm.row0) + i0;
-        const T *R = (const T *)tm.R + (t.col - tm.col0) + j0;
-        acc_outer(acc, L, 1, tm.ldL, R, 1, tm.ldR, mt, nt, tm.rank, ls, rs);
+      for (int blk = t.blk; blk >= 0; blk = blocks[blk].parent) {
+        const int2 rg = blk_terms[blk];
+        for (int ti = rg.x; ti < rg.y; ti++) {
+          const TermDev tm = terms[ti];
+          const T *L = (const T *)tm.L + (t.row - tm.row0) + i0;
+          const T *R = (const T *)tm.R + (t.col - tm.col0) + j0;
+          acc_outer(acc, L, 1, tm.ldL, R, 1, tm.ldR, mt, nt, tm.rank, ls, rs);
+        }
       }
       for (int pi = t.pair_lo; pi < t.pair_hi; pi++) {
         const PairDev pr = pairs[pi];
@@ -508,58 +511,6 @@ __global__ void __launch_bounds__(NT) k_near_eval(const TargetDev *tg, const int
         }
       __syncthreads();
     }
-}
-
-// ---------------------------------------------------------------------------------------
-// a3 / a6: sum-expression applications for all far targets
-// ---------------------------------------------------------------------------------------
-
-template <typename T, bool TRANS>
-__global__ void __launch_bounds__(NT) k_apply(ApplyArgs a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T *cs, *ms, *xs;
-  Smem::get((T *)smem_raw, cs, ms, xs);
-  const int b = blockIdx.x;
-  if (a.state[b].active == 0) return;  // uniform over the block
-  const TargetDev t = a.tg[b];
-  const int p = a.p;
-  const T *X = (const T *)a.x_base + t.x_off;
-  T *Out = (T *)a.y_base + t.y_off;
-  T *Z = (T *)a.z_base + t.z_off;
-  const int64_t ldx = TRANS ? t.m : t.n;
-  const int64_t ldo = TRANS ? t.n : t.m;
-  zero_mat(Out, ldo, (int)ldo, p);
-  // low-rank terms: Out += L (R^T X)   or   Out += R (L^T X)
-  for (int ti = t.term_lo; ti < t.term_hi; ti++) {
-    const TermDev tm = a.terms[a.tg_terms[ti]];
-    const T *L = (const T *)tm.L + (t.row - tm.row0);
-    const T *R = (const T *)tm.R + (t.col - tm.col0);
-    if (!TRANS) {
-      gemm_tn(cs, R, tm.ldR, X, ldx, t.n, tm.rank, p, ms, xs);
-      gemm_nn_acc(Out, ldo, L, tm.ldL, cs, tm.rank, t.m, tm.rank, p, xs);
-    } else {
-      gemm_tn(cs, L, tm.ldL, X, ldx, t.m, tm.rank, p, ms, xs);
-      gemm_nn_acc(Out, ldo, R, tm.ldR, cs, tm.rank, t.n, tm.rank, p, xs);
-    }
-  }
-  // H-pairs: Out += A|tau x rho (B|rho x sigma X)   or   Out += B^T (A^T X)
-  for (int pi = t.pair_lo; pi < t.pair_hi; pi++) {
-    const PairDev pr = a.pairs[pi];
-    const BlockDev ba = a.blocks[pr.blkA], bb = a.blocks[pr.blkB];
-    const int rho = ba.n;
-    zero_mat(Z, rho, rho, p);
-    if (!TRANS) {
-      hblock_apply(a.leafB, (const T *)a.dataB, bb.leaf_lo, bb.leaf_hi, bb.row, bb.col, false, X, ldx, p, Z, rho,
-                   cs, ms, xs);
-      hblock_apply(a.leafA, (const T *)a.dataA, ba.leaf_lo, ba.leaf_hi, ba.row, ba.col, false, Z, rho, p, Out, ldo,
-                   cs, ms, xs);
-    } else {
-      hblock_apply(a.leafA, (const T *)a.dataA, ba.leaf_lo, ba.leaf_hi, ba.row, ba.col, true, X, ldx, p, Z, rho,
-                   cs, ms, xs);
-      hblock_apply(a.leafB, (const T *)a.dataB, bb.leaf_lo, bb.leaf_hi, bb.row, bb.col, true, Z, rho, p, Out, ldo,
-                   cs, ms, xs);
-    }
-  }
 }
 
 // ---------------------------------------------------------------------------------------
@@ -694,6 +645,7 @@ __global__ void __launch_bounds__(NT) k_orth(const TargetDev *tg, TargetState *s
   }
   if (threadIdx.x == 0) {
     st[b].p_new = kept;
+    st[b].nfwd += 1;
     if (kept == 0) st[b].active = 0;
   }
 }
@@ -747,7 +699,8 @@ constexpr int JMAX = 96;  // max basis size handled by the Jacobi core solver (e
 // Eigen-decomposition of G = W^T W (r x r) by cyclic Jacobi with a round-robin ordering
 // (r/2 disjoint rotations per step, all applied at once), then the eps-rank: the smallest k
 // with sum_{i >= k} lambda_i <= eps^2 sum_i lambda_i; finally Q <- Q V_k and W <- W V_k in place.
-__global__ void __launch_bounds__(NT) k_final(const TargetDev *tg, TargetState *st, double eps, double *qw) {
+__global__ void __launch_bounds__(NT) k_final(const TargetDev *tg, TargetState *st, const int32_t *ids, double eps,
+                                              double *qw) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double *G = (double *)smem_raw;          // JMAX x JMAX
   double *V = G + JMAX * JMAX;             // JMAX x JMAX
@@ -755,7 +708,7 @@ __global__ void __launch_bounds__(NT) k_final(const TargetDev *tg, TargetState *
   int *pr = (int *)(cs + JMAX);            // JMAX pairing
   int *order = pr + JMAX;                  // JMAX
   __shared__ int rank_s, changed_s;
-  const int b = blockIdx.x;
+  const int b = ids[blockIdx.x];
   const TargetDev t = tg[b];
   const int r = st[b].r;
   const int64_t m = t.m, n = t.n;
@@ -889,6 +842,150 @@ __global__ void __launch_bounds__(NT) k_final(const TargetDev *tg, TargetState *
   }
 }
 
+
+// The same core truncation with one warp per target for bases of at most 32 columns (the
+// common case): Gram, round-robin Jacobi, eps-rank and the in-place rotation of Q and W, with
+// warp synchronisation only.
+constexpr int WJ = 32;
+constexpr int WF_WARPS = 4;
+struct WarpFinalSmem {
+  double G[WJ * WJ];
+  double V[WJ * WJ];
+  double co[WJ / 2], si[WJ / 2];
+  int pa[WJ / 2], pc[WJ / 2];
+  int order[WJ];
+};
+
+__global__ void __launch_bounds__(WF_WARPS * 32) k_final_warp(const TargetDev *tg, TargetState *st, const int32_t *ids,
+                                                              int nids, double eps, double *qw) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int idx = blockIdx.x * WF_WARPS + w;
+  if (idx >= nids) return;  // whole warps; no block barrier in this kernel
+  WarpFinalSmem &S = ((WarpFinalSmem *)smem_raw)[w];
+  const int b = ids[idx];
+  const TargetDev t = tg[b];
+  const int r = st[b].r;
+  const int64_t m = t.m, n = t.n;
+  double *Q = qw + t.q_off, *W = qw + t.w_off;
+  if (r == 0) {
+    if (lane == 0) { st[b].rank = 0; st[b].tail2 = 0.0; }
+    return;
+  }
+  const int rr = r + (r & 1);
+  // G = W^T W (upper triangle by pairs, mirrored)
+  for (int o = lane; o < rr * rr; o += 32) {
+    const int i = o % rr, j = o / rr;
+    S.V[i + j * WJ] = (i == j) ? 1.0 : 0.0;
+    if (i > j) continue;
+    double sum = 0.0;
+    if (i < r && j < r) {
+      const double *wi = W + (int64_t)i * n, *wj = W + (int64_t)j * n;
+      for (int64_t k = 0; k < n; k++) sum += wi[k] * wj[k];
+    }
+    S.G[i + j * WJ] = sum;
+    S.G[j + i * WJ] = sum;
+  }
+  __syncwarp();
+  const int npair = rr / 2;
+  for (int sweep = 0; sweep < 40; sweep++) {
+    bool changed = false;
+    for (int step = 0; step < rr - 1; step++) {
+      if (lane < npair) {
+        const int k = lane;
+        int a = (k == 0) ? 0 : 1 + ((k - 1 + step) % (rr - 1));
+        int c = 1 + ((rr - 2 - k + step) % (rr - 1));
+        if (a > c) { const int tmp = a; a = c; c = tmp; }
+        const double app = S.G[a + a * WJ], aqq = S.G[c + c * WJ], apq = S.G[a + c * WJ];
+        double co = 1.0, si = 0.0;
+        if (apq != 0.0 && fabs(apq) > 1e-15 * sqrt(fabs(app * aqq)) && fabs(apq) > 1e-300) {
+          const double zeta = (aqq - app) / (2.0 * apq);
+          const double tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+          co = 1.0 / sqrt(1.0 + tt * tt);
+          si = co * tt;
+          changed = true;
+        }
+        S.pa[k] = a;
+        S.pc[k] = c;
+        S.co[k] = co;
+        S.si[k] = si;
+      }
+      __syncwarp();
+      for (int o = lane; o < npair * rr; o += 32) {  // columns (G J) and V J
+        const int k = o / rr, i = o % rr;
+        const int a = S.pa[k], c = S.pc[k];
+        const double co = S.co[k], si = S.si[k];
+        const double ga = S.G[i + a * WJ], gc = S.G[i + c * WJ];
+        S.G[i + a * WJ] = co * ga - si * gc;
+        S.G[i + c * WJ] = si * ga + co * gc;
+        const double va = S.V[i + a * WJ], vc = S.V[i + c * WJ];
+        S.V[i + a * WJ] = co * va - si * vc;
+        S.V[i + c * WJ] = si * va + co * vc;
+      }
+      __syncwarp();
+      for (int o = lane; o < npair * rr; o += 32) {  // rows J^T G
+        const int k = o / rr, j = o % rr;
+        const int a = S.pa[k], c = S.pc[k];
+        const double co = S.co[k], si = S.si[k];
+        const double ga = S.G[a + j * WJ], gc = S.G[c + j * WJ];
+        S.G[a + j * WJ] = co * ga - si * gc;
+        S.G[c + j * WJ] = si * ga + co * gc;
+      }
+      __syncwarp();
+    }
+    if (!__any_sync(0xffffffffu, changed)) break;
+  }
+  int k = 0;
+  if (lane == 0) {
+    for (int i = 0; i < rr; i++) S.order[i] = i;
+    for (int i = 1; i < rr; i++) {
+      const int x = S.order[i];
+      const double lx = S.G[x + x * WJ];
+      int j = i - 1;
+      while (j >= 0 && S.G[S.order[j] + S.order[j] * WJ] < lx) { S.order[j + 1] = S.order[j]; j--; }
+      S.order[j + 1] = x;
+    }
+    double tot = 0.0;
+    for (int i = 0; i < rr; i++) tot += fmax(S.G[i + i * WJ], 0.0);
+    double tail = 0.0;
+    k = rr;
+    for (int i = rr - 1; i >= 0; i--) {
+      const double nt = tail + fmax(S.G[S.order[i] + S.order[i] * WJ], 0.0);
+      if (nt <= eps * eps * tot) { tail = nt; k = i; }
+      else break;
+    }
+    if (k > r) k = r;
+    st[b].tail2 = tail;
+  }
+  k = __shfl_sync(0xffffffffu, k, 0);
+  __syncwarp();
+  // V_k (r x k) into G's storage, then rows of Q and W rotated in place
+  for (int o = lane; o < r * k; o += 32) {
+    const int i = o % r, j = o / r;
+    S.G[i + j * WJ] = S.V[i + S.order[j] * WJ];
+  }
+  __syncwarp();
+  for (int mat = 0; mat < 2; mat++) {
+    double *M = mat == 0 ? Q : W;
+    const int64_t rows = mat == 0 ? m : n;
+    for (int64_t i = lane; i < rows; i += 32) {
+      double row[WJ];
+#pragma unroll
+      for (int q = 0; q < WJ; q++) row[q] = q < r ? M[i + (int64_t)q * rows] : 0.0;
+      for (int j = 0; j < k; j++) {
+        double sum = 0.0;
+#pragma unroll
+        for (int q = 0; q < WJ; q++) sum += row[q] * S.G[q + j * WJ];
+        M[i + (int64_t)j * rows] = sum;
+      }
+    }
+  }
+  if (lane == 0) {
+    if (st[b].rank != -2) st[b].rank = k;
+    else st[b].rank = -(k + 3);
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(NT) k_write_far(const TargetDev *tg, const TargetState *st, const double *qw,
                                                   const LeafDev *leafC, T *dataC) {
@@ -945,35 +1042,76 @@ cudaError_t launch_aca_compact(int prec, const LeafDev *leaves, const int32_t *f
   return cudaGetLastError();
 }
 
-cudaError_t launch_term_jobs(int prec, const TermJob *jobs, int njobs, const LeafDev *leafA, const LeafDev *leafB,
-                             const BlockDev *blocks, const void *dataA, const void *dataB, void *terms,
-                             cudaStream_t s) {
+cudaError_t launch_term_jobs(int prec, const TermJob *jobs, const int32_t *ids, int njobs, const LeafDev *leafA,
+                             const LeafDev *leafB, const BlockDev *blocks, const void *dataA, const void *dataB,
+                             void *terms, cudaStream_t s) {
   if (njobs == 0) return cudaSuccess;
   cudaError_t e;
   if (prec == 64) {
     const size_t sm = Smem::bytes<double>();
     if ((e = set_smem(k_term_jobs<double>, sm)) != cudaSuccess) return e;
-    k_term_jobs<double><<<njobs, NT, sm, s>>>(jobs, leafA, leafB, blocks, (const double *)dataA,
+    k_term_jobs<double><<<njobs, NT, sm, s>>>(jobs, ids, leafA, leafB, blocks, (const double *)dataA,
                                               (const double *)dataB, (double *)terms);
   } else {
     const size_t sm = Smem::bytes<float>();
     if ((e = set_smem(k_term_jobs<float>, sm)) != cudaSuccess) return e;
-    k_term_jobs<float><<<njobs, NT, sm, s>>>(jobs, leafA, leafB, blocks, (const float *)dataA,
+    k_term_jobs<float><<<njobs, NT, sm, s>>>(jobs, ids, leafA, leafB, blocks, (const float *)dataA,
                                              (const float *)dataB, (float *)terms);
   }
   return cudaGetLastError();
 }
 
-cudaError_t launch_near_eval(int prec, const TargetDev *tg, int ntg, const int32_t *tg_terms, const TermDev *terms,
+
+// TermDev of every low-rank product from its job: the created block gives the origin and the
+// leading dimensions; one factor is a stored factor of A or B, the other the new one.
+template <typename T>
+__global__ void k_make_terms(const TermJob *jobs, int njobs, const BlockDev *blocks, const LeafDev *leafA,
+                             const LeafDev *leafB, const T *dataA, const T *dataB, const T *termbuf, TermDev *terms) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= njobs) return;
+  const TermJob jb = jobs[i];
+  const BlockDev bk = blocks[jb.blk];
+  TermDev d;
+  d.row0 = bk.row;
+  d.col0 = bk.col;
+  d.ldL = bk.m;
+  d.ldR = bk.n;
+  d.rank = jb.rank;
+  d.pad = 0;
+  if (jb.type == JOB_FF_R || jb.type == JOB_FH) {
+    d.L = dataA + leafA[jb.a].off_u;
+    d.R = termbuf + jb.out;
+  } else {
+    d.L = termbuf + jb.out;
+    d.R = dataB + leafB[jb.b].off_v;
+  }
+  terms[i] = d;
+}
+
+cudaError_t launch_make_terms(int prec, const TermJob *jobs, int njobs, const BlockDev *blocks, const LeafDev *leafA,
+                              const LeafDev *leafB, const void *dataA, const void *dataB, const void *termbuf,
+                              TermDev *terms, cudaStream_t s) {
+  if (njobs == 0) return cudaSuccess;
+  const int g = (njobs + 255) / 256;
+  if (prec == 64)
+    k_make_terms<double><<<g, 256, 0, s>>>(jobs, njobs, blocks, leafA, leafB, (const double *)dataA,
+                                           (const double *)dataB, (const double *)termbuf, terms);
+  else
+    k_make_terms<float><<<g, 256, 0, s>>>(jobs, njobs, blocks, leafA, leafB, (const float *)dataA,
+                                          (const float *)dataB, (const float *)termbuf, terms);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_near_eval(int prec, const TargetDev *tg, int ntg, const int2 *blk_terms, const TermDev *terms,
                              const PairDev *pairs, const BlockDev *blocks, const LeafDev *leafA,
                              const LeafDev *leafB, const void *dataA, const void *dataB, const LeafDev *leafC,
                              void *dataC, cudaStream_t s) {
   if (ntg == 0) return cudaSuccess;
   if (prec == 64)
-    k_near_eval<double><<<ntg, NT, 0, s>>>(tg, tg_terms, terms, pairs, blocks, leafA, leafB, (const double *)dataA,
+    k_near_eval<double><<<ntg, NT, 0, s>>>(tg, blk_terms, terms, pairs, blocks, leafA, leafB, (const double *)dataA,
                                            (const double *)dataB, leafC, (double *)dataC);
   else
-    k_near_eval<float><<<ntg, NT, 0, s>>>(tg, tg_terms, terms, pairs, blocks, leafA, leafB, (const float *)dataA,
+    k_near_eval<float><<<ntg, NT, 0, s>>>(tg, blk_terms, terms, pairs, blocks, leafA, leafB, (const float *)dataA,
                                           (const float *)dataB, leafC, (float *)dataC);
   return cudaGetLastError();
 }
@@ -985,31 +1123,6 @@ cudaError_t launch_gaussian(int prec, const TargetDev *tg, const TargetState *st
     k_gaussian<double><<<ntg, NT, 0, s>>>(tg, st, p, seed, round, (double *)x_base);
   else
     k_gaussian<float><<<ntg, NT, 0, s>>>(tg, st, p, seed, round, (float *)x_base);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_apply(int prec, bool trans, const ApplyArgs &a, cudaStream_t s) {
-  if (a.ntarget == 0) return cudaSuccess;
-  cudaError_t e;
-  if (prec == 64) {
-    const size_t sm = Smem::bytes<double>();
-    if (!trans) {
-      if ((e = set_smem(k_apply<double, false>, sm)) != cudaSuccess) return e;
-      k_apply<double, false><<<a.ntarget, NT, sm, s>>>(a);
-    } else {
-      if ((e = set_smem(k_apply<double, true>, sm)) != cudaSuccess) return e;
-      k_apply<double, true><<<a.ntarget, NT, sm, s>>>(a);
-    }
-  } else {
-    const size_t sm = Smem::bytes<float>();
-    if (!trans) {
-      if ((e = set_smem(k_apply<float, false>, sm)) != cudaSuccess) return e;
-      k_apply<float, false><<<a.ntarget, NT, sm, s>>>(a);
-    } else {
-      if ((e = set_smem(k_apply<float, true>, sm)) != cudaSuccess) return e;
-      k_apply<float, true><<<a.ntarget, NT, sm, s>>>(a);
-    }
-  }
   return cudaGetLastError();
 }
 
@@ -1036,12 +1149,19 @@ cudaError_t launch_absorb_w(int prec, const TargetDev *tg, TargetState *st, int 
   return cudaGetLastError();
 }
 
-cudaError_t launch_final(const TargetDev *tg, TargetState *st, int ntg, double eps, double *qw, cudaStream_t s) {
-  if (ntg == 0) return cudaSuccess;
-  const size_t sm = sizeof(double) * (2 * JMAX * JMAX + JMAX) + sizeof(int) * 2 * JMAX;
+cudaError_t launch_final(const TargetDev *tg, TargetState *st, const int32_t *ids, int nids, bool warp_kernel,
+                         double eps, double *qw, cudaStream_t s) {
+  if (nids == 0) return cudaSuccess;
   cudaError_t e;
-  if ((e = set_smem(k_final, sm)) != cudaSuccess) return e;
-  k_final<<<ntg, NT, sm, s>>>(tg, st, eps, qw);
+  if (warp_kernel) {
+    const size_t sm = sizeof(WarpFinalSmem) * WF_WARPS;
+    if ((e = set_smem(k_final_warp, sm)) != cudaSuccess) return e;
+    k_final_warp<<<(nids + WF_WARPS - 1) / WF_WARPS, WF_WARPS * 32, sm, s>>>(tg, st, ids, nids, eps, qw);
+  } else {
+    const size_t sm = sizeof(double) * (2 * JMAX * JMAX + JMAX) + sizeof(int) * 2 * JMAX;
+    if ((e = set_smem(k_final, sm)) != cudaSuccess) return e;
+    k_final<<<nids, NT, sm, s>>>(tg, st, ids, eps, qw);
+  }
   return cudaGetLastError();
 }
 

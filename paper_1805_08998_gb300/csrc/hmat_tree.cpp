@@ -107,6 +107,7 @@ struct Builder {
       for (int i = 0; i < 2; i++)
         for (int j = 0; j < 2; j++) {
           const int c = block(t.cl[tau].child[i], t.cl[sigma].child[j]);
+          t.bl[c].parent = id;
           t.bl[id].child[k++] = c;
         }
       t.bl[id].nchild = 4;
@@ -166,65 +167,83 @@ struct Planner {
   const Tree &t;
   const std::vector<int32_t> &rA, &rB;
   Plan &plan;
-  std::vector<int32_t> stack;  // low-rank terms of the current block (ids)
+  std::vector<PairDev> pool;  // pairs of the blocks on the current path, innermost last
+  // compact copies of the block tree for the hot loop
+  std::vector<int32_t> child;  // 4 per block
+  std::vector<int8_t> kind;
+  std::vector<int32_t> leaf;
+  std::vector<int8_t> cidx;    // per block: (index of tau among its parent's children) * 2 + sigma's
 
-  static int child_index(const Tree &t, int parent_cluster, int child_cluster) {
-    return t.cl[parent_cluster].child[0] == child_cluster ? 0 : 1;
+  void prepare() {
+    const size_t nb = t.bl.size();
+    child.resize(nb * 4);
+    kind.resize(nb);
+    leaf.resize(nb);
+    cidx.assign(nb, 0);
+    for (size_t b = 0; b < nb; b++) {
+      const Block &bk = t.bl[b];
+      for (int c = 0; c < 4; c++) child[b * 4 + c] = bk.child[c];
+      kind[b] = (int8_t)bk.kind;
+      leaf[b] = bk.leaf;
+      if (bk.kind == BK_INNER)
+        for (int c = 0; c < bk.nchild; c++) cidx[bk.child[c]] = (int8_t)c;  // children are tau'-major
+    }
   }
 
-  void visit(int b, const std::vector<PairDev> &pairs) {
-    const Block &bk = t.bl[b];
-    if (bk.kind != BK_INNER) {
-      const int leaf = bk.leaf;
-      plan.leaf_term_off[leaf] = (int64_t)plan.leaf_terms.size();
-      plan.leaf_terms.insert(plan.leaf_terms.end(), stack.begin(), stack.end());
-      plan.leaf_pair_off[leaf] = (int64_t)plan.leaf_pairs.size();
-      plan.leaf_pairs.insert(plan.leaf_pairs.end(), pairs.begin(), pairs.end());
+  // pairs of block b are pool[p0, p1)
+  void visit(int b, size_t p0, size_t p1) {
+    if (kind[b] != BK_INNER) {
+      const int lf = leaf[b];
+      plan.leaf_pair_off[lf] = (int64_t)plan.leaf_pairs.size();
+      plan.leaf_pairs.insert(plan.leaf_pairs.end(), pool.begin() + p0, pool.begin() + p1);
       return;
     }
-    for (int c = 0; c < bk.nchild; c++) {
-      const int cb = bk.child[c];
-      const int ti = child_index(t, bk.tau, t.bl[cb].tau);
-      const int si = child_index(t, bk.sigma, t.bl[cb].sigma);
-      const size_t mark = stack.size();
-      std::vector<PairDev> np;
-      np.reserve(pairs.size() * 2);
-      for (const PairDev &pr : pairs) {
-        const Block &ba = t.bl[pr.blkA], &bb = t.bl[pr.blkB];
-        // tau x rho and rho x sigma are inner blocks (pairs of inner blocks only reach here)
+    for (int c = 0; c < 4; c++) {
+      const int cb = child[b * 4 + c];
+      const int ti = c >> 1, si = c & 1;  // tau'-major order of the children
+      plan.blk_term_lo[cb] = (int32_t)plan.terms.size();
+      int64_t rsum = 0;
+      const size_t q0 = pool.size();
+      for (size_t q = p0; q < p1; q++) {
+        const PairDev pr = pool[q];
+        const int32_t *ca = &child[(size_t)pr.blkA * 4], *cbb = &child[(size_t)pr.blkB * 4];
         for (int ri = 0; ri < 2; ri++) {
-          const int a2 = ba.child[ti * 2 + ri];   // tau' x rho'
-          const int b2 = bb.child[ri * 2 + si];   // rho' x sigma'
-          const Block &x = t.bl[a2], &y = t.bl[b2];
-          if (x.kind == BK_FAR || y.kind == BK_FAR) {
+          const int a2 = ca[ti * 2 + ri];   // tau' x rho'
+          const int b2 = cbb[ri * 2 + si];  // rho' x sigma'
+          const int kx = kind[a2], ky = kind[b2];
+          if (kx == BK_FAR || ky == BK_FAR) {
             PlanTerm tm;
             tm.block = cb;
-            if (x.kind == BK_FAR && y.kind == BK_FAR) {
-              const int ka = rA[x.leaf], kb = rB[y.leaf];
+            if (kx == BK_FAR && ky == BK_FAR) {
+              const int ka = rA[leaf[a2]], kb = rB[leaf[b2]];
               tm.type = ka <= kb ? JOB_FF_R : JOB_FF_L;
-              tm.a = x.leaf;
-              tm.b = y.leaf;
+              tm.a = leaf[a2];
+              tm.b = leaf[b2];
               tm.rank = ka <= kb ? ka : kb;
-            } else if (x.kind == BK_FAR) {
+            } else if (kx == BK_FAR) {
               tm.type = JOB_FH;
-              tm.a = x.leaf;
+              tm.a = leaf[a2];
               tm.b = b2;
-              tm.rank = rA[x.leaf];
+              tm.rank = rA[leaf[a2]];
             } else {
               tm.type = JOB_HF;
               tm.a = a2;
-              tm.b = y.leaf;
-              tm.rank = rB[y.leaf];
+              tm.b = leaf[b2];
+              tm.rank = rB[leaf[b2]];
             }
-            stack.push_back((int32_t)plan.terms.size());
+            rsum += tm.rank;
             plan.terms.push_back(tm);
           } else {
-            np.push_back(PairDev{a2, b2});
+            pool.push_back(PairDev{a2, b2});
           }
         }
       }
-      visit(cb, np);
-      stack.resize(mark);
+      plan.blk_term_hi[cb] = (int32_t)plan.terms.size();
+      plan.nterm_cum[cb] = plan.nterm_cum[b] + (plan.blk_term_hi[cb] - plan.blk_term_lo[cb]);
+      plan.rank_cum[cb] = plan.rank_cum[b] + rsum;
+      const size_t q1 = pool.size();
+      visit(cb, q0, q1);
+      pool.resize(q0);
     }
   }
 };
@@ -232,16 +251,21 @@ struct Planner {
 }  // namespace
 
 void build_plan(const Tree &t, const std::vector<int32_t> &rankA, const std::vector<int32_t> &rankB, Plan &plan) {
-  const size_t nleaf = t.leaf_block.size();
+  const size_t nleaf = t.leaf_block.size(), nb = t.bl.size();
   plan.terms.clear();
-  plan.leaf_terms.clear();
+  plan.terms.reserve(nb * 24);
   plan.leaf_pairs.clear();
-  plan.leaf_term_off.assign(nleaf + 1, 0);
+  plan.leaf_pairs.reserve(nleaf * 8);
+  plan.blk_term_lo.assign(nb, 0);
+  plan.blk_term_hi.assign(nb, 0);
+  plan.nterm_cum.assign(nb, 0);
+  plan.rank_cum.assign(nb, 0);
   plan.leaf_pair_off.assign(nleaf + 1, 0);
-  Planner pl{t, rankA, rankB, plan, {}};
-  std::vector<PairDev> root{PairDev{0, 0}};
-  pl.visit(0, root);
-  plan.leaf_term_off[nleaf] = (int64_t)plan.leaf_terms.size();
+  Planner pl{t, rankA, rankB, plan, {}, {}, {}, {}, {}};
+  pl.prepare();
+  pl.pool.reserve(1 << 16);
+  pl.pool.push_back(PairDev{0, 0});  // S(I, I) = S_H(I, I) = {(A|I x I, B|I x I)}
+  pl.visit(0, 0, 1);
   plan.leaf_pair_off[nleaf] = (int64_t)plan.leaf_pairs.size();
 }
 

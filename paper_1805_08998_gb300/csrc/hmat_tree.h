@@ -19,6 +19,7 @@ enum BlockKind : int { BK_INNER = 0, BK_FAR = 1, BK_NEAR = 2 };
 
 struct Block {
   int tau = -1, sigma = -1, kind = BK_INNER, level = 0;
+  int parent = -1;
   int child[4] = {-1, -1, -1, -1};
   int nchild = 0;
   int leaf = -1;               // depth-first leaf number (leaves only)
@@ -53,13 +54,16 @@ struct PlanTerm {
   int block;           // block tau' x sigma' where the term was created
 };
 
+// The low-rank terms of S_R(b) are the terms created (by the restriction into b) at b and at
+// every ancestor of b; the planner stores the terms created at a block contiguously, so a
+// target's terms are the ranges of the blocks on its path to the root.
 struct Plan {
-  std::vector<PlanTerm> terms;
-  // per leaf: term ids and pairs (CSR)
-  std::vector<int64_t> leaf_term_off;   // nleaf + 1
-  std::vector<int32_t> leaf_terms;
+  std::vector<PlanTerm> terms;          // grouped by creating block
+  std::vector<int32_t> blk_term_lo, blk_term_hi;  // per block: its created terms
+  std::vector<int32_t> nterm_cum;       // per block: number of terms of S_R(block)
+  std::vector<int64_t> rank_cum;        // per block: sum of their ranks
   std::vector<int64_t> leaf_pair_off;   // nleaf + 1
-  std::vector<PairDev> leaf_pairs;
+  std::vector<PairDev> leaf_pairs;      // S_H(leaf)
 };
 
 // rankA/rankB: per leaf ranks of the two factors (-1 for dense leaves).

@@ -26,6 +26,7 @@ MODE_F64, MODE_MIXED = 0, 1
 # every symbol include/hmat.h declares
 EXPORTS = ["hmat_points", "hmat_build", "hmat_multiply", "hmat_to_dense", "hmat_leaf_count", "hmat_leaf_info",
            "hmat_leaf_get", "hmat_permutation", "hmat_stats", "hmat_sumexpr_counts", "hmat_destroy",
+           "hmat_data_bytes", "hmat_data_get",
            "hmat_last_error", "hmat_set_allocator"]
 
 
@@ -61,7 +62,10 @@ class Stats(ctypes.Structure):
                 ("flops_apply", ctypes.c_double), ("flops_terms", ctypes.c_double),
                 ("flops_near", ctypes.c_double), ("bytes_apply", ctypes.c_double),
                 ("ms_plan", ctypes.c_double), ("ms_terms", ctypes.c_double), ("ms_near", ctypes.c_double),
-                ("ms_sample", ctypes.c_double), ("ms_final", ctypes.c_double)]
+                ("ms_sample", ctypes.c_double), ("ms_final", ctypes.c_double),
+                ("ms_apply", ctypes.c_double), ("apply_launches", ctypes.c_int64),
+                ("bytes_apply_use", ctypes.c_double), ("launches", ctypes.c_int64),
+                ("n_ff_jobs", ctypes.c_int64), ("n_panels", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -93,12 +97,14 @@ def lib():
     L.hmat_permutation.argtypes = [_P, _PI64]
     L.hmat_stats.argtypes = [_P, ctypes.POINTER(Stats)]
     L.hmat_sumexpr_counts.argtypes = [_P, _P, _PI64, _PI64]
+    L.hmat_data_bytes.argtypes = [_P, _PI64]
+    L.hmat_data_get.argtypes = [_P, _P, _I64]
     L.hmat_destroy.argtypes = [_P]
     L.hmat_destroy.restype = None
     L.hmat_last_error.restype = ctypes.c_char_p
     for name in ["hmat_points", "hmat_build", "hmat_multiply", "hmat_to_dense", "hmat_leaf_count",
                  "hmat_leaf_info", "hmat_leaf_get", "hmat_permutation", "hmat_stats", "hmat_sumexpr_counts",
-                 "hmat_set_allocator"]:
+                 "hmat_set_allocator", "hmat_data_bytes", "hmat_data_get"]:
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -175,6 +181,20 @@ class HMatrix:
         perm = np.zeros(n, np.int64)
         _check(lib().hmat_permutation(self._h, perm.ctypes.data_as(_PI64)))
         return perm
+
+    def data_bytes(self) -> int:
+        n = ctypes.c_int64()
+        _check(lib().hmat_data_bytes(self._h, ctypes.byref(n)))
+        return n.value
+
+    def data_get(self, out) -> None:
+        """Copy the packed factor buffer into `out` (a host buffer: numpy array or a pinned
+        torch tensor's data_ptr() with its byte size given as a (ptr, nbytes) tuple)."""
+        if isinstance(out, tuple):
+            ptr, nbytes = out
+        else:
+            ptr, nbytes = out.ctypes.data, out.nbytes
+        _check(lib().hmat_data_get(self._h, ctypes.c_void_p(ptr), nbytes))
 
     def stats(self) -> dict:
         s = Stats()

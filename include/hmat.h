@@ -82,7 +82,7 @@ typedef struct {
                           1: learned proposal (reserved; currently treated as 0) */
   int max_rank;        /* cap on the sampled basis per block (0 = default 96) */
   int max_rounds;      /* cap on adaptive rounds (0 = default max_rank / block_width + 1) */
-  int block_width;     /* columns added per adaptive round (0 = default 8; <= 32) */
+  int block_width;     /* columns added per adaptive round (0 = default 8; <= 16) */
   uint64_t seed;       /* seed of the Gaussian test matrices (counter-based, splitmix64) */
 } hmat_mult_opts;
 

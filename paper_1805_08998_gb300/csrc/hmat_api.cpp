@@ -4,6 +4,8 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <limits>
 #include <memory>
@@ -539,6 +541,24 @@ struct Product {
   void run();
 };
 
+// HMAT_CHECK_FINITE=1: after each phase of a product, scan its outputs for NaN/Inf and report
+// the first bad entry on stderr (a debugging aid; off by default).
+bool check_finite_enabled() {
+  const char *e = std::getenv("HMAT_CHECK_FINITE");
+  return e && e[0] == '1';
+}
+
+void check_finite(int prec, const void *x, int64_t count, const char *what, cudaStream_t s) {
+  if (!check_finite_enabled() || count == 0) return;
+  DevBuf d(sizeof(unsigned long long), s);
+  ck(cudaMemsetAsync(d.p, 0xff, sizeof(unsigned long long), s), "check");
+  ck(launch_find_nonfinite(prec, x, count, d.as<unsigned long long>(), s), "check");
+  unsigned long long h = 0;
+  ck(cudaMemcpyAsync(&h, d.p, sizeof(h), cudaMemcpyDeviceToHost, s), "check");
+  ck(cudaStreamSynchronize(s), "check");
+  if (h != ~0ull) std::fprintf(stderr, "hmat: non-finite value after %s at element %llu of %lld\n", what, h, (long long)count);
+}
+
 void Product::run() {
   const Tree &t = *A->tree;
   const double t_plan0 = now_ms();
@@ -550,7 +570,7 @@ void Product::run() {
   hmat_stats_t &S = C->stats;
   const size_t es = esize(cprec);
   const int p = o->block_width > 0 ? o->block_width : 8;
-  if (p > 32) fail(HMAT_EINVAL, "block_width must be <= 32");
+  if (p > 16) fail(HMAT_EINVAL, "block_width must be <= 16");
   int max_rank = o->max_rank > 0 ? o->max_rank : 96;
   if (max_rank > 96) fail(HMAT_EINVAL, "max_rank must be <= 96");
   if (max_rank < p) max_rank = p;
@@ -592,8 +612,11 @@ void Product::run() {
   const size_t nterm = plan.terms.size();
   std::vector<TermJob> jobs(nterm);
   std::vector<int32_t> ff_ids;
-  std::vector<PanelDev> pk[3];
-  int pdim[3] = {0, 0, 0};
+  // panel kinds: 0 = one dense leaf; 1..NB = inner block in shared memory, by size bucket
+  // (at most 64 << (kind - 1) rows and columns); NB + 1 = inner block, global staging
+  constexpr int NB = 10;
+  std::vector<PanelDev> pk[NB + 2];
+  int pdim[NB + 2] = {0};
   int64_t term_elems = 0;
   double flops_terms = 0;
   for (size_t i = 0; i < nterm; i++) {
@@ -620,9 +643,15 @@ void Product::run() {
       const Block &bk = t.bl[hb];
       const int dm = (int)t.cl[bk.tau].size, dn = (int)t.cl[bk.sigma].size;
       int kind;
+      const int dmx = std::max(dm, dn);
       if (bk.kind == BK_NEAR) kind = 0;
-      else if ((size_t)(dm + dn) * PW * es + pcw_bytes <= smem_cap) kind = 1;
-      else kind = 2;
+      else {
+        int bkt = 1;
+        while ((64 << (bkt - 1)) < dmx && bkt < NB) bkt++;
+        const int cap = 64 << (bkt - 1);
+        if (cap >= dmx && (size_t)(2 * cap) * PW * es + pcw_bytes <= smem_cap) kind = bkt;
+        else kind = NB + 1;
+      }
       for (int q0 = 0; q0 < pt.rank; q0 += PW) pk[kind].push_back(PanelDev{(int32_t)i, q0});
       pdim[kind] = std::max(pdim[kind], std::max(dm, dn));
     }
@@ -653,14 +682,15 @@ void Product::run() {
   }
   S.n_lr_refs = lr_refs;
   // Size classes of the application kernel: 0 = panels staged in global memory (targets too
-  // large for shared memory), 1 = large targets staged in shared memory, 2 = targets of at most
-  // 128 rows and columns (small shared footprint, full occupancy). Far targets are ordered by
+  // large for shared memory); class c >= 1 = targets of at most 32 << (c - 1) rows, columns
+  // and H-pair rows, staged in shared memory sized for that bound. Far targets are ordered by
   // class, then by decreasing cost, so every class is one contiguous launch.
+  constexpr int NCLS = 12;
   const int P = apply_panel_width(p);
   int cw_rows = std::max(t.leaf_size, pcw_rows);
   for (const PlanTerm &pt : plan.terms) cw_rows = std::max(cw_rows, (int)pt.rank);
   const size_t cw_bytes = (size_t)8 * cw_rows * P * es;
-  std::vector<int> rho_inner(t.leaf_block.size(), 0), klass(t.leaf_block.size(), 2);
+  std::vector<int> rho_inner(t.leaf_block.size(), 0), klass(t.leaf_block.size(), 1);
   auto is_leaf_pair = [&](const PairDev &pr) {
     return t.bl[pr.blkA].kind == BK_NEAR && t.bl[pr.blkB].kind == BK_NEAR;
   };
@@ -673,9 +703,13 @@ void Product::run() {
     rho_inner[l] = rho;
     const LeafDev &lc = A->leaves[l];
     const int dmax = std::max(std::max((int)lc.m, (int)lc.n), rho);
-    if (dmax <= 128) klass[l] = 2;
-    else if ((size_t)3 * dmax * P * es + cw_bytes <= smem_cap) klass[l] = 1;
-    else klass[l] = 0;
+    int c = 1;
+    while ((32 << (c - 1)) < dmax && c < NCLS - 1) c++;
+    const int cap = 32 << (c - 1);
+    const int rb = apply_rows_per_lane(cap);
+    const size_t zrows = rb > 0 ? std::max(cap, 8 * cap) : cap;
+    if (cap < dmax || (size_t)(2 * cap + zrows) * P * es + cw_bytes > smem_cap) c = 0;
+    klass[l] = c;
   }
   std::stable_sort(far.begin(), far.end(), [&](const Tgt &a, const Tgt &b) {
     if (klass[a.leaf] != klass[b.leaf]) return klass[a.leaf] < klass[b.leaf];
@@ -713,8 +747,8 @@ void Product::run() {
   int64_t qw_elems = 0, xy_elems = 0, stage_elems = 0;
   struct ClassLaunch {
     int first = 0, count = 0, dmax = 0, rho = 0;
-  } cls[3];
-  for (int c = 0; c < 3; c++) cls[c].first = -1;
+  } cls[NCLS];
+  for (int c = 0; c < NCLS; c++) cls[c].first = -1;
   for (size_t i = 0; i < ftg.size(); i++) {
     TargetDev &d = ftg[i];
     const int mn = std::min(d.m, d.n);
@@ -740,8 +774,8 @@ void Product::run() {
     }
   }
   std::vector<PanelDev> panels;
-  int pfirst[3];
-  for (int k = 0; k < 3; k++) {
+  int pfirst[NB + 2];
+  for (int k = 0; k < NB + 2; k++) {
     pfirst[k] = (int)panels.size();
     panels.insert(panels.end(), pk[k].begin(), pk[k].end());
   }
@@ -768,16 +802,16 @@ void Product::run() {
                       A->d_leaves.as<LeafDev>(), B->d_leaves.as<LeafDev>(), t.d_blocks, dataA, dataB, d_termbuf.p, s),
      "far x far products");
   int64_t launches = 1 + (ff_ids.empty() ? 0 : 1);
-  const int64_t pstride = (int64_t)2 * pdim[2] * PW;
-  DevBuf d_pstage(es * std::max<int64_t>(pstride * (int64_t)pk[2].size(), 1), s);
-  for (int k = 0; k < 3; k++) {
+  const int64_t pstride = (int64_t)2 * pdim[NB + 1] * PW;
+  DevBuf d_pstage(es * std::max<int64_t>(pstride * (int64_t)pk[NB + 1].size(), 1), s);
+  for (int k = 0; k < NB + 2; k++) {
     if (pk[k].empty()) continue;
     PanelArgs pa{};
     pa.first = pfirst[k];
     pa.count = (int)pk[k].size();
     pa.smem_in = pa.smem_out = pdim[k];
     pa.smem_cw = pcw_rows;
-    pa.gstage = k == 2 ? 1 : 0;
+    pa.gstage = k == NB + 1 ? 1 : 0;
     pa.stage_stride = pstride;
     pa.stage_base = d_pstage.p;
     pa.panels = d_panels.as<PanelDev>();
@@ -793,6 +827,7 @@ void Product::run() {
   }
   S.n_ff_jobs = (int64_t)ff_ids.size();
   S.n_panels = (int64_t)panels.size();
+  check_finite(cprec, d_termbuf.p, term_elems, "low-rank products", s);
   ck(cudaEventRecord(ev[1], s), "event");
 
   // ---- a3..a7: adaptive randomized truncation of all far targets
@@ -801,6 +836,11 @@ void Product::run() {
   DevBuf d_qw(sizeof(double) * std::max<int64_t>(qw_elems, 1), s);
   DevBuf d_x(es * std::max<int64_t>(xy_elems, 1), s), d_y(es * std::max<int64_t>(xy_elems, 1), s);
   DevBuf d_stage(es * std::max<int64_t>(stage_elems, 1), s);
+  if (check_finite_enabled()) {  // the finiteness check scans whole buffers: start them at zero
+    ck(cudaMemsetAsync(d_qw.p, 0, sizeof(double) * std::max<int64_t>(qw_elems, 1), s), "memset");
+    ck(cudaMemsetAsync(d_x.p, 0, es * std::max<int64_t>(xy_elems, 1), s), "memset");
+    ck(cudaMemsetAsync(d_y.p, 0, es * std::max<int64_t>(xy_elems, 1), s), "memset");
+  }
   std::vector<TargetState> st0(nf);
   for (auto &x : st0) {
     std::memset(&x, 0, sizeof(x));
@@ -839,13 +879,15 @@ void Product::run() {
     ck(cudaEventCreate(&e1), "event");
     aev.push_back(e1);
     ck(cudaEventRecord(e0, s), "event");
-    for (int c = 0; c < 3; c++) {
+    for (int c = 0; c < NCLS; c++) {
       if (cls[c].count == 0) continue;
       ApplyArgs ac = aa;
       ac.first = cls[c].first;
       ac.count = cls[c].count;
       ac.smem_in = ac.smem_out = cls[c].dmax;
       ac.smem_rho = cls[c].rho;
+      // register-accumulating launches also keep every warp's partial output in this region
+      if (c > 0 && apply_rows_per_lane(cls[c].dmax) > 0) ac.smem_rho = std::max(ac.smem_rho, 8 * cls[c].dmax);
       ac.smem_cw = cw_rows;
       ac.gstage = c == 0 ? 1 : 0;
       ck(launch_apply(cprec, trans, ac, s), trans ? "apply S^T" : "apply S");
@@ -857,8 +899,11 @@ void Product::run() {
     rounds++;
     ck(launch_gaussian(cprec, aa.tg, aa.state, nf, p, o->seed, round, d_x.p, s), "gaussian");
     timed_apply(false);
+    check_finite(cprec, d_y.p, xy_elems, "apply S", s);
     ck(launch_orth(cprec, aa.tg, aa.state, nf, p, eps, d_y.p, d_qw.as<double>(), d_x.p, round, s), "orth");
+    check_finite(64, d_qw.p, qw_elems, "orthogonalisation", s);
     timed_apply(true);
+    check_finite(cprec, d_y.p, xy_elems, "apply S^T", s);
     launches += 3;
     ck(cudaMemsetAsync(d_cnt.p, 0, sizeof(int32_t), s), "memset");
     ck(launch_absorb_w(cprec, aa.tg, aa.state, nf, p, eps_stop, d_y.p, d_qw.as<double>(), round, max_rounds,

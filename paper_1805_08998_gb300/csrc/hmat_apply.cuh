@@ -1,0 +1,430 @@
+#pragma once
+// hmat_apply.cuh -- the sum-expression application for all far targets (a3: Y = S(b) Omega,
+// a6: W = S(b)^T Q), the dominant kernel of the product.
+//
+// For a target b = tau x sigma with sum-expression S(b) = sum_j L_j R_j^T + sum_rho A|tau x rho
+// B|rho x sigma (Sec. 3.3: S v = sum A_j (B_j^T v) + sum H_j (K_j v)), one thread block applies
+// every term of b to the p sample columns:
+//   * the input panel (Omega or Q, p columns padded to P) and the output panel are staged
+//     row-major in shared memory (or, for very large targets, in a global staging area);
+//   * each warp takes whole low-rank terms: c = R^T X by lane-per-column reductions into a
+//     private scratch, then Out += L c by lane-per-row expansions accumulated with atomics;
+//   * H-pairs of two dense leaves (the leaf level) are taken warp per pair, the intermediate
+//     B|rho x sigma X kept in the warp's scratch;
+//   * H-pairs of inner blocks walk their two subtrees (Algorithm 2), leaves split over warps,
+//     with one block barrier between the B side and the A side.
+// No block barrier separates two terms, so warps stream the factor data independently.
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "hmat_internal.h"
+
+namespace hm {
+namespace apply_detail {
+
+constexpr int AT = 256;
+constexpr int NWARP = AT / 32;
+
+template <typename T>
+__device__ __forceinline__ void acc_add(T *p, T v, bool atomic) {
+  if (atomic) atomicAdd(p, v);
+  else *p = v;
+}
+
+// out[q*osr + c*osc] (+)= sum_{i < len} M[i + q*ldm] * X[i*P + c]  for q < r, c < P (only
+// c < ncol stored). With r <= 32/G, G lanes share column q (rows split round-robin) and are
+// combined by shuffles, so narrow ranks still use the whole warp. Default strides: row-major
+// panel (osr = P, osc = 1).
+template <typename T, int P, int G, bool ATOMIC>
+__device__ __forceinline__ void warp_tn_g(T *out, const T *__restrict__ M, int64_t ldm, const T *X, int len, int r,
+                                          int64_t osr, int64_t osc, int ncol) {
+  const int lane = threadIdx.x & 31;
+  constexpr int COLS = 32 / G;
+  const int g = lane % G;
+  for (int q0 = 0; q0 < r; q0 += COLS) {
+    const int q = q0 + lane / G;
+    T acc[P];
+#pragma unroll
+    for (int c = 0; c < P; c++) acc[c] = T(0);
+    if (q < r) {
+      const T *mc = M + (int64_t)q * ldm;
+      int i = g;
+      for (; i + 3 * G < len; i += 4 * G) {
+        const T m0 = __ldg(mc + i), m1 = __ldg(mc + i + G), m2 = __ldg(mc + i + 2 * G), m3 = __ldg(mc + i + 3 * G);
+        const T *x = X + i * P;
+#pragma unroll
+        for (int c = 0; c < P; c++) {
+          T s = acc[c];
+          s += m0 * x[c];
+          s += m1 * x[G * P + c];
+          s += m2 * x[2 * G * P + c];
+          s += m3 * x[3 * G * P + c];
+          acc[c] = s;
+        }
+      }
+      for (; i < len; i += G) {
+        const T m0 = __ldg(mc + i);
+#pragma unroll
+        for (int c = 0; c < P; c++) acc[c] += m0 * X[i * P + c];
+      }
+    }
+#pragma unroll
+    for (int off = G / 2; off > 0; off >>= 1)
+#pragma unroll
+      for (int c = 0; c < P; c++) acc[c] += __shfl_down_sync(0xffffffffu, acc[c], off, G);
+    if (q < r && g == 0) {
+#pragma unroll
+      for (int c = 0; c < P; c++)
+        if (c < ncol) acc_add(out + q * osr + c * osc, acc[c], ATOMIC);
+    }
+  }
+}
+
+template <typename T, int P, bool ATOMIC>
+__device__ __forceinline__ void warp_tn(T *out, const T *__restrict__ M, int64_t ldm, const T *X, int len, int r,
+                                        int64_t osr = P, int64_t osc = 1, int ncol = P) {
+  if (r <= 4) warp_tn_g<T, P, 8, ATOMIC>(out, M, ldm, X, len, r, osr, osc, ncol);
+  else if (r <= 8) warp_tn_g<T, P, 4, ATOMIC>(out, M, ldm, X, len, r, osr, osc, ncol);
+  else if (r <= 16) warp_tn_g<T, P, 2, ATOMIC>(out, M, ldm, X, len, r, osr, osc, ncol);
+  else warp_tn_g<T, P, 1, ATOMIC>(out, M, ldm, X, len, r, osr, osc, ncol);
+}
+
+// out[i*osr + c*osc] (+)= sum_{q < r} M[i + q*ldm] * C[q*P + c]  for i < rows; lane owns rows.
+template <typename T, int P, bool ATOMIC>
+__device__ __forceinline__ void warp_nn(T *out, const T *__restrict__ M, int64_t ldm, const T *C, int rows, int r,
+                                        int64_t osr = P, int64_t osc = 1, int ncol = P) {
+  const int lane = threadIdx.x & 31;
+  for (int i0 = 0; i0 < rows; i0 += 64) {
+    const int ia = i0 + lane, ib = i0 + 32 + lane;
+    const bool va = ia < rows, vb = ib < rows;
+    T a[P], b[P];
+#pragma unroll
+    for (int c = 0; c < P; c++) { a[c] = T(0); b[c] = T(0); }
+    int q = 0;
+    for (; q + 2 <= r; q += 2) {
+      const T *m0 = M + (int64_t)q * ldm, *m1 = m0 + ldm;
+      const T x0 = va ? __ldg(m0 + ia) : T(0), y0 = vb ? __ldg(m0 + ib) : T(0);
+      const T x1 = va ? __ldg(m1 + ia) : T(0), y1 = vb ? __ldg(m1 + ib) : T(0);
+      const T *c0 = C + q * P;
+#pragma unroll
+      for (int c = 0; c < P; c++) {
+        const T u = c0[c], v = c0[P + c];
+        a[c] += x0 * u;
+        b[c] += y0 * u;
+        a[c] += x1 * v;
+        b[c] += y1 * v;
+      }
+    }
+    if (q < r) {
+      const T *m0 = M + (int64_t)q * ldm;
+      const T x0 = va ? __ldg(m0 + ia) : T(0), y0 = vb ? __ldg(m0 + ib) : T(0);
+#pragma unroll
+      for (int c = 0; c < P; c++) {
+        a[c] += x0 * C[q * P + c];
+        b[c] += y0 * C[q * P + c];
+      }
+    }
+    if (va)
+#pragma unroll
+      for (int c = 0; c < P; c++)
+        if (c < ncol) acc_add(out + ia * osr + c * osc, a[c], ATOMIC);
+    if (vb)
+#pragma unroll
+      for (int c = 0; c < P; c++)
+        if (c < ncol) acc_add(out + ib * osr + c * osc, b[c], ATOMIC);
+  }
+}
+
+// One leaf of an H-matrix block with origin (row0, col0):
+//   trans = false: Out[rows of leaf] += leaf   * X[cols of leaf]
+//   trans = true:  Out[cols of leaf] += leaf^T * X[rows of leaf]
+template <typename T, int P>
+__device__ __forceinline__ void warp_leaf(const LeafDev &lf, const T *data, bool trans, int64_t row0, int64_t col0,
+                                          const T *X, T *Out, T *cw) {
+  const int ro = (int)(lf.row - row0), co = (int)(lf.col - col0);
+  if (lf.rank < 0) {
+    const T *D = data + lf.off_u;
+    if (!trans) warp_nn<T, P, true>(Out + ro * P, D, lf.m, X + co * P, lf.m, lf.n);
+    else warp_tn<T, P, true>(Out + co * P, D, lf.m, X + ro * P, lf.m, lf.n);
+  } else if (lf.rank > 0) {
+    const T *U = data + lf.off_u, *V = data + lf.off_v;
+    if (!trans) {
+      warp_tn<T, P, false>(cw, V, lf.n, X + co * P, lf.n, lf.rank);
+      __syncwarp();
+      warp_nn<T, P, true>(Out + ro * P, U, lf.m, cw, lf.m, lf.rank);
+    } else {
+      warp_tn<T, P, false>(cw, U, lf.m, X + ro * P, lf.m, lf.rank);
+      __syncwarp();
+      warp_nn<T, P, true>(Out + co * P, V, lf.n, cw, lf.n, lf.rank);
+    }
+    __syncwarp();
+  }
+}
+
+// acc[rr][c] += sum_{q < r} M[lane + 32 rr + q*ldm] * C[q*P + c], rows < rows (lane owns rows)
+template <typename T, int P, int RB>
+__device__ __forceinline__ void warp_nn_reg(T (&acc)[RB][P], const T *__restrict__ M, int64_t ldm, const T *C, int rows,
+                                            int r) {
+  const int lane = threadIdx.x & 31;
+  for (int q = 0; q < r; q++) {
+    const T *mq = M + (int64_t)q * ldm;
+    T mv[RB];
+#pragma unroll
+    for (int rr = 0; rr < RB; rr++) {
+      const int i = lane + 32 * rr;
+      mv[rr] = i < rows ? __ldg(mq + i) : T(0);
+    }
+    const T *cq = C + q * P;
+#pragma unroll
+    for (int c = 0; c < P; c++) {
+      const T cv = cq[c];
+#pragma unroll
+      for (int rr = 0; rr < RB; rr++) acc[rr][c] += mv[rr] * cv;
+    }
+  }
+}
+
+template <typename T, int P, bool TRANS, bool GSTAGE, int RB>
+__global__ void __launch_bounds__(AT) k_apply(ApplyArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int b = a.first + blockIdx.x;
+  if (a.state[b].active == 0) return;  // uniform over the block
+  const TargetDev t = a.tg[b];
+  const int inlen = TRANS ? t.m : t.n, outlen = TRANS ? t.n : t.m;
+  T *sm = (T *)smem_raw;
+  T *Xs, *Ys, *Zs, *cwall;
+  if (GSTAGE) {
+    Xs = (T *)a.stage_base + t.stage_off;
+    Ys = Xs + (int64_t)inlen * P;
+    Zs = Ys + (int64_t)outlen * P;
+    cwall = sm;
+  } else {
+    Xs = sm;
+    Ys = Xs + a.smem_in * P;
+    Zs = Ys + a.smem_out * P;  // H-pair intermediate, or (RB > 0) the warps' partial outputs
+    cwall = Zs + a.smem_rho * P;
+  }
+  const int warp = threadIdx.x >> 5;
+  T *cw = cwall + warp * a.smem_cw * P;
+  const T *X = (const T *)a.x_base + t.x_off;  // column-major inlen x p
+  T *Out = (T *)a.y_base + t.y_off;            // column-major outlen x p
+  const int p = a.p;
+  for (int o = threadIdx.x; o < inlen * P; o += AT) {
+    const int i = o / P, c = o - i * P;
+    Xs[o] = c < p ? X[i + (int64_t)c * inlen] : T(0);
+  }
+  for (int o = threadIdx.x; o < outlen * P; o += AT) Ys[o] = T(0);
+  __syncthreads();
+
+  // low-rank terms (those created at the target's block and its ancestors), warp per term.
+  // RB > 0 (outputs of at most 32 RB rows): every warp accumulates its terms and leaf pairs in
+  // registers and the warps' partial results are summed in a fixed order; RB = 0: shared atomics.
+  constexpr int RBX = RB > 0 ? RB : 1;
+  T racc[RBX][P];
+#pragma unroll
+  for (int rr = 0; rr < RBX; rr++)
+#pragma unroll
+    for (int c = 0; c < P; c++) racc[rr][c] = T(0);
+  int base = 0;
+  for (int blk = t.blk; blk >= 0; blk = a.blocks[blk].parent) {
+    const int2 rg = a.blk_terms[blk];
+    const int cnt = rg.y - rg.x;
+    const int j0 = ((warp - base) % NWARP + NWARP) % NWARP;
+    base += cnt;
+    for (int j = j0; j < cnt; j += NWARP) {
+      const TermDev tm = a.terms[rg.x + j];
+      const T *L = (const T *)tm.L + (t.row - tm.row0);
+      const T *R = (const T *)tm.R + (t.col - tm.col0);
+      const T *red = TRANS ? L : R;   // the factor contracted with the input panel
+      const T *exp = TRANS ? R : L;   // the factor that expands into the output
+      const int64_t ldred = TRANS ? tm.ldL : tm.ldR, ldexp = TRANS ? tm.ldR : tm.ldL;
+      warp_tn<T, P, false>(cw, red, ldred, Xs, inlen, tm.rank);
+      __syncwarp();
+      if (RB > 0) warp_nn_reg<T, P, RBX>(racc, exp, ldexp, cw, outlen, tm.rank);
+      else warp_nn<T, P, true>(Ys, exp, ldexp, cw, outlen, tm.rank);
+      __syncwarp();
+    }
+  }
+
+  // H-pairs of two dense leaves, warp per pair; the intermediate lives in the warp's scratch
+  for (int pi = t.pair_lo + warp; pi < t.pair_mid; pi += NWARP) {
+    const PairDev pr = a.pairs[pi];
+    const LeafDev la = a.leafA[a.blocks[pr.blkA].leaf_lo], lb = a.leafB[a.blocks[pr.blkB].leaf_lo];
+    const T *DA = (const T *)a.dataA + la.off_u;  // m x rho, ld m
+    const T *DB = (const T *)a.dataB + lb.off_u;  // rho x n, ld rho
+    const int rho = la.n;
+    if (!TRANS) {
+      warp_nn<T, P, false>(cw, DB, rho, Xs, rho, lb.n);   // cw = D_B X      (rho x P)
+      __syncwarp();
+      if (RB > 0) warp_nn_reg<T, P, RBX>(racc, DA, la.m, cw, la.m, rho);
+      else warp_nn<T, P, true>(Ys, DA, la.m, cw, la.m, rho);   // Y += D_A cw
+    } else {
+      warp_tn<T, P, false>(cw, DA, la.m, Xs, la.m, rho);  // cw = D_A^T Q    (rho x P)
+      __syncwarp();
+      warp_tn<T, P, true>(Ys, DB, rho, cw, rho, lb.n);    // W += D_B^T cw
+    }
+    __syncwarp();
+  }
+  if (RB > 0) {
+    // fixed-order sum of the warps' register partials (deterministic), through the scratch
+    T *part = Zs;  // NWARP * outlen * P entries reserved for RB > 0 launches
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int rr = 0; rr < RBX; rr++) {
+      const int i = lane + 32 * rr;
+      if (i < outlen)
+#pragma unroll
+        for (int c = 0; c < P; c++) part[(warp * outlen + i) * P + c] = racc[rr][c];
+    }
+    __syncthreads();
+    for (int o = threadIdx.x; o < outlen * P; o += AT) {
+      T v = Ys[o];
+      for (int w2 = 0; w2 < NWARP; w2++) v += part[w2 * outlen * P + o];
+      Ys[o] = v;
+    }
+    __syncthreads();
+  }
+
+  // H-pairs of inner blocks: walk the two subtrees (Algorithm 2), leaves split over warps
+  for (int pi = t.pair_mid; pi < t.pair_hi; pi++) {
+    const PairDev pr = a.pairs[pi];
+    const BlockDev ba = a.blocks[pr.blkA], bb = a.blocks[pr.blkB];
+    const int rho = ba.n;
+    __syncthreads();
+    for (int o = threadIdx.x; o < rho * P; o += AT) Zs[o] = T(0);
+    __syncthreads();
+    if (!TRANS) {
+      for (int l = bb.leaf_lo + warp; l < bb.leaf_hi; l += NWARP)
+        warp_leaf<T, P>(a.leafB[l], (const T *)a.dataB, false, bb.row, bb.col, Xs, Zs, cw);
+      __syncthreads();
+      for (int l = ba.leaf_lo + warp; l < ba.leaf_hi; l += NWARP)
+        warp_leaf<T, P>(a.leafA[l], (const T *)a.dataA, false, ba.row, ba.col, Zs, Ys, cw);
+    } else {
+      for (int l = ba.leaf_lo + warp; l < ba.leaf_hi; l += NWARP)
+        warp_leaf<T, P>(a.leafA[l], (const T *)a.dataA, true, ba.row, ba.col, Xs, Zs, cw);
+      __syncthreads();
+      for (int l = bb.leaf_lo + warp; l < bb.leaf_hi; l += NWARP)
+        warp_leaf<T, P>(a.leafB[l], (const T *)a.dataB, true, bb.row, bb.col, Zs, Ys, cw);
+    }
+  }
+  __syncthreads();
+  for (int o = threadIdx.x; o < outlen * p; o += AT) {
+    const int c = o / outlen, i = o - c * outlen;
+    Out[o] = Ys[i * P + c];
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// a2: low-rank products of Algorithm 3 with an inadmissible factor, batched by H-block.
+// A panel = up to P columns of far factors (U_b of B for products A|tau' x rho' U_b, V_a of A
+// for B|rho' x sigma'^T V_a) that meet the same H-block; each column's result goes to its own
+// term's new factor. The H-block's leaves are read once per panel.
+// ---------------------------------------------------------------------------------------
+
+// what a panel multiplies: the H-block, the direction, the input columns and the outputs
+struct PanelJob {
+  int blk;
+  bool trans;
+  int64_t src, src_ld;  // first input column (element offset into A's or B's data) and its stride
+  int64_t dst, dst_ld;  // first output column (element offset into the term buffer) and its stride
+  int ncol;
+};
+
+__device__ __forceinline__ PanelJob panel_job(const PanelArgs &a, const PanelDev &pn, int P) {
+  const TermJob jb = a.jobs[pn.job];
+  PanelJob q;
+  q.ncol = min(P, jb.rank - pn.q0);
+  q.dst_ld = jb.rows;
+  q.dst = jb.out + (int64_t)pn.q0 * jb.rows;
+  if (jb.type == JOB_HF) {  // Out = A|tau' x rho' U_b
+    const LeafDev lb = a.leafB[jb.b];
+    q.blk = jb.a;
+    q.trans = false;
+    q.src_ld = lb.m;
+    q.src = lb.off_u + (int64_t)pn.q0 * lb.m;
+  } else {  // FH: Out = B|rho' x sigma'^T V_a
+    const LeafDev la = a.leafA[jb.a];
+    q.blk = jb.b;
+    q.trans = true;
+    q.src_ld = la.n;
+    q.src = la.off_v + (int64_t)pn.q0 * la.n;
+  }
+  return q;
+}
+
+template <typename T, int P>
+__device__ __forceinline__ void panel_stage(T *Xs, const PanelJob &q, int inlen, const T *src, int lane0,
+                                            int nthreads) {
+  for (int o = lane0; o < inlen * P; o += nthreads) {
+    const int i = o / P, c = o - i * P;
+    Xs[o] = c < q.ncol ? src[q.src + (int64_t)c * q.src_ld + i] : T(0);
+  }
+}
+
+// one warp per panel whose H-block is a single dense leaf: private input and output panels in
+// shared memory, then each output column is written to its own term
+template <typename T, int P>
+__global__ void __launch_bounds__(AT) k_panel_leaf(PanelArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int pi = blockIdx.x * NWARP + warp;
+  if (pi >= a.count) return;  // whole warps only; no block barrier below
+  const PanelJob pj = panel_job(a, a.panels[a.first + pi], P);
+  const BlockDev bk = a.blocks[pj.blk];
+  const bool trans = pj.trans;
+  const LeafDev lf = (trans ? a.leafB : a.leafA)[bk.leaf_lo];
+  const T *D = (const T *)(trans ? a.dataB : a.dataA) + lf.off_u;
+  const T *src = (const T *)(trans ? a.dataA : a.dataB);
+  T *Xs = (T *)smem_raw + warp * (a.smem_in + a.smem_out) * P;
+  T *Os = Xs + a.smem_in * P;
+  const int inlen = trans ? lf.m : lf.n, outlen = trans ? lf.n : lf.m;
+  panel_stage<T, P>(Xs, pj, inlen, src, lane, 32);
+  __syncwarp();
+  if (!trans) warp_nn<T, P, false>(Os, D, lf.m, Xs, lf.m, lf.n);   // Os = D X
+  else warp_tn<T, P, false>(Os, D, lf.m, Xs, lf.m, lf.n);          // Os = D^T X
+  __syncwarp();
+  T *out = (T *)a.terms;
+  for (int c = 0; c < pj.ncol; c++) {
+    const int64_t dst = pj.dst + (int64_t)c * pj.dst_ld;
+    for (int i = lane; i < outlen; i += 32) out[dst + i] = Os[i * P + c];
+  }
+}
+
+// one block per panel of an inner H-block; leaves split over warps, shared-memory atomics
+template <typename T, int P, bool GSTAGE>
+__global__ void __launch_bounds__(AT) k_panel(PanelArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const PanelJob pj = panel_job(a, a.panels[a.first + blockIdx.x], P);
+  const BlockDev bk = a.blocks[pj.blk];
+  const bool trans = pj.trans;
+  const int inlen = trans ? bk.m : bk.n, outlen = trans ? bk.n : bk.m;
+  T *Xs, *Os, *cwall;
+  if (GSTAGE) {
+    Xs = (T *)a.stage_base + (int64_t)blockIdx.x * a.stage_stride;
+    Os = Xs + (int64_t)inlen * P;
+    cwall = (T *)smem_raw;
+  } else {
+    Xs = (T *)smem_raw;
+    Os = Xs + a.smem_in * P;
+    cwall = Os + a.smem_out * P;
+  }
+  const int warp = threadIdx.x >> 5;
+  T *cw = cwall + warp * a.smem_cw * P;
+  const T *src = (const T *)(trans ? a.dataA : a.dataB);
+  panel_stage<T, P>(Xs, pj, inlen, src, threadIdx.x, AT);
+  for (int o = threadIdx.x; o < outlen * P; o += AT) Os[o] = T(0);
+  __syncthreads();
+  const LeafDev *leaves = trans ? a.leafB : a.leafA;
+  const T *data = (const T *)(trans ? a.dataB : a.dataA);
+  for (int l = bk.leaf_lo + warp; l < bk.leaf_hi; l += NWARP)
+    warp_leaf<T, P>(leaves[l], data, trans, bk.row, bk.col, Xs, Os, cw);
+  __syncthreads();
+  T *out = (T *)a.terms;
+  for (int o = threadIdx.x; o < outlen * pj.ncol; o += AT) {
+    const int c = o / outlen, i = o - c * outlen;
+    out[pj.dst + (int64_t)c * pj.dst_ld + i] = Os[i * P + c];
+  }
+}
+
+}  // namespace apply_detail
+}  // namespace hm

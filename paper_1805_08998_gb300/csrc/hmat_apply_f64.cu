@@ -1,0 +1,14 @@
+// hmat_apply_f64.cu -- the application and panel kernels instantiated for double elements.
+#include "hmat_apply_launch.cuh"
+
+namespace hm {
+
+cudaError_t launch_apply_f64(int P, bool trans, const ApplyArgs &a, cudaStream_t s) {
+  return apply_detail::launch_apply_t<double>(P, trans, a, s);
+}
+
+cudaError_t launch_panels_f64(const PanelArgs &a, bool leaf_kind, cudaStream_t s) {
+  return apply_detail::launch_panels_t<double>(a, leaf_kind, s);
+}
+
+}  // namespace hm

@@ -1,0 +1,72 @@
+// hmat_apply_launch.cuh -- launch helpers of the application and panel kernels, instantiated
+// once per element type (hmat_apply_f32.cu, hmat_apply_f64.cu) so the two compile in parallel.
+#pragma once
+#include "hmat_apply.cuh"
+
+namespace hm {
+namespace apply_detail {
+
+constexpr int PANEL_P = 16;
+
+template <typename T, int P, bool TRANS, bool GSTAGE, int RB>
+static cudaError_t launch_one(const ApplyArgs &a, size_t smem, cudaStream_t s) {
+  cudaError_t e = cudaFuncSetAttribute(k_apply<T, P, TRANS, GSTAGE, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  k_apply<T, P, TRANS, GSTAGE, RB><<<a.count, AT, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+// register blocking of the launch (rows per lane; 0: shared atomics), from its largest output
+inline int rows_per_lane(int dmax) { return dmax <= 64 ? 2 : dmax <= 128 ? 4 : 0; }
+
+template <typename T, int P, bool TRANS>
+static cudaError_t launch_rb(const ApplyArgs &a, size_t smem, cudaStream_t s) {
+  if (a.gstage) return launch_one<T, P, TRANS, true, 0>(a, smem, s);
+  switch (rows_per_lane(a.smem_out)) {
+    case 2: return launch_one<T, P, TRANS, false, 2>(a, smem, s);
+    case 4: return launch_one<T, P, TRANS, false, 4>(a, smem, s);
+    default: return launch_one<T, P, TRANS, false, 0>(a, smem, s);
+  }
+}
+
+inline size_t smem_bytes(size_t es, int P, const ApplyArgs &a) {
+  const size_t cw = (size_t)NWARP * a.smem_cw * P * es;
+  return a.gstage ? cw : (size_t)(a.smem_in + a.smem_out + a.smem_rho) * P * es + cw;
+}
+
+template <typename T>
+static cudaError_t launch_apply_t(int P, bool trans, const ApplyArgs &a, cudaStream_t s) {
+  const size_t smem = smem_bytes(sizeof(T), P, a);
+  if (P == 8) return trans ? launch_rb<T, 8, true>(a, smem, s) : launch_rb<T, 8, false>(a, smem, s);
+  return trans ? launch_rb<T, 16, true>(a, smem, s) : launch_rb<T, 16, false>(a, smem, s);
+}
+
+template <typename T>
+static cudaError_t launch_panels_t(const PanelArgs &a, bool leaf_kind, cudaStream_t s) {
+  constexpr int P = PANEL_P;
+  const size_t es = sizeof(T);
+  cudaError_t e;
+  if (leaf_kind) {
+    const size_t smem = (size_t)NWARP * (a.smem_in + a.smem_out) * P * es;
+    if ((e = cudaFuncSetAttribute(k_panel_leaf<T, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
+      return e;
+    k_panel_leaf<T, P><<<(a.count + NWARP - 1) / NWARP, AT, smem, s>>>(a);
+    return cudaGetLastError();
+  }
+  const size_t cw = (size_t)NWARP * a.smem_cw * P * es;
+  const size_t smem = a.gstage ? cw : (size_t)(a.smem_in + a.smem_out) * P * es + cw;
+  if (a.gstage) {
+    if ((e = cudaFuncSetAttribute(k_panel<T, P, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
+      return e;
+    k_panel<T, P, true><<<a.count, AT, smem, s>>>(a);
+  } else {
+    if ((e = cudaFuncSetAttribute(k_panel<T, P, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
+      return e;
+    k_panel<T, P, false><<<a.count, AT, smem, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace apply_detail
+}  // namespace hm

@@ -153,6 +153,7 @@ cudaError_t launch_gaussian(int prec, const TargetDev *tg, const TargetState *st
                             uint64_t seed, int round, void *x_base, cudaStream_t s);
 cudaError_t launch_apply(int prec, bool trans, const ApplyArgs &a, cudaStream_t s);
 size_t apply_smem_bytes(int prec, int P, const ApplyArgs &a);
+int apply_rows_per_lane(int dmax);
 cudaError_t launch_panels(int prec, const PanelArgs &a, bool leaf_kind, cudaStream_t s);
 int panel_width();
 int apply_panel_width(int p);
@@ -168,5 +169,7 @@ cudaError_t launch_final(const TargetDev *tg, TargetState *st, const int32_t *id
 cudaError_t launch_write_far(int prec, const TargetDev *tg, const TargetState *st, int ntg,
                              const double *qw, const LeafDev *leafC, void *dataC, cudaStream_t s);
 cudaError_t launch_convert(int prec, const void *src, double *dst, int64_t count, cudaStream_t s);
+// atomicMin of the index of every non-finite entry into *first (initialise to ~0ull)
+cudaError_t launch_find_nonfinite(int prec, const void *x, int64_t count, unsigned long long *first, cudaStream_t s);
 
 }  // namespace hm

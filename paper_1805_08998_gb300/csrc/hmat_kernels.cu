@@ -959,10 +959,10 @@ __global__ void __launch_bounds__(WF_WARPS * 32) k_final_warp(const TargetDev *t
   }
   k = __shfl_sync(0xffffffffu, k, 0);
   __syncwarp();
-  // V_k (r x k) into G's storage, then rows of Q and W rotated in place
-  for (int o = lane; o < r * k; o += 32) {
-    const int i = o % r, j = o / r;
-    S.G[i + j * WJ] = S.V[i + S.order[j] * WJ];
+  // V_k (r x k, zero below row r) into G's storage, then rows of Q and W rotated in place
+  for (int o = lane; o < WJ * k; o += 32) {
+    const int i = o % WJ, j = o / WJ;
+    S.G[i + j * WJ] = i < r ? S.V[i + S.order[j] * WJ] : 0.0;
   }
   __syncwarp();
   for (int mat = 0; mat < 2; mat++) {
@@ -996,6 +996,21 @@ __global__ void __launch_bounds__(NT) k_write_far(const TargetDev *tg, const Tar
   for (int64_t o = threadIdx.x; o < (int64_t)t.m * k; o += NT) dataC[lc.off_u + o] = T(Q[o]);
   for (int64_t o = threadIdx.x; o < (int64_t)t.n * k; o += NT) dataC[lc.off_v + o] = T(W[o]);
   (void)st;
+}
+
+// index of the first non-finite entry (or -1) of an array, for the opt-in finiteness check
+template <typename T>
+__global__ void k_find_nonfinite(const T *x, int64_t count, unsigned long long *first) {
+  for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < count; o += (int64_t)gridDim.x * blockDim.x)
+    if (!isfinite((double)x[o])) atomicMin(first, (unsigned long long)o);
+}
+
+cudaError_t launch_find_nonfinite(int prec, const void *x, int64_t count, unsigned long long *first, cudaStream_t s) {
+  if (count == 0) return cudaSuccess;
+  const int blocks = (int)std::min<int64_t>((count + NT - 1) / NT, 152 * 16);
+  if (prec == 64) k_find_nonfinite<double><<<blocks, NT, 0, s>>>((const double *)x, count, first);
+  else k_find_nonfinite<float><<<blocks, NT, 0, s>>>((const float *)x, count, first);
+  return cudaGetLastError();
 }
 
 template <typename T>

@@ -575,6 +575,9 @@ void Product::run() {
   if (max_rank > 96) fail(HMAT_EINVAL, "max_rank must be <= 96");
   if (max_rank < p) max_rank = p;
   const int max_rounds = o->max_rounds > 0 ? o->max_rounds : max_rank / p + 1;
+  // columns of the first round (the same as later rounds unless a rank proposal widens it)
+  const int p0 = p;
+  const int pmax = std::max(p, p0);
 
   // factors in compute precision
   DevBuf convA, convB;
@@ -686,7 +689,7 @@ void Product::run() {
   // and H-pair rows, staged in shared memory sized for that bound. Far targets are ordered by
   // class, then by decreasing cost, so every class is one contiguous launch.
   constexpr int NCLS = 12;
-  const int P = apply_panel_width(p);
+  const int P = apply_panel_width(pmax);
   int cw_rows = std::max(t.leaf_size, pcw_rows);
   for (const PlanTerm &pt : plan.terms) cw_rows = std::max(cw_rows, (int)pt.rank);
   const size_t cw_bytes = (size_t)8 * cw_rows * P * es;
@@ -711,9 +714,11 @@ void Product::run() {
     if (cap < dmax || (size_t)(2 * cap + zrows) * P * es + cw_bytes > smem_cap) c = 0;
     klass[l] = c;
   }
+  // within a class, depth-first leaf order: neighbouring targets share the low-rank terms of
+  // their common ancestors and the blocks of their H-pairs, which then stay in L2
   std::stable_sort(far.begin(), far.end(), [&](const Tgt &a, const Tgt &b) {
     if (klass[a.leaf] != klass[b.leaf]) return klass[a.leaf] < klass[b.leaf];
-    return a.cost > b.cost;
+    return a.leaf < b.leaf;
   });
 
   auto make_targets = [&](const std::vector<Tgt> &tv, std::vector<TargetDev> &tg, std::vector<PairDev> &tpairs) {
@@ -753,7 +758,7 @@ void Product::run() {
     TargetDev &d = ftg[i];
     const int mn = std::min(d.m, d.n);
     d.rmax = std::min(max_rank, ((mn + p + p - 1) / p) * p);
-    if (d.rmax < p) d.rmax = p;
+    if (d.rmax < pmax) d.rmax = pmax;
     d.q_off = qw_elems;
     qw_elems += (int64_t)d.m * d.rmax;
     d.w_off = qw_elems;
@@ -761,7 +766,7 @@ void Product::run() {
     const int64_t mx = std::max(d.m, d.n);
     d.x_off = xy_elems;
     d.y_off = xy_elems;  // separate buffers x and y share the same offsets
-    xy_elems += mx * p;
+    xy_elems += mx * pmax;
     const int c = klass[d.leaf];
     ClassLaunch &cl = cls[c];
     if (cl.first < 0) cl.first = (int)i;
@@ -771,6 +776,23 @@ void Product::run() {
     if (c == 0) {
       d.stage_off = stage_elems;
       stage_elems += ((int64_t)d.m + d.n + rho_inner[d.leaf]) * P;
+    }
+  }
+  // panels of one H-block next to each other (its leaves then stay in L2): counting sort by block
+  {
+    std::vector<int32_t> cnt(t.bl.size() + 1);
+    for (int k = 0; k < NB + 2; k++) {
+      if (pk[k].size() < 2) continue;
+      std::fill(cnt.begin(), cnt.end(), 0);
+      auto hblock = [&](const PanelDev &x) {
+        const TermJob &j = jobs[x.job];
+        return j.type == JOB_HF ? j.a : j.b;
+      };
+      for (const PanelDev &x : pk[k]) cnt[hblock(x) + 1]++;
+      for (size_t b = 1; b < cnt.size(); b++) cnt[b] += cnt[b - 1];
+      std::vector<PanelDev> sorted(pk[k].size());
+      for (const PanelDev &x : pk[k]) sorted[cnt[hblock(x)]++] = x;
+      pk[k].swap(sorted);
     }
   }
   std::vector<PanelDev> panels;
@@ -897,10 +919,12 @@ void Product::run() {
   };
   for (int round = 0; round < max_rounds && nf > 0; round++) {
     rounds++;
-    ck(launch_gaussian(cprec, aa.tg, aa.state, nf, p, o->seed, round, d_x.p, s), "gaussian");
+    const int pr = round == 0 ? p0 : p;  // columns sampled this round
+    aa.p = pr;
+    ck(launch_gaussian(cprec, aa.tg, aa.state, nf, pr, o->seed, round, d_x.p, s), "gaussian");
     timed_apply(false);
     check_finite(cprec, d_y.p, xy_elems, "apply S", s);
-    ck(launch_orth(cprec, aa.tg, aa.state, nf, p, eps, d_y.p, d_qw.as<double>(), d_x.p, round, s), "orth");
+    ck(launch_orth(cprec, aa.tg, aa.state, nf, pr, eps, d_y.p, d_qw.as<double>(), d_x.p, round, s), "orth");
     check_finite(64, d_qw.p, qw_elems, "orthogonalisation", s);
     timed_apply(true);
     check_finite(cprec, d_y.p, xy_elems, "apply S^T", s);

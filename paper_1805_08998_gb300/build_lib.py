@@ -64,7 +64,7 @@ def build(verbose: bool = False, ptxas_v: bool = False) -> str:
             sys.stdout.write(o)
     if jobs or not os.path.exists(LIB):
         tmp = LIB + ".tmp"
-        _run([NVCC, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"])
+        _run([NVCC, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-lpthread"])
         os.replace(tmp, LIB)
     return LIB
 

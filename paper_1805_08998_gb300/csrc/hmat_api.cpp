@@ -2,6 +2,8 @@
 // product (Algorithm 4 driven level-free: all far targets of the whole tree are truncated
 // together by the blocked adaptive range finder, all near targets evaluated together).
 #include <algorithm>
+#include <array>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -11,6 +13,7 @@
 #include <memory>
 #include <stdexcept>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -126,6 +129,20 @@ DevBuf upload(const std::vector<T> &v, cudaStream_t s) {
   DevBuf b(sizeof(T) * std::max<size_t>(v.size(), 1), s);
   if (!v.empty()) ck(cudaMemcpyAsync(b.p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, s), "upload");
   return b;
+}
+
+// run fn(0 .. count-1) on up to 16 host threads
+template <typename F>
+void parallel_for(size_t count, F &&fn) {
+  const unsigned hw = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+  std::atomic<size_t> next{0};
+  auto worker = [&]() {
+    for (size_t i = next++; i < count; i = next++) fn(i);
+  };
+  std::vector<std::thread> th;
+  for (unsigned k = 1; k < std::min<size_t>(hw, count); k++) th.emplace_back(worker);
+  worker();
+  for (auto &x : th) x.join();
 }
 
 double now_ms() {
@@ -559,9 +576,26 @@ void check_finite(int prec, const void *x, int64_t count, const char *what, cuda
   if (h != ~0ull) std::fprintf(stderr, "hmat: non-finite value after %s at element %llu of %lld\n", what, h, (long long)count);
 }
 
+// HMAT_TRACE=1: print the host-side phases of a product with their wall times to stderr.
+struct Trace {
+  bool on;
+  double t0, last;
+  Trace() : on(false), t0(now_ms()), last(t0) {
+    const char *e = std::getenv("HMAT_TRACE");
+    on = e && e[0] == '1';
+  }
+  void mark(const char *what) {
+    if (!on) return;
+    const double t = now_ms();
+    std::fprintf(stderr, "hmat trace: %-28s %8.2f ms (total %8.2f)\n", what, t - last, t - t0);
+    last = t;
+  }
+};
+
 void Product::run() {
   const Tree &t = *A->tree;
   const double t_plan0 = now_ms();
+  Trace tr;
   C = std::make_unique<hmat_s>();
   C->tree = A->tree;
   C->stream = s;
@@ -599,8 +633,12 @@ void Product::run() {
   // ---- a1: symbolic restriction (Algorithm 3) over the tree
   std::vector<int32_t> ra(A->leaves.size()), rb(B->leaves.size());
   for (size_t l = 0; l < ra.size(); l++) { ra[l] = A->leaves[l].rank; rb[l] = B->leaves[l].rank; }
-  Plan plan;
+  // host tables of the product are kept between calls (thread-local), so their memory is mapped
+  static thread_local Plan plan_tl;
+  static thread_local std::vector<TermJob> jobs_tl;
+  Plan &plan = plan_tl;
   build_plan(t, ra, rb, plan);
+  tr.mark("plan (Algorithm 3)");
   const std::vector<double> storA = block_storage(t, A->leaves), storB = block_storage(t, B->leaves);
   const size_t smem_cap = 200 * 1024;  // shared memory a launch may ask for per block
 
@@ -613,58 +651,178 @@ void Product::run() {
   for (const LeafDev &l : B->leaves) pcw_rows = std::max(pcw_rows, (int)l.rank);
   const size_t pcw_bytes = (size_t)8 * pcw_rows * PW * es;
   const size_t nterm = plan.terms.size();
-  std::vector<TermJob> jobs(nterm);
+  std::vector<TermJob> &jobs = jobs_tl;
+  jobs.resize(nterm);
   std::vector<int32_t> ff_ids;
   // panel kinds: 0 = one dense leaf; 1..NB = inner block in shared memory, by size bucket
   // (at most 64 << (kind - 1) rows and columns); NB + 1 = inner block, global staging
   constexpr int NB = 10;
-  std::vector<PanelDev> pk[NB + 2];
+  static thread_local std::vector<PanelDev> pk_tl[NB + 2];
+  std::vector<PanelDev> *pk = pk_tl;
+  for (int k = 0; k < NB + 2; k++) pk[k].clear();
   int pdim[NB + 2] = {0};
   int64_t term_elems = 0;
   double flops_terms = 0;
-  for (size_t i = 0; i < nterm; i++) {
-    const PlanTerm &pt = plan.terms[i];
-    const Block &cb = t.bl[pt.block];
-    const int64_t mp = t.cl[cb.tau].size, np = t.cl[cb.sigma].size;
-    TermJob &j = jobs[i];
-    j.type = pt.type;
-    j.a = pt.a;
-    j.b = pt.b;
-    j.rank = pt.rank;
-    j.rows = (pt.type == JOB_FF_L || pt.type == JOB_HF) ? mp : np;
-    j.out = term_elems;
-    j.blk = pt.block;
-    j.pad = 0;
-    term_elems += j.rows * j.rank;
-    if (pt.type == JOB_FF_R || pt.type == JOB_FF_L) {
-      const LeafDev &la = A->leaves[pt.a], &lb = B->leaves[pt.b];
-      flops_terms += 2.0 * la.n * la.rank * lb.rank + 2.0 * j.rows * la.rank * lb.rank;
-      ff_ids.push_back((int32_t)i);
-    } else {
+  {
+    // two passes over chunks of the terms on a thread pool, with the serial order preserved:
+    // (1) per chunk: storage, flops, far x far count, panels per kind; (2) fill at the offsets
+    struct Chunk {
+      int64_t elems = 0, nff = 0;
+      double flops = 0;
+      int64_t npk[NB + 2] = {0};
+      int pd[NB + 2] = {0};
+    };
+    const size_t nch = std::max<size_t>(1, std::min<size_t>(64, nterm / 4096 + 1));
+    std::vector<Chunk> ch(nch);
+    auto range = [&](size_t c) { return std::make_pair(nterm * c / nch, nterm * (c + 1) / nch); };
+    auto kind_of = [&](const PlanTerm &pt, int &dmx) {
       const int hb = pt.type == JOB_HF ? pt.a : pt.b;  // the inadmissible H-block
-      flops_terms += 2.0 * (pt.type == JOB_HF ? storA[hb] : storB[hb]) * pt.rank;
       const Block &bk = t.bl[hb];
       const int dm = (int)t.cl[bk.tau].size, dn = (int)t.cl[bk.sigma].size;
-      int kind;
-      const int dmx = std::max(dm, dn);
-      if (bk.kind == BK_NEAR) kind = 0;
-      else {
-        int bkt = 1;
-        while ((64 << (bkt - 1)) < dmx && bkt < NB) bkt++;
-        const int cap = 64 << (bkt - 1);
-        if (cap >= dmx && (size_t)(2 * cap) * PW * es + pcw_bytes <= smem_cap) kind = bkt;
-        else kind = NB + 1;
+      dmx = std::max(dm, dn);
+      if (bk.kind == BK_NEAR) return 0;
+      int bkt = 1;
+      while ((64 << (bkt - 1)) < dmx && bkt < NB) bkt++;
+      const int cap = 64 << (bkt - 1);
+      if (cap >= dmx && (size_t)(2 * cap) * PW * es + pcw_bytes <= smem_cap) return bkt;
+      return NB + 1;
+    };
+    auto rows_of = [&](const PlanTerm &pt) -> int64_t {
+      const Block &cb = t.bl[pt.block];
+      return (pt.type == JOB_FF_L || pt.type == JOB_HF) ? t.cl[cb.tau].size : t.cl[cb.sigma].size;
+    };
+    parallel_for(nch, [&](size_t c) {
+      Chunk &k = ch[c];
+      const auto r = range(c);
+      for (size_t i = r.first; i < r.second; i++) {
+        const PlanTerm &pt = plan.terms[i];
+        const int64_t rows = rows_of(pt);
+        k.elems += rows * pt.rank;
+        if (pt.type == JOB_FF_R || pt.type == JOB_FF_L) {
+          const LeafDev &la = A->leaves[pt.a], &lb = B->leaves[pt.b];
+          k.flops += 2.0 * la.n * la.rank * lb.rank + 2.0 * rows * la.rank * lb.rank;
+          k.nff++;
+        } else {
+          const int hb = pt.type == JOB_HF ? pt.a : pt.b;
+          k.flops += 2.0 * (pt.type == JOB_HF ? storA[hb] : storB[hb]) * pt.rank;
+          int dmx;
+          const int kind = kind_of(pt, dmx);
+          k.npk[kind] += (pt.rank + PW - 1) / PW;
+          k.pd[kind] = std::max(k.pd[kind], dmx);
+        }
       }
-      for (int q0 = 0; q0 < pt.rank; q0 += PW) pk[kind].push_back(PanelDev{(int32_t)i, q0});
-      pdim[kind] = std::max(pdim[kind], std::max(dm, dn));
+    });
+    std::vector<int64_t> eoff(nch + 1, 0), foff(nch + 1, 0);
+    std::vector<std::array<int64_t, NB + 2>> poff(nch + 1);
+    poff[0].fill(0);
+    for (size_t c = 0; c < nch; c++) {
+      eoff[c + 1] = eoff[c] + ch[c].elems;
+      foff[c + 1] = foff[c] + ch[c].nff;
+      flops_terms += ch[c].flops;
+      for (int k = 0; k < NB + 2; k++) {
+        poff[c + 1][k] = poff[c][k] + ch[c].npk[k];
+        pdim[k] = std::max(pdim[k], ch[c].pd[k]);
+      }
     }
+    term_elems = eoff[nch];
+    ff_ids.resize(foff[nch]);
+    for (int k = 0; k < NB + 2; k++) pk[k].resize(poff[nch][k]);
+    parallel_for(nch, [&](size_t c) {
+      const auto r = range(c);
+      int64_t e = eoff[c], f = foff[c];
+      std::array<int64_t, NB + 2> q = poff[c];
+      for (size_t i = r.first; i < r.second; i++) {
+        const PlanTerm &pt = plan.terms[i];
+        TermJob &j = jobs[i];
+        j.type = pt.type;
+        j.a = pt.a;
+        j.b = pt.b;
+        j.rank = pt.rank;
+        j.rows = rows_of(pt);
+        j.out = e;
+        j.blk = pt.block;
+        j.pad = 0;
+        e += j.rows * j.rank;
+        if (pt.type == JOB_FF_R || pt.type == JOB_FF_L) {
+          ff_ids[f++] = (int32_t)i;
+        } else {
+          int dmx;
+          const int kind = kind_of(pt, dmx);
+          for (int q0 = 0; q0 < pt.rank; q0 += PW) pk[kind][q[kind]++] = PanelDev{(int32_t)i, q0};
+        }
+      }
+    });
   }
+  tr.mark("jobs and panels");
   S.n_terms = (int64_t)nterm;
   S.n_hpairs = (int64_t)plan.leaf_pairs.size();
   S.flops_terms = flops_terms;
   std::vector<int2> blk_terms(t.bl.size());
   for (size_t b = 0; b < t.bl.size(); b++) blk_terms[b] = make_int2(plan.blk_term_lo[b], plan.blk_term_hi[b]);
 
+  tr.mark("block term ranges");
+  static thread_local std::vector<PanelDev> panels_tl;
+  std::vector<PanelDev> &panels = panels_tl;
+  panels.clear();
+  int pfirst[NB + 2];
+  for (int k = 0; k < NB + 2; k++) {
+    pfirst[k] = (int)panels.size();
+    panels.insert(panels.end(), pk[k].begin(), pk[k].end());
+  }
+  tr.mark("panel tables");
+  S.ms_plan = now_ms() - t_plan0;
+
+  cudaEvent_t ev[6];
+  for (auto &e : ev) ck(cudaEventCreate(&e), "event");
+  struct EvGuard {
+    cudaEvent_t *e;
+    ~EvGuard() { for (int i = 0; i < 6; i++) cudaEventDestroy(e[i]); }
+  } evg{ev};
+
+  // ---- a2: low-rank products. Far x far products (small) run one job per block; products with
+  // an inadmissible factor run as panels of up to panel_width() columns.
+  ck(cudaEventRecord(ev[0], s), "event");
+  DevBuf d_termbuf(es * std::max<int64_t>(term_elems, 1), s);
+  DevBuf d_jobs = upload(jobs, s), d_ffids = upload(ff_ids, s), d_panels = upload(panels, s);
+  DevBuf d_blkterms = upload(blk_terms, s);
+  DevBuf d_terms(sizeof(TermDev) * std::max<size_t>(nterm, 1), s);
+  ck(launch_make_terms(cprec, d_jobs.as<TermJob>(), (int)nterm, t.d_blocks, A->d_leaves.as<LeafDev>(),
+                       B->d_leaves.as<LeafDev>(), dataA, dataB, d_termbuf.p, d_terms.as<TermDev>(), s),
+     "term table");
+  ck(launch_term_jobs(cprec, d_jobs.as<TermJob>(), d_ffids.as<int32_t>(), (int)ff_ids.size(),
+                      A->d_leaves.as<LeafDev>(), B->d_leaves.as<LeafDev>(), t.d_blocks, dataA, dataB, d_termbuf.p, s),
+     "far x far products");
+  int64_t launches = 1 + (ff_ids.empty() ? 0 : 1);
+  const int64_t pstride = (int64_t)2 * pdim[NB + 1] * PW;
+  DevBuf d_pstage(es * std::max<int64_t>(pstride * (int64_t)pk[NB + 1].size(), 1), s);
+  for (int k = 0; k < NB + 2; k++) {
+    if (pk[k].empty()) continue;
+    PanelArgs pa{};
+    pa.first = pfirst[k];
+    pa.count = (int)pk[k].size();
+    pa.smem_in = pa.smem_out = pdim[k];
+    pa.smem_cw = pcw_rows;
+    pa.gstage = k == NB + 1 ? 1 : 0;
+    pa.stage_stride = pstride;
+    pa.stage_base = d_pstage.p;
+    pa.panels = d_panels.as<PanelDev>();
+    pa.jobs = d_jobs.as<TermJob>();
+    pa.blocks = t.d_blocks;
+    pa.leafA = A->d_leaves.as<LeafDev>();
+    pa.leafB = B->d_leaves.as<LeafDev>();
+    pa.dataA = dataA;
+    pa.dataB = dataB;
+    pa.terms = d_termbuf.p;
+    ck(launch_panels(cprec, pa, k == 0, s), "low-rank products (panels)");
+    launches++;
+  }
+  S.n_ff_jobs = (int64_t)ff_ids.size();
+  S.n_panels = (int64_t)panels.size();
+  check_finite(cprec, d_termbuf.p, term_elems, "low-rank products", s);
+  tr.mark("a2 launched");
+  ck(cudaEventRecord(ev[1], s), "event");
+
+  // host work below overlaps the low-rank products on the GPU
   // ---- targets
   struct Tgt {
     int leaf;
@@ -721,6 +879,7 @@ void Product::run() {
     return a.leaf < b.leaf;
   });
 
+  tr.mark("target classes + sort");
   auto make_targets = [&](const std::vector<Tgt> &tv, std::vector<TargetDev> &tg, std::vector<PairDev> &tpairs) {
     tg.resize(tv.size());
     for (size_t i = 0; i < tv.size(); i++) {
@@ -748,6 +907,7 @@ void Product::run() {
   std::vector<PairDev> fpairs, npairs;
   make_targets(far, ftg, fpairs);
   make_targets(nearv, ntg, npairs);
+  tr.mark("target tables");
   // scratch offsets for far targets and the per-class launch parameters
   int64_t qw_elems = 0, xy_elems = 0, stage_elems = 0;
   struct ClassLaunch {
@@ -778,80 +938,43 @@ void Product::run() {
       stage_elems += ((int64_t)d.m + d.n + rho_inner[d.leaf]) * P;
     }
   }
-  // panels of one H-block next to each other (its leaves then stay in L2): counting sort by block
-  {
-    std::vector<int32_t> cnt(t.bl.size() + 1);
-    for (int k = 0; k < NB + 2; k++) {
-      if (pk[k].size() < 2) continue;
-      std::fill(cnt.begin(), cnt.end(), 0);
-      auto hblock = [&](const PanelDev &x) {
-        const TermJob &j = jobs[x.job];
-        return j.type == JOB_HF ? j.a : j.b;
-      };
-      for (const PanelDev &x : pk[k]) cnt[hblock(x) + 1]++;
-      for (size_t b = 1; b < cnt.size(); b++) cnt[b] += cnt[b - 1];
-      std::vector<PanelDev> sorted(pk[k].size());
-      for (const PanelDev &x : pk[k]) sorted[cnt[hblock(x)]++] = x;
-      pk[k].swap(sorted);
+
+  // ---- a8 on a second stream, concurrent with the far-field rounds: C's buffer starts with the
+  // near leaves (their offsets are known now); they are evaluated into a staging buffer that is
+  // copied into C once the far ranks are known.
+  C->leaves = base_leaves(t);
+  int64_t near_elems = 0;
+  for (const TargetDev &d : ntg) {
+    LeafDev &l = C->leaves[d.leaf];
+    l.off_u = near_elems;
+    near_elems += (int64_t)l.m * l.n;
+  }
+  struct StreamGuard {
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    ~StreamGuard() {
+      if (e0) cudaEventDestroy(e0);
+      if (e1) cudaEventDestroy(e1);
+      if (st) cudaStreamDestroy(st);
     }
-  }
-  std::vector<PanelDev> panels;
-  int pfirst[NB + 2];
-  for (int k = 0; k < NB + 2; k++) {
-    pfirst[k] = (int)panels.size();
-    panels.insert(panels.end(), pk[k].begin(), pk[k].end());
-  }
-  S.ms_plan = now_ms() - t_plan0;
+  } s2;
+  ck(cudaStreamCreateWithFlags(&s2.st, cudaStreamNonBlocking), "stream");
+  ck(cudaEventCreateWithFlags(&s2.e0, cudaEventDisableTiming), "event");
+  ck(cudaEventCreateWithFlags(&s2.e1, cudaEventDisableTiming), "event");
+  // the near field's tables go up on the second stream (idle, so the copies do not wait for the
+  // products), then that stream waits for the products
+  DevBuf d_near(es * std::max<int64_t>(near_elems, 1), s2.st);
+  DevBuf d_near_leaves = upload(C->leaves, s2.st);
+  DevBuf d_ntg = upload(ntg, s2.st), d_npairs = upload(npairs, s2.st);
+  ck(cudaEventRecord(s2.e0, s), "event");
+  ck(cudaStreamWaitEvent(s2.st, s2.e0, 0), "stream wait");
+  ck(launch_near_eval(cprec, d_ntg.as<TargetDev>(), (int)ntg.size(), d_blkterms.as<int2>(), d_terms.as<TermDev>(),
+                      d_npairs.as<PairDev>(), t.d_blocks, A->d_leaves.as<LeafDev>(), B->d_leaves.as<LeafDev>(), dataA,
+                      dataB, d_near_leaves.as<LeafDev>(), d_near.p, s2.st),
+     "near field");
+  ck(cudaEventRecord(s2.e1, s2.st), "event");
 
-  cudaEvent_t ev[6];
-  for (auto &e : ev) ck(cudaEventCreate(&e), "event");
-  struct EvGuard {
-    cudaEvent_t *e;
-    ~EvGuard() { for (int i = 0; i < 6; i++) cudaEventDestroy(e[i]); }
-  } evg{ev};
-
-  // ---- a2: low-rank products. Far x far products (small) run one job per block; products with
-  // an inadmissible factor run as panels of up to panel_width() columns.
-  ck(cudaEventRecord(ev[0], s), "event");
-  DevBuf d_termbuf(es * std::max<int64_t>(term_elems, 1), s);
-  DevBuf d_jobs = upload(jobs, s), d_ffids = upload(ff_ids, s), d_panels = upload(panels, s);
-  DevBuf d_blkterms = upload(blk_terms, s);
-  DevBuf d_terms(sizeof(TermDev) * std::max<size_t>(nterm, 1), s);
-  ck(launch_make_terms(cprec, d_jobs.as<TermJob>(), (int)nterm, t.d_blocks, A->d_leaves.as<LeafDev>(),
-                       B->d_leaves.as<LeafDev>(), dataA, dataB, d_termbuf.p, d_terms.as<TermDev>(), s),
-     "term table");
-  ck(launch_term_jobs(cprec, d_jobs.as<TermJob>(), d_ffids.as<int32_t>(), (int)ff_ids.size(),
-                      A->d_leaves.as<LeafDev>(), B->d_leaves.as<LeafDev>(), t.d_blocks, dataA, dataB, d_termbuf.p, s),
-     "far x far products");
-  int64_t launches = 1 + (ff_ids.empty() ? 0 : 1);
-  const int64_t pstride = (int64_t)2 * pdim[NB + 1] * PW;
-  DevBuf d_pstage(es * std::max<int64_t>(pstride * (int64_t)pk[NB + 1].size(), 1), s);
-  for (int k = 0; k < NB + 2; k++) {
-    if (pk[k].empty()) continue;
-    PanelArgs pa{};
-    pa.first = pfirst[k];
-    pa.count = (int)pk[k].size();
-    pa.smem_in = pa.smem_out = pdim[k];
-    pa.smem_cw = pcw_rows;
-    pa.gstage = k == NB + 1 ? 1 : 0;
-    pa.stage_stride = pstride;
-    pa.stage_base = d_pstage.p;
-    pa.panels = d_panels.as<PanelDev>();
-    pa.jobs = d_jobs.as<TermJob>();
-    pa.blocks = t.d_blocks;
-    pa.leafA = A->d_leaves.as<LeafDev>();
-    pa.leafB = B->d_leaves.as<LeafDev>();
-    pa.dataA = dataA;
-    pa.dataB = dataB;
-    pa.terms = d_termbuf.p;
-    ck(launch_panels(cprec, pa, k == 0, s), "low-rank products (panels)");
-    launches++;
-  }
-  S.n_ff_jobs = (int64_t)ff_ids.size();
-  S.n_panels = (int64_t)panels.size();
-  check_finite(cprec, d_termbuf.p, term_elems, "low-rank products", s);
-  ck(cudaEventRecord(ev[1], s), "event");
-
+  tr.mark("near field launched");
   // ---- a3..a7: adaptive randomized truncation of all far targets
   const int nf = (int)ftg.size();
   DevBuf d_ftg = upload(ftg, s), d_fpairs = upload(fpairs, s);
@@ -938,6 +1061,7 @@ void Product::run() {
     ck(cudaStreamSynchronize(s), "round");
     if (act == 0) break;
   }
+  tr.mark("sampling rounds done");
   ck(cudaEventRecord(ev[2], s), "event");
   std::vector<TargetState> st(nf);
   if (nf) ck(cudaMemcpyAsync(st.data(), d_st.p, sizeof(TargetState) * nf, cudaMemcpyDeviceToHost, s), "states");
@@ -957,9 +1081,9 @@ void Product::run() {
   }
   ck(cudaEventRecord(ev[3], s), "event");
 
-  // ---- C: leaves, storage, write far factors, evaluate near leaves (a8, a9)
-  C->leaves = base_leaves(t);
-  int64_t off = 0;
+  tr.mark("core truncation done");
+  // ---- C: far leaves after the near ones, write far factors (a9), join the near field (a8)
+  int64_t off = near_elems;
   int64_t notconv = 0;
   for (size_t i = 0; i < ftg.size(); i++) {
     int k = st[i].rank;
@@ -970,24 +1094,18 @@ void Product::run() {
     l.off_v = off + (int64_t)l.m * k;
     off = l.off_v + (int64_t)l.n * k;
   }
-  for (const TargetDev &d : ntg) {
-    LeafDev &l = C->leaves[d.leaf];
-    l.off_u = off;
-    off += (int64_t)l.m * l.n;
-  }
   C->data_elems = off;
   C->d_data = DevBuf(es * std::max<int64_t>(off, 1), s);
   C->d_leaves = upload(C->leaves, s);
   ck(launch_write_far(cprec, aa.tg, aa.state, nf, d_qw.as<double>(), C->d_leaves.as<LeafDev>(), C->d_data.p, s),
      "write far");
-  DevBuf d_ntg = upload(ntg, s), d_npairs = upload(npairs, s);
-  ck(launch_near_eval(cprec, d_ntg.as<TargetDev>(), (int)ntg.size(), d_blkterms.as<int2>(), d_terms.as<TermDev>(),
-                      d_npairs.as<PairDev>(), t.d_blocks, A->d_leaves.as<LeafDev>(), B->d_leaves.as<LeafDev>(), dataA,
-                      dataB, C->d_leaves.as<LeafDev>(), C->d_data.p, s),
-     "near field");
+  ck(cudaStreamWaitEvent(s, s2.e1, 0), "stream wait");
+  if (near_elems > 0)
+    ck(cudaMemcpyAsync(C->d_data.p, d_near.p, es * near_elems, cudaMemcpyDeviceToDevice, s), "near copy");
   launches += (nf > 0 ? 1 : 0) + (ntg.empty() ? 0 : 1);
   ck(cudaEventRecord(ev[4], s), "event");
   ck(cudaStreamSynchronize(s), "product");
+  tr.mark("C written, synchronised");
   double ms_apply = 0;
   for (size_t i = 0; i + 1 < aev.size(); i += 2) {
     float x = 0;

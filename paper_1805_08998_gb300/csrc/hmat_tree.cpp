@@ -5,7 +5,9 @@
 #include "hmat_tree.h"
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
+#include <thread>
 #include <cuda_runtime.h>
 
 namespace hm {
@@ -163,82 +165,118 @@ std::shared_ptr<Tree> build_tree(const double *xyz, int64_t n, int dim, int leaf
 
 namespace {
 
-struct Planner {
+// Read-only copies of the block tree for the planner's hot loop.
+struct PlanTree {
   const Tree &t;
   const std::vector<int32_t> &rA, &rB;
-  Plan &plan;
-  std::vector<PairDev> pool;  // pairs of the blocks on the current path, innermost last
-  // compact copies of the block tree for the hot loop
-  std::vector<int32_t> child;  // 4 per block
+  std::vector<int32_t> child;  // 4 per block, tau'-major
   std::vector<int8_t> kind;
   std::vector<int32_t> leaf;
-  std::vector<int8_t> cidx;    // per block: (index of tau among its parent's children) * 2 + sigma's
-
-  void prepare() {
+  std::vector<int8_t> level;
+  PlanTree(const Tree &tt, const std::vector<int32_t> &a, const std::vector<int32_t> &b) : t(tt), rA(a), rB(b) {
     const size_t nb = t.bl.size();
     child.resize(nb * 4);
     kind.resize(nb);
     leaf.resize(nb);
-    cidx.assign(nb, 0);
-    for (size_t b = 0; b < nb; b++) {
-      const Block &bk = t.bl[b];
-      for (int c = 0; c < 4; c++) child[b * 4 + c] = bk.child[c];
-      kind[b] = (int8_t)bk.kind;
-      leaf[b] = bk.leaf;
-      if (bk.kind == BK_INNER)
-        for (int c = 0; c < bk.nchild; c++) cidx[bk.child[c]] = (int8_t)c;  // children are tau'-major
+    level.resize(nb);
+    for (size_t i = 0; i < nb; i++) {
+      const Block &bk = t.bl[i];
+      for (int c = 0; c < 4; c++) child[i * 4 + c] = bk.child[c];
+      kind[i] = (int8_t)bk.kind;
+      leaf[i] = bk.leaf;
+      level[i] = (int8_t)bk.level;
     }
+  }
+};
+
+struct Task {
+  int block;
+  std::vector<PairDev> pairs;
+};
+
+// One depth-first walk of Algorithm 3 below a block. Terms and leaf pairs go to local vectors;
+// the per-block arrays of the plan are written at the indices of this walk's blocks only, so
+// walks of disjoint subtrees can run on different threads.
+struct Planner {
+  const PlanTree *ptp = nullptr;
+  Plan *planp = nullptr;
+  int stop_level = -1;               // >= 0: record a Task instead of descending below this level
+  std::vector<Task> *tasks = nullptr;
+  std::vector<PlanTerm> terms;
+  std::vector<int32_t> blocks;       // blocks whose term range this walk set (local indices)
+  std::vector<PairDev> leaf_pairs;
+  std::vector<int64_t> leaf_rec;     // (leaf, local offset, count) triples
+  std::vector<PairDev> pool;         // pairs of the blocks on the current path, innermost last
+
+  void reset(const PlanTree *t, Plan *p, int stop, std::vector<Task> *tk) {
+    ptp = t;
+    planp = p;
+    stop_level = stop;
+    tasks = tk;
+    terms.clear();
+    blocks.clear();
+    leaf_pairs.clear();
+    leaf_rec.clear();
+    pool.clear();
   }
 
   // pairs of block b are pool[p0, p1)
   void visit(int b, size_t p0, size_t p1) {
-    if (kind[b] != BK_INNER) {
-      const int lf = leaf[b];
-      plan.leaf_pair_off[lf] = (int64_t)plan.leaf_pairs.size();
-      plan.leaf_pairs.insert(plan.leaf_pairs.end(), pool.begin() + p0, pool.begin() + p1);
+    const PlanTree &pt = *ptp;
+    Plan &plan = *planp;
+    if (pt.kind[b] != BK_INNER) {
+      leaf_rec.push_back(pt.leaf[b]);
+      leaf_rec.push_back((int64_t)leaf_pairs.size());
+      leaf_rec.push_back((int64_t)(p1 - p0));
+      leaf_pairs.insert(leaf_pairs.end(), pool.begin() + p0, pool.begin() + p1);
+      return;
+    }
+    if (stop_level >= 0 && pt.level[b] == stop_level) {
+      tasks->push_back(Task{b, std::vector<PairDev>(pool.begin() + p0, pool.begin() + p1)});
       return;
     }
     for (int c = 0; c < 4; c++) {
-      const int cb = child[b * 4 + c];
+      const int cb = pt.child[(size_t)b * 4 + c];
       const int ti = c >> 1, si = c & 1;  // tau'-major order of the children
-      plan.blk_term_lo[cb] = (int32_t)plan.terms.size();
+      plan.blk_term_lo[cb] = (int32_t)terms.size();
       int64_t rsum = 0;
       const size_t q0 = pool.size();
       for (size_t q = p0; q < p1; q++) {
         const PairDev pr = pool[q];
-        const int32_t *ca = &child[(size_t)pr.blkA * 4], *cbb = &child[(size_t)pr.blkB * 4];
+        const int32_t *ca = &pt.child[(size_t)pr.blkA * 4], *cbb = &pt.child[(size_t)pr.blkB * 4];
         for (int ri = 0; ri < 2; ri++) {
           const int a2 = ca[ti * 2 + ri];   // tau' x rho'
           const int b2 = cbb[ri * 2 + si];  // rho' x sigma'
-          const int kx = kind[a2], ky = kind[b2];
+          const int kx = pt.kind[a2], ky = pt.kind[b2];
           if (kx == BK_FAR || ky == BK_FAR) {
             PlanTerm tm;
             tm.block = cb;
             if (kx == BK_FAR && ky == BK_FAR) {
-              const int ka = rA[leaf[a2]], kb = rB[leaf[b2]];
+              const int ka = pt.rA[pt.leaf[a2]], kb = pt.rB[pt.leaf[b2]];
               tm.type = ka <= kb ? JOB_FF_R : JOB_FF_L;
-              tm.a = leaf[a2];
-              tm.b = leaf[b2];
+              tm.a = pt.leaf[a2];
+              tm.b = pt.leaf[b2];
               tm.rank = ka <= kb ? ka : kb;
             } else if (kx == BK_FAR) {
               tm.type = JOB_FH;
-              tm.a = leaf[a2];
+              tm.a = pt.leaf[a2];
               tm.b = b2;
-              tm.rank = rA[leaf[a2]];
+              tm.rank = pt.rA[pt.leaf[a2]];
             } else {
               tm.type = JOB_HF;
               tm.a = a2;
-              tm.b = leaf[b2];
-              tm.rank = rB[leaf[b2]];
+              tm.b = pt.leaf[b2];
+              tm.rank = pt.rB[pt.leaf[b2]];
             }
             rsum += tm.rank;
-            plan.terms.push_back(tm);
+            terms.push_back(tm);
           } else {
             pool.push_back(PairDev{a2, b2});
           }
         }
       }
-      plan.blk_term_hi[cb] = (int32_t)plan.terms.size();
+      plan.blk_term_hi[cb] = (int32_t)terms.size();
+      blocks.push_back(cb);
       plan.nterm_cum[cb] = plan.nterm_cum[b] + (plan.blk_term_hi[cb] - plan.blk_term_lo[cb]);
       plan.rank_cum[cb] = plan.rank_cum[b] + rsum;
       const size_t q1 = pool.size();
@@ -252,21 +290,78 @@ struct Planner {
 
 void build_plan(const Tree &t, const std::vector<int32_t> &rankA, const std::vector<int32_t> &rankB, Plan &plan) {
   const size_t nleaf = t.leaf_block.size(), nb = t.bl.size();
-  plan.terms.clear();
-  plan.terms.reserve(nb * 24);
-  plan.leaf_pairs.clear();
-  plan.leaf_pairs.reserve(nleaf * 8);
   plan.blk_term_lo.assign(nb, 0);
   plan.blk_term_hi.assign(nb, 0);
   plan.nterm_cum.assign(nb, 0);
   plan.rank_cum.assign(nb, 0);
+  PlanTree pt(t, rankA, rankB);
+  // serial walk down to split_level, then one walk per remaining subtree on a thread pool. The
+  // walks' buffers are kept between calls (thread-local), so their memory is already mapped.
+  static thread_local std::vector<Planner> walks_tl;
+  static thread_local std::vector<Task> tasks_tl;
+  std::vector<Planner> &walks = walks_tl;  // the calling thread's buffers, shared with the workers
+  std::vector<Task> &tasks = tasks_tl;
+  const int split_level = t.depth >= 6 ? 3 : -1;
+  tasks.clear();
+  if (walks.empty()) walks.resize(1);
+  walks[0].reset(&pt, &plan, split_level, &tasks);
+  walks[0].pool.push_back(PairDev{0, 0});  // S(I, I) = S_H(I, I) = {(A|I x I, B|I x I)}
+  walks[0].visit(0, 0, 1);
+  const size_t ntask = tasks.size();
+  if (walks.size() < 1 + ntask) walks.resize(1 + ntask);
+  for (size_t i = 0; i < ntask; i++) walks[1 + i].reset(&pt, &plan, -1, nullptr);
+  const size_t nwalk = 1 + ntask;
+  const unsigned hw = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+  auto parallel = [&](size_t count, auto &&fn) {
+    std::atomic<size_t> next{0};
+    auto worker = [&]() {
+      for (size_t i = next++; i < count; i = next++) fn(i);
+    };
+    std::vector<std::thread> th;
+    for (unsigned k = 1; k < std::min<size_t>(hw, count); k++) th.emplace_back(worker);
+    worker();
+    for (auto &x : th) x.join();
+  };
+  if (ntask > 0)
+    parallel(ntask, [&](size_t i) {
+      Planner &w = walks[1 + i];
+      w.pool.assign(tasks[i].pairs.begin(), tasks[i].pairs.end());
+      w.visit(tasks[i].block, 0, tasks[i].pairs.size());
+    });
+  // merge: terms concatenated walk by walk (block ranges shifted), leaf pairs laid out in leaf order
+  std::vector<size_t> toff(nwalk + 1, 0);
+  size_t npairs = 0;
+  for (size_t i = 0; i < nwalk; i++) {
+    toff[i + 1] = toff[i] + walks[i].terms.size();
+    npairs += walks[i].leaf_pairs.size();
+  }
+  plan.terms.resize(toff[nwalk]);
+  std::vector<const PairDev *> src(nleaf, nullptr);
+  std::vector<int64_t> cnt(nleaf, 0);
+  for (size_t i = 0; i < nwalk; i++) {
+    const Planner &w = walks[i];
+    for (size_t k = 0; k + 2 < w.leaf_rec.size(); k += 3) {
+      const int64_t lf = w.leaf_rec[k];
+      src[lf] = w.leaf_pairs.data() + w.leaf_rec[k + 1];
+      cnt[lf] = w.leaf_rec[k + 2];
+    }
+  }
   plan.leaf_pair_off.assign(nleaf + 1, 0);
-  Planner pl{t, rankA, rankB, plan, {}, {}, {}, {}, {}};
-  pl.prepare();
-  pl.pool.reserve(1 << 16);
-  pl.pool.push_back(PairDev{0, 0});  // S(I, I) = S_H(I, I) = {(A|I x I, B|I x I)}
-  pl.visit(0, 0, 1);
-  plan.leaf_pair_off[nleaf] = (int64_t)plan.leaf_pairs.size();
+  for (size_t l = 0; l < nleaf; l++) plan.leaf_pair_off[l + 1] = plan.leaf_pair_off[l] + cnt[l];
+  plan.leaf_pairs.resize(npairs);
+  parallel(nwalk, [&](size_t i) {
+    const Planner &w = walks[i];
+    std::copy(w.terms.begin(), w.terms.end(), plan.terms.begin() + toff[i]);
+    const int32_t off = (int32_t)toff[i];
+    for (int32_t b : w.blocks) {
+      plan.blk_term_lo[b] += off;
+      plan.blk_term_hi[b] += off;
+    }
+    for (size_t k = 0; k + 2 < w.leaf_rec.size(); k += 3) {
+      const int64_t lf = w.leaf_rec[k];
+      std::copy(src[lf], src[lf] + cnt[lf], plan.leaf_pairs.begin() + plan.leaf_pair_off[lf]);
+    }
+  });
 }
 
 }  // namespace hm

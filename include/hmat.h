@@ -36,6 +36,12 @@ extern "C" {
 #endif
 
 typedef struct hmat_s *hmat_t;
+typedef struct hmat_rankmodel_s *hmat_rankmodel_t;  /* learned rank proposal (an MLP) */
+
+/* Number of features per far block fed to the rank proposal, and of the MLP's parameters
+ * (12 -> 64 -> 64 -> 1, ReLU; layout W1[64][12], b1[64], W2[64][64], b2[64], w3[64], b3). */
+#define HMAT_RANK_FEATURES 12
+#define HMAT_RANK_PARAMS 5057
 
 typedef enum {
   HMAT_OK = 0,
@@ -78,13 +84,24 @@ typedef struct {
 typedef struct {
   double eps;          /* relative Frobenius tolerance per far block (> 0) */
   int mode;            /* hmat_mode */
-  int rank_proposal;   /* 0: none (first round uses block_width columns);
-                          1: learned proposal (reserved; currently treated as 0) */
+  int rank_proposal;   /* first-round width of each far block: 0 = block_width columns;
+                          1 = learned (rank_model must be set): predicted rank + block_width;
+                          2 = heuristic: max of A's and B's ranks on the block + block_width.
+                          With 1 or 2 the first round holds a verification block (its last
+                          block_width/2 kept columns) and eq. (truncaca) is tested within it; the
+                          adaptive rounds continue whenever that test fails. Widths <= 16. */
   int max_rank;        /* cap on the sampled basis per block (0 = default 96) */
   int max_rounds;      /* cap on adaptive rounds (0 = default max_rank / block_width + 1) */
   int block_width;     /* columns added per adaptive round (0 = default 8; <= 16) */
   uint64_t seed;       /* seed of the Gaussian test matrices (counter-based, splitmix64) */
+  hmat_rankmodel_t rank_model;  /* used when rank_proposal == 1 (NULL otherwise) */
 } hmat_mult_opts;
+
+typedef struct {
+  int epochs;          /* full-batch training steps (0 = default 1500) */
+  float lr;            /* Adam learning rate (0 = default 3e-3) */
+  uint64_t seed;       /* initial weights */
+} hmat_train_opts;
 
 typedef struct {
   int64_t row_begin, row_size;   /* permuted row range of tau */
@@ -122,6 +139,9 @@ typedef struct {
   int64_t launches;              /* kernels this call launched (all of them are the library's) */
   int64_t n_ff_jobs;             /* low-rank products with two far factors */
   int64_t n_panels;              /* panels of products with one inadmissible factor */
+  int64_t first_round_cols;      /* columns sampled in the first round, summed over far blocks */
+  int64_t done_in_first_round;   /* far blocks whose stop test held in the first round */
+  int64_t sample_passes;         /* sum over far blocks of the rounds each one took part in */
 } hmat_stats_t;
 
 /* Fill xyz (n*dim doubles, row-major, caller-owned) with the seeded points of the given
@@ -187,6 +207,41 @@ hmat_status hmat_stats(const hmat_t h, hmat_stats_t *stats);
  * restriction of Algorithm 3 builds from S(I,I) = AB (Algorithm 4); arrays of leaf-count
  * entries, caller-owned. Needs only the block tree of A (B must share it). */
 hmat_status hmat_sumexpr_counts(const hmat_t A, const hmat_t B, int64_t *n_lowrank, int64_t *n_hpairs);
+
+/* Features of the far blocks of the product A B for the rank proposal, in depth-first leaf order
+ * (n_far x HMAT_RANK_FEATURES, row-major, caller-owned): log2 of the block's rows and columns,
+ * its level, diam(tau)/dist and diam(sigma)/dist, log2(1 + #low-rank terms), log2(1 + #H-pairs),
+ * the largest and log2(1 + sum of) the terms' ranks, the ranks of A and B on the block, and
+ * -log10(eps). If C (the product) is given, ranks[i] = C's rank on the block. *n_far: in the
+ * capacity of the arrays (rows), out the number of far blocks (EINVAL if the capacity is
+ * too small; pass features = NULL to query the count). Host-only. */
+hmat_status hmat_rank_features(const hmat_t A, const hmat_t B, double eps, const hmat_t C, float *features,
+                               float *ranks, int64_t *n_far);
+
+/* Train a rank model on the GPU on (features, ranks) samples (host arrays, count rows): features
+ * are standardised with the sample mean and deviation, the target is log2(1 + rank), the loss
+ * the mean squared error, optimised by Adam over full batches; forward and backward run in the
+ * library's kernels (FP16 weights, FP32 accumulation). Synchronises. */
+hmat_status hmat_rankmodel_train(const float *features, const float *ranks, int64_t count,
+                                 const hmat_train_opts *opts, void *stream, hmat_rankmodel_t *out);
+
+/* Predicted ranks (2^y - 1 of the network's output y) for count feature rows. Synchronises. */
+hmat_status hmat_rankmodel_predict(const hmat_rankmodel_t m, const float *features, int64_t count, float *ranks);
+
+/* Copy the model out: weights (HMAT_RANK_PARAMS floats, the FP16 values the forward pass uses,
+ * widened), feature mean and deviation (HMAT_RANK_FEATURES each), final training loss. Any output
+ * may be NULL. */
+hmat_status hmat_rankmodel_get(const hmat_rankmodel_t m, float *weights, float *mean, float *dev, float *loss);
+
+/* A model from given weights (rounded to FP16) and normalisation. */
+hmat_status hmat_rankmodel_create(const float *weights, const float *mean, const float *dev, hmat_rankmodel_t *out);
+
+/* Gradient of the training loss with respect to the weights at the model's current weights, and
+ * the loss, on the given samples (as one training step computes them). Synchronises. */
+hmat_status hmat_rankmodel_grad(const hmat_rankmodel_t m, const float *features, const float *ranks, int64_t count,
+                                float *grad, float *loss);
+
+void hmat_rankmodel_destroy(hmat_rankmodel_t m);
 
 /* Release h and its device memory (NULL is a no-op). */
 void hmat_destroy(hmat_t h);

@@ -247,6 +247,78 @@ bool same_points(const Tree &t, const double *xyz, int64_t n, int dim) {
 
 }  // namespace
 
+// ------------------------------------------------------------------ rank proposal
+
+struct hmat_rankmodel_s {
+  float *w = nullptr;   // FP32 master weights (device)
+  void *w16 = nullptr;  // FP16 weights used by the forward pass (device)
+  float mean[RANK_FEATURES], dev[RANK_FEATURES];
+  float loss = 0.f;
+  ~hmat_rankmodel_s() {
+    if (w) cudaFree(w);
+    if (w16) cudaFree(w16);
+  }
+};
+
+namespace {
+
+// per block: the largest rank among the terms of S_R(block) (created at it or an ancestor);
+// parents precede children in the block numbering
+std::vector<int32_t> chain_max_rank(const Tree &t, const Plan &plan) {
+  std::vector<int32_t> mx(t.bl.size(), 0);
+  for (size_t b = 0; b < t.bl.size(); b++) {
+    int32_t v = t.bl[b].parent >= 0 ? mx[t.bl[b].parent] : 0;
+    for (int32_t i = plan.blk_term_lo[b]; i < plan.blk_term_hi[b]; i++) v = std::max(v, plan.terms[i].rank);
+    mx[b] = v;
+  }
+  return mx;
+}
+
+double box_diam(const Cluster &c, int dim) {
+  double s = 0.0;
+  for (int d = 0; d < dim; d++) s += (c.hi[d] - c.lo[d]) * (c.hi[d] - c.lo[d]);
+  return std::sqrt(s);
+}
+
+double box_dist(const Cluster &a, const Cluster &b, int dim) {
+  double s = 0.0;
+  for (int d = 0; d < dim; d++) {
+    const double g = std::max(0.0, std::max(b.lo[d] - a.hi[d], a.lo[d] - b.hi[d]));
+    s += g * g;
+  }
+  return std::sqrt(s);
+}
+
+// the HMAT_RANK_FEATURES features of far leaf l (see hmat_rank_features)
+void far_features(const Tree &t, const Plan &plan, const std::vector<int32_t> &mxr, const std::vector<LeafDev> &LA,
+                  const std::vector<LeafDev> &LB, double eps, int l, float *f) {
+  const int b = t.leaf_block[l];
+  const Block &bk = t.bl[b];
+  const Cluster &ct = t.cl[bk.tau], &cs = t.cl[bk.sigma];
+  const double dist = std::max(box_dist(ct, cs, t.dim), 1e-300);
+  f[0] = (float)std::log2((double)ct.size);
+  f[1] = (float)std::log2((double)cs.size);
+  f[2] = (float)bk.level;
+  f[3] = (float)(box_diam(ct, t.dim) / dist);
+  f[4] = (float)(box_diam(cs, t.dim) / dist);
+  f[5] = (float)std::log2(1.0 + plan.nterm_cum[b]);
+  f[6] = (float)std::log2(1.0 + (double)(plan.leaf_pair_off[l + 1] - plan.leaf_pair_off[l]));
+  f[7] = (float)mxr[b];
+  f[8] = (float)std::log2(1.0 + (double)plan.rank_cum[b]);
+  f[9] = (float)std::max(0, (int)LA[l].rank);
+  f[10] = (float)std::max(0, (int)LB[l].rank);
+  f[11] = (float)(-std::log10(eps));
+}
+
+void normalise(const hmat_rankmodel_s *m, const float *in, int64_t count, std::vector<float> &out) {
+  out.resize((size_t)count * RANK_FEATURES);
+  for (int64_t i = 0; i < count; i++)
+    for (int k = 0; k < RANK_FEATURES; k++)
+      out[i * RANK_FEATURES + k] = (in[i * RANK_FEATURES + k] - m->mean[k]) / m->dev[k];
+}
+
+}  // namespace
+
 // ------------------------------------------------------------------ C-ABI
 
 extern "C" {
@@ -525,6 +597,173 @@ hmat_status hmat_stats(const hmat_t h, hmat_stats_t *stats) {
   });
 }
 
+hmat_status hmat_rank_features(const hmat_t A, const hmat_t B, double eps, const hmat_t C, float *features,
+                               float *ranks, int64_t *n_far) {
+  return guard([&] {
+    if (!A || !B || !n_far) fail(HMAT_EINVAL, "NULL argument");
+    if (!(eps > 0.0)) fail(HMAT_EINVAL, "eps must be > 0");
+    if (A->tree != B->tree && !same_points(*A->tree, B->tree->orig.data(), B->tree->n, B->tree->dim))
+      fail(HMAT_EMISMATCH, "A and B are not on one block tree");
+    const Tree &t = *A->tree;
+    int64_t nfar = 0;
+    for (const LeafDev &l : A->leaves) nfar += l.rank >= 0 ? 1 : 0;
+    if (!features) {
+      *n_far = nfar;
+      return;
+    }
+    if (*n_far < nfar) fail(HMAT_EINVAL, "feature array smaller than the number of far blocks");
+    if (C && C->leaves.size() != A->leaves.size()) fail(HMAT_EMISMATCH, "C is not on the tree of A and B");
+    std::vector<int32_t> ra(A->leaves.size()), rb(B->leaves.size());
+    for (size_t l = 0; l < ra.size(); l++) { ra[l] = A->leaves[l].rank; rb[l] = B->leaves[l].rank; }
+    Plan plan;
+    build_plan(t, ra, rb, plan);
+    const std::vector<int32_t> mxr = chain_max_rank(t, plan);
+    int64_t i = 0;
+    for (size_t l = 0; l < A->leaves.size(); l++) {
+      if (A->leaves[l].rank < 0) continue;
+      far_features(t, plan, mxr, A->leaves, B->leaves, eps, (int)l, features + i * RANK_FEATURES);
+      if (ranks) ranks[i] = C ? (float)std::max(0, (int)C->leaves[l].rank) : 0.f;
+      i++;
+    }
+    *n_far = nfar;
+  });
+}
+
+hmat_status hmat_rankmodel_create(const float *weights, const float *mean, const float *dev, hmat_rankmodel_t *out) {
+  if (out) *out = nullptr;
+  return guard([&] {
+    if (!weights || !mean || !dev || !out) fail(HMAT_EINVAL, "NULL argument");
+    auto m = std::make_unique<hmat_rankmodel_s>();
+    for (int k = 0; k < RANK_FEATURES; k++) {
+      if (!(dev[k] > 0.f)) fail(HMAT_EINVAL, "feature deviations must be > 0");
+      m->mean[k] = mean[k];
+      m->dev[k] = dev[k];
+    }
+    ck(cudaMalloc(&m->w, sizeof(float) * RANK_PARAMS), "model");
+    ck(cudaMalloc(&m->w16, 2 * RANK_PARAMS), "model");
+    ck(cudaMemcpy(m->w, weights, sizeof(float) * RANK_PARAMS, cudaMemcpyHostToDevice), "model");
+    ck(launch_to_half(m->w, m->w16, nullptr), "model");
+    ck(cudaDeviceSynchronize(), "model");
+    *out = m.release();
+  });
+}
+
+hmat_status hmat_rankmodel_train(const float *features, const float *ranks, int64_t count,
+                                 const hmat_train_opts *opts, void *stream, hmat_rankmodel_t *out) {
+  if (out) *out = nullptr;
+  return guard([&] {
+    if (!features || !ranks || !out || count < 1) fail(HMAT_EINVAL, "NULL argument or no samples");
+    const int epochs = opts && opts->epochs > 0 ? opts->epochs : 1500;
+    const float lr = opts && opts->lr > 0.f ? opts->lr : 3e-3f;
+    const uint64_t seed = opts ? opts->seed : 0;
+    cudaStream_t s = (cudaStream_t)stream;
+    auto m = std::make_unique<hmat_rankmodel_s>();
+    for (int k = 0; k < RANK_FEATURES; k++) {
+      double mu = 0.0, sq = 0.0;
+      for (int64_t i = 0; i < count; i++) mu += features[i * RANK_FEATURES + k];
+      mu /= (double)count;
+      for (int64_t i = 0; i < count; i++) {
+        const double d = features[i * RANK_FEATURES + k] - mu;
+        sq += d * d;
+      }
+      m->mean[k] = (float)mu;
+      m->dev[k] = (float)std::max(std::sqrt(sq / (double)count), 1e-3);
+    }
+    std::vector<float> xn, y(count);
+    normalise(m.get(), features, count, xn);
+    double ymean = 0.0;
+    for (int64_t i = 0; i < count; i++) {
+      y[i] = (float)std::log2(1.0 + std::max(0.f, ranks[i]));
+      ymean += y[i];
+    }
+    ymean /= (double)count;
+    // He-uniform initial weights from a splitmix64 stream, zero biases, output bias = mean target
+    std::vector<float> w(RANK_PARAMS, 0.f);
+    uint64_t c = 0;
+    auto uni = [&]() {
+      uint64_t z = seed + (++c) * 0x9E3779B97F4A7C15ull;
+      z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+      z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+      z ^= z >> 31;
+      return (double)(z >> 11) * 0x1.0p-53 * 2.0 - 1.0;
+    };
+    const int F = RANK_FEATURES, Hh = 64;
+    for (int i = 0; i < Hh * F; i++) w[i] = (float)(uni() * std::sqrt(6.0 / F));
+    for (int i = 0; i < Hh * Hh; i++) w[Hh * F + Hh + i] = (float)(uni() * std::sqrt(6.0 / Hh));
+    for (int i = 0; i < Hh; i++) w[Hh * F + Hh + Hh * Hh + Hh + i] = (float)(uni() * std::sqrt(6.0 / Hh) * 0.1);
+    w[RANK_PARAMS - 1] = (float)ymean;
+    ck(cudaMalloc(&m->w, sizeof(float) * RANK_PARAMS), "model");
+    ck(cudaMalloc(&m->w16, 2 * RANK_PARAMS), "model");
+    DevBuf dx(sizeof(float) * xn.size(), s), dy(sizeof(float) * count, s);
+    ck(cudaMemcpyAsync(m->w, w.data(), sizeof(float) * RANK_PARAMS, cudaMemcpyHostToDevice, s), "model");
+    ck(cudaMemcpyAsync(dx.p, xn.data(), sizeof(float) * xn.size(), cudaMemcpyHostToDevice, s), "samples");
+    ck(cudaMemcpyAsync(dy.p, y.data(), sizeof(float) * count, cudaMemcpyHostToDevice, s), "samples");
+    ck(mlp_train(m->w, m->w16, dx.as<float>(), dy.as<float>(), (int)count, epochs, lr, s, &m->loss), "training");
+    ck(cudaStreamSynchronize(s), "training");
+    *out = m.release();
+  });
+}
+
+hmat_status hmat_rankmodel_predict(const hmat_rankmodel_t m, const float *features, int64_t count, float *ranks) {
+  return guard([&] {
+    if (!m || !features || !ranks) fail(HMAT_EINVAL, "NULL argument");
+    if (count == 0) return;
+    std::vector<float> xn;
+    normalise(m, features, count, xn);
+    DevBuf dx(sizeof(float) * xn.size(), nullptr), dout(sizeof(float) * count, nullptr);
+    ck(cudaMemcpyAsync(dx.p, xn.data(), sizeof(float) * xn.size(), cudaMemcpyHostToDevice, nullptr), "samples");
+    ck(launch_mlp_forward(m->w16, dx.as<float>(), (int)count, dout.as<float>(), nullptr), "forward");
+    std::vector<float> y(count);
+    ck(cudaMemcpyAsync(y.data(), dout.p, sizeof(float) * count, cudaMemcpyDeviceToHost, nullptr), "forward");
+    ck(cudaStreamSynchronize(nullptr), "forward");
+    for (int64_t i = 0; i < count; i++) ranks[i] = std::max(0.f, std::exp2(y[i]) - 1.f);
+  });
+}
+
+hmat_status hmat_rankmodel_get(const hmat_rankmodel_t m, float *weights, float *mean, float *dev, float *loss) {
+  return guard([&] {
+    if (!m) fail(HMAT_EINVAL, "NULL model");
+    if (weights) {
+      std::vector<uint16_t> h(RANK_PARAMS);
+      ck(cudaMemcpy(h.data(), m->w16, 2 * RANK_PARAMS, cudaMemcpyDeviceToHost), "weights");
+      for (int i = 0; i < RANK_PARAMS; i++) {  // IEEE binary16 -> float
+        const uint32_t hb = h[i], sign = (hb >> 15) & 1, ex = (hb >> 10) & 31, man = hb & 1023;
+        float v;
+        if (ex == 0) v = std::ldexp((float)man, -24);
+        else if (ex == 31) v = man ? NAN : INFINITY;
+        else v = std::ldexp((float)(man | 1024), (int)ex - 25);
+        weights[i] = sign ? -v : v;
+      }
+    }
+    if (mean) std::memcpy(mean, m->mean, sizeof(m->mean));
+    if (dev) std::memcpy(dev, m->dev, sizeof(m->dev));
+    if (loss) *loss = m->loss;
+  });
+}
+
+hmat_status hmat_rankmodel_grad(const hmat_rankmodel_t m, const float *features, const float *ranks, int64_t count,
+                                float *grad, float *loss) {
+  return guard([&] {
+    if (!m || !features || !ranks || !grad || count < 1) fail(HMAT_EINVAL, "NULL argument or no samples");
+    std::vector<float> xn, y(count);
+    normalise(m, features, count, xn);
+    for (int64_t i = 0; i < count; i++) y[i] = (float)std::log2(1.0 + std::max(0.f, ranks[i]));
+    DevBuf dx(sizeof(float) * xn.size(), nullptr), dy(sizeof(float) * count, nullptr);
+    DevBuf dg(sizeof(float) * RANK_PARAMS, nullptr), dl(sizeof(float), nullptr);
+    ck(cudaMemcpyAsync(dx.p, xn.data(), sizeof(float) * xn.size(), cudaMemcpyHostToDevice, nullptr), "samples");
+    ck(cudaMemcpyAsync(dy.p, y.data(), sizeof(float) * count, cudaMemcpyHostToDevice, nullptr), "samples");
+    ck(launch_mlp_grad(m->w16, dx.as<float>(), dy.as<float>(), (int)count, dg.as<float>(), dl.as<float>(), nullptr),
+       "gradient");
+    float l = 0.f;
+    ck(cudaMemcpyAsync(grad, dg.p, sizeof(float) * RANK_PARAMS, cudaMemcpyDeviceToHost, nullptr), "gradient");
+    ck(cudaMemcpyAsync(&l, dl.p, sizeof(float), cudaMemcpyDeviceToHost, nullptr), "gradient");
+    ck(cudaStreamSynchronize(nullptr), "gradient");
+    if (loss) *loss = l;
+  });
+}
+
+void hmat_rankmodel_destroy(hmat_rankmodel_t m) { delete m; }
+
 hmat_status hmat_sumexpr_counts(const hmat_t A, const hmat_t B, int64_t *n_lowrank, int64_t *n_hpairs) {
   return guard([&] {
     if (!A || !B || !n_lowrank || !n_hpairs) fail(HMAT_EINVAL, "NULL argument");
@@ -609,9 +848,8 @@ void Product::run() {
   if (max_rank > 96) fail(HMAT_EINVAL, "max_rank must be <= 96");
   if (max_rank < p) max_rank = p;
   const int max_rounds = o->max_rounds > 0 ? o->max_rounds : max_rank / p + 1;
-  // columns of the first round (the same as later rounds unless a rank proposal widens it)
-  const int p0 = p;
-  const int pmax = std::max(p, p0);
+  if (o->rank_proposal < 0 || o->rank_proposal > 2) fail(HMAT_EINVAL, "rank_proposal must be 0, 1 or 2");
+  if (o->rank_proposal == 1 && !o->rank_model) fail(HMAT_EINVAL, "rank_proposal 1 needs a rank_model");
 
   // factors in compute precision
   DevBuf convA, convB;
@@ -842,6 +1080,42 @@ void Product::run() {
     (lc.rank < 0 ? nearv : far).push_back(Tgt{(int)l, e});
   }
   S.n_lr_refs = lr_refs;
+  // Columns of each far target's first round: p, or a proposed rank + p (at most PROP_MAX),
+  // the last p/2 of which form the verification block of the in-round stop test.
+  constexpr int PROP_MAX = 16;
+  std::vector<int> p0v(t.leaf_block.size(), p);
+  if (o->rank_proposal != 0 && !far.empty() && p < PROP_MAX) {
+    std::vector<float> khat(far.size(), 0.f);
+    if (o->rank_proposal == 2) {
+      for (size_t i = 0; i < far.size(); i++)
+        khat[i] = (float)std::max(A->leaves[far[i].leaf].rank, B->leaves[far[i].leaf].rank);
+    } else {
+      const hmat_rankmodel_s *m = o->rank_model;
+      const std::vector<int32_t> mxr = chain_max_rank(t, plan);
+      std::vector<float> f(far.size() * RANK_FEATURES), fn;
+      const size_t nch = (far.size() + 255) / 256;
+      parallel_for(nch, [&](size_t c) {
+        for (size_t i = c * 256; i < std::min(far.size(), c * 256 + 256); i++)
+          far_features(t, plan, mxr, A->leaves, B->leaves, o->eps, far[i].leaf, f.data() + i * RANK_FEATURES);
+      });
+      normalise(m, f.data(), (int64_t)far.size(), fn);
+      DevBuf dx = upload(fn, s), dy(sizeof(float) * far.size(), s);
+      ck(launch_mlp_forward(m->w16, dx.as<float>(), (int)far.size(), dy.as<float>(), s), "rank proposal");
+      launches++;
+      ck(cudaMemcpyAsync(khat.data(), dy.p, sizeof(float) * far.size(), cudaMemcpyDeviceToHost, s), "rank proposal");
+      ck(cudaStreamSynchronize(s), "rank proposal");
+      for (float &k : khat) k = std::max(0.f, std::exp2(k) - 1.f);
+    }
+    for (size_t i = 0; i < far.size(); i++) {
+      const LeafDev &lc = A->leaves[far[i].leaf];
+      const int mn = (int)std::min(lc.m, lc.n);
+      const int k = std::min((int)std::ceil(khat[i] - 0.25f), mn);
+      p0v[far[i].leaf] = std::max(p, std::min(PROP_MAX, k + p));
+    }
+    tr.mark("rank proposal");
+  }
+  int pmax = p;
+  for (const Tgt &g : far) pmax = std::max(pmax, p0v[g.leaf]);
   // Size classes of the application kernel: 0 = panels staged in global memory (targets too
   // large for shared memory); class c >= 1 = targets of at most 32 << (c - 1) rows, columns
   // and H-pair rows, staged in shared memory sized for that bound. Far targets are ordered by
@@ -892,6 +1166,7 @@ void Product::run() {
       d.m = lc.m;
       d.n = lc.n;
       d.leaf = l;
+      d.p0 = p0v[l];
       d.blk = t.leaf_block[l];
       d.nterms = plan.nterm_cum[d.blk];
       d.pair_lo = (int32_t)tpairs.size();
@@ -1042,8 +1317,9 @@ void Product::run() {
   };
   for (int round = 0; round < max_rounds && nf > 0; round++) {
     rounds++;
-    const int pr = round == 0 ? p0 : p;  // columns sampled this round
+    const int pr = round == 0 ? pmax : p;  // widest panel this round (round 0: each target's p0)
     aa.p = pr;
+    aa.round = round;
     ck(launch_gaussian(cprec, aa.tg, aa.state, nf, pr, o->seed, round, d_x.p, s), "gaussian");
     timed_apply(false);
     check_finite(cprec, d_y.p, xy_elems, "apply S", s);
@@ -1066,6 +1342,11 @@ void Product::run() {
   std::vector<TargetState> st(nf);
   if (nf) ck(cudaMemcpyAsync(st.data(), d_st.p, sizeof(TargetState) * nf, cudaMemcpyDeviceToHost, s), "states");
   ck(cudaStreamSynchronize(s), "states");
+  for (int i = 0; i < nf; i++) {
+    S.first_round_cols += ftg[i].p0;
+    if (st[i].nfwd <= 1 && st[i].rank != -2) S.done_in_first_round++;
+    S.sample_passes += st[i].nfwd;
+  }
   {
     std::vector<int32_t> ids_small, ids_big;
     for (int i = 0; i < nf; i++) (st[i].r <= 32 ? ids_small : ids_big).push_back(i);

@@ -208,7 +208,7 @@ __global__ void __launch_bounds__(AT) k_apply(ApplyArgs a) {
   T *cw = cwall + warp * a.smem_cw * P;
   const T *X = (const T *)a.x_base + t.x_off;  // column-major inlen x p
   T *Out = (T *)a.y_base + t.y_off;            // column-major outlen x p
-  const int p = a.p;
+  const int p = a.round == 0 ? t.p0 : a.p;     // this target's columns this round (<= P)
   for (int o = threadIdx.x; o < inlen * P; o += AT) {
     const int i = o / P, c = o - i * P;
     Xs[o] = c < p ? X[i + (int64_t)c * inlen] : T(0);

@@ -16,6 +16,10 @@
 
 namespace hm {
 
+// learned rank proposal: 12 features -> 64 -> 64 -> 1
+constexpr int RANK_FEATURES = 12;
+constexpr int RANK_PARAMS = 64 * 12 + 64 + 64 * 64 + 64 + 64 + 1;
+
 struct LeafDev {
   int64_t row, col;     // permuted begin of tau and sigma
   int32_t m, n, rank;   // rank < 0: dense leaf
@@ -90,7 +94,7 @@ struct TargetDev {
   int32_t pair_lo, pair_mid, pair_hi;  // [lo, mid): pairs of two dense leaves; [mid, hi): inner blocks
   int32_t leaf;         // leaf id in the block tree
   int32_t rmax;         // basis capacity (columns of Q and W)
-  int32_t pad;
+  int32_t p0;           // columns of the first round (its last p are a verification block when p0 > p)
   int64_t q_off, w_off; // FP64 basis Q (m x rmax) and W (n x rmax)
   int64_t y_off, x_off; // per-round sample buffers (max(m,n) x p each), element type T
   int64_t stage_off;    // global staging panels (targets too large for shared memory)
@@ -125,7 +129,8 @@ struct ApplyArgs {
   TargetState *state;
   void *y_base;          // per-target In/Out regions (element type T), offsets in TargetDev
   void *x_base;
-  int p;                 // columns this round
+  int p;                 // columns this round (the first round: each target's p0 instead)
+  int round;
 };
 
 // ---- launch wrappers (hmat_kernels.cu); all return cudaError_t of the launch ----
@@ -171,5 +176,13 @@ cudaError_t launch_write_far(int prec, const TargetDev *tg, const TargetState *s
 cudaError_t launch_convert(int prec, const void *src, double *dst, int64_t count, cudaStream_t s);
 // atomicMin of the index of every non-finite entry into *first (initialise to ~0ull)
 cudaError_t launch_find_nonfinite(int prec, const void *x, int64_t count, unsigned long long *first, cudaStream_t s);
+
+// learned rank proposal (hmat_rank.cu); w16 holds RANK_PARAMS FP16 weights
+cudaError_t launch_mlp_forward(const void *w16, const float *x, int count, float *out, cudaStream_t s);
+cudaError_t launch_mlp_grad(const void *w16, const float *x, const float *y, int count, float *grad, float *loss,
+                            cudaStream_t s);
+cudaError_t launch_to_half(const float *w, void *w16, cudaStream_t s);
+cudaError_t mlp_train(float *w, void *w16, const float *x, const float *y, int count, int epochs, float lr,
+                      cudaStream_t s, float *final_loss);
 
 }  // namespace hm

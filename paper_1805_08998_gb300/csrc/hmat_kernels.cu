@@ -532,6 +532,7 @@ __global__ void __launch_bounds__(NT) k_gaussian(const TargetDev *tg, const Targ
   if (st[b].active == 0) return;
   const TargetDev t = tg[b];
   T *X = x_base + t.x_off;
+  if (round == 0) p = t.p0;
   for (int64_t o = threadIdx.x; o < (int64_t)t.n * p; o += NT) {
     const int64_t i = o % t.n, c = o / t.n;
     const uint64_t ctr = ((((uint64_t)t.leaf * 64u + (uint64_t)round) * 64u + (uint64_t)c) << 24) + (uint64_t)i;
@@ -561,6 +562,7 @@ __global__ void __launch_bounds__(NT) k_orth(const TargetDev *tg, TargetState *s
   const TargetDev t = tg[b];
   const int64_t m = t.m;
   const int r = st[b].r;
+  if (round == 0) p = t.p0;
   double *Q = qw + t.q_off;
   double *Y = Q + (int64_t)r * m;  // m x p workspace inside Q
   const T *Ys = y_base + t.y_off;
@@ -673,6 +675,16 @@ __global__ void __launch_bounds__(NT) k_absorb_w(const TargetDev *tg, TargetStat
     part += v * v;
   }
   const double nw2 = block_sum(part, red);
+  // a first round wider than p holds a verification block: its last v = p/2 kept columns. Their
+  // energy against the rest's (the proposed rank plus p/2 columns of oversampling) is the
+  // blocked eq. (truncaca) within the round.
+  const int v = (round == 0 && t.p0 > p && pn >= 2) ? min(max(p / 2, 1), pn - 1) : 0;
+  double last2 = 0.0;
+  if (v > 0) {
+    double pl = 0.0;
+    for (int64_t o = (int64_t)t.n * (pn - v) + threadIdx.x; o < (int64_t)t.n * pn; o += NT) pl += W[o] * W[o];
+    last2 = block_sum(pl, red);
+  }
   if (threadIdx.x == 0) {
     const double old = st[b].nrm2;
     st[b].nrm2 = old + nw2;
@@ -680,6 +692,7 @@ __global__ void __launch_bounds__(NT) k_absorb_w(const TargetDev *tg, TargetStat
     st[b].r = rn;
     int act = 1;
     if (nw2 <= eps_stop * eps_stop * old) act = 0;
+    if (v > 0 && last2 <= eps_stop * eps_stop * (nw2 - last2)) act = 0;
     if (rn >= min(t.m, t.n)) act = 0;                       // range exhausted: exact
     if (rn + p > t.rmax || round + 1 >= max_rounds) {
       if (act) st[b].rank = -2;                              // marks "hit a cap"

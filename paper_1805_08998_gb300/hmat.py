@@ -26,8 +26,13 @@ MODE_F64, MODE_MIXED = 0, 1
 # every symbol include/hmat.h declares
 EXPORTS = ["hmat_points", "hmat_build", "hmat_multiply", "hmat_to_dense", "hmat_leaf_count", "hmat_leaf_info",
            "hmat_leaf_get", "hmat_permutation", "hmat_stats", "hmat_sumexpr_counts", "hmat_destroy",
-           "hmat_data_bytes", "hmat_data_get",
-           "hmat_last_error", "hmat_set_allocator"]
+           "hmat_data_bytes", "hmat_data_get", "hmat_rank_features", "hmat_rankmodel_train",
+           "hmat_rankmodel_predict", "hmat_rankmodel_get", "hmat_rankmodel_create", "hmat_rankmodel_grad",
+           "hmat_rankmodel_destroy", "hmat_last_error", "hmat_set_allocator"]
+
+RANK_FEATURES = 12
+RANK_PARAMS = 5057
+PROP_NONE, PROP_LEARNED, PROP_HEURISTIC = 0, 1, 2
 
 
 class HmatError(RuntimeError):
@@ -44,7 +49,11 @@ class BuildOpts(ctypes.Structure):
 class MultOpts(ctypes.Structure):
     _fields_ = [("eps", ctypes.c_double), ("mode", ctypes.c_int), ("rank_proposal", ctypes.c_int),
                 ("max_rank", ctypes.c_int), ("max_rounds", ctypes.c_int), ("block_width", ctypes.c_int),
-                ("seed", ctypes.c_uint64)]
+                ("seed", ctypes.c_uint64), ("rank_model", ctypes.c_void_p)]
+
+
+class TrainOpts(ctypes.Structure):
+    _fields_ = [("epochs", ctypes.c_int), ("lr", ctypes.c_float), ("seed", ctypes.c_uint64)]
 
 
 class Leaf(ctypes.Structure):
@@ -65,7 +74,9 @@ class Stats(ctypes.Structure):
                 ("ms_sample", ctypes.c_double), ("ms_final", ctypes.c_double),
                 ("ms_apply", ctypes.c_double), ("apply_launches", ctypes.c_int64),
                 ("bytes_apply_use", ctypes.c_double), ("launches", ctypes.c_int64),
-                ("n_ff_jobs", ctypes.c_int64), ("n_panels", ctypes.c_int64)]
+                ("n_ff_jobs", ctypes.c_int64), ("n_panels", ctypes.c_int64),
+                ("first_round_cols", ctypes.c_int64), ("done_in_first_round", ctypes.c_int64),
+                ("sample_passes", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -75,6 +86,7 @@ _P = ctypes.c_void_p
 _I64 = ctypes.c_int64
 _PD = ctypes.POINTER(ctypes.c_double)
 _PI64 = ctypes.POINTER(ctypes.c_int64)
+_PF = ctypes.POINTER(ctypes.c_float)
 _lib = None
 
 
@@ -99,12 +111,22 @@ def lib():
     L.hmat_sumexpr_counts.argtypes = [_P, _P, _PI64, _PI64]
     L.hmat_data_bytes.argtypes = [_P, _PI64]
     L.hmat_data_get.argtypes = [_P, _P, _I64]
+    L.hmat_rank_features.argtypes = [_P, _P, ctypes.c_double, _P, _PF, _PF, _PI64]
+    L.hmat_rankmodel_train.argtypes = [_PF, _PF, _I64, ctypes.POINTER(TrainOpts), _P, ctypes.POINTER(_P)]
+    L.hmat_rankmodel_predict.argtypes = [_P, _PF, _I64, _PF]
+    L.hmat_rankmodel_get.argtypes = [_P, _PF, _PF, _PF, _PF]
+    L.hmat_rankmodel_create.argtypes = [_PF, _PF, _PF, ctypes.POINTER(_P)]
+    L.hmat_rankmodel_grad.argtypes = [_P, _PF, _PF, _I64, _PF, _PF]
+    L.hmat_rankmodel_destroy.argtypes = [_P]
+    L.hmat_rankmodel_destroy.restype = None
     L.hmat_destroy.argtypes = [_P]
     L.hmat_destroy.restype = None
     L.hmat_last_error.restype = ctypes.c_char_p
     for name in ["hmat_points", "hmat_build", "hmat_multiply", "hmat_to_dense", "hmat_leaf_count",
                  "hmat_leaf_info", "hmat_leaf_get", "hmat_permutation", "hmat_stats", "hmat_sumexpr_counts",
-                 "hmat_set_allocator", "hmat_data_bytes", "hmat_data_get"]:
+                 "hmat_set_allocator", "hmat_data_bytes", "hmat_data_get", "hmat_rank_features",
+                 "hmat_rankmodel_train", "hmat_rankmodel_predict", "hmat_rankmodel_get", "hmat_rankmodel_create",
+                 "hmat_rankmodel_grad"]:
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -222,8 +244,9 @@ def hmat_build(xyz: np.ndarray, kernel: int, leaf_size: int = 32, eta: float = 1
 
 def hmat_multiply(A: HMatrix, B: HMatrix, eps: float, mode: int = MODE_F64, rank_proposal: int = 0,
                   max_rank: int = 0, max_rounds: int = 0, block_width: int = 0, seed: int = 0,
-                  stream=None, allow_notconv: bool = True) -> HMatrix:
-    opts = MultOpts(eps, mode, rank_proposal, max_rank, max_rounds, block_width, seed)
+                  stream=None, allow_notconv: bool = True, rank_model: "RankModel | None" = None) -> HMatrix:
+    opts = MultOpts(eps, mode, rank_proposal, max_rank, max_rounds, block_width, seed,
+                    rank_model.handle if rank_model is not None else None)
     h = _P()
     st = lib().hmat_multiply(A.handle, B.handle, ctypes.byref(opts), _stream_ptr(stream), ctypes.byref(h))
     _check(st, allow=(HMAT_ENOTCONV,) if allow_notconv else ())
@@ -256,3 +279,81 @@ def leaf_arrays(H: HMatrix) -> LeafArrays:
     infos = H.leaves()
     f = lambda k: np.array([getattr(x, k) for x in infos], np.int64)
     return LeafArrays(f("row_begin"), f("row_size"), f("col_begin"), f("col_size"), f("far"), f("rank"), f("level"))
+
+
+def _f32(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+class RankModel:
+    """Owner of an hmat_rankmodel_t (the learned rank proposal); released with
+    hmat_rankmodel_destroy."""
+
+    def __init__(self, handle: int):
+        self._h = handle
+
+    def __del__(self):
+        self.close()
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().hmat_rankmodel_destroy(self._h)
+            self._h = None
+
+    @property
+    def handle(self):
+        return self._h
+
+    def predict(self, features) -> np.ndarray:
+        X = _f32(features)
+        out = np.zeros(X.shape[0], np.float32)
+        _check(lib().hmat_rankmodel_predict(self._h, X.ctypes.data_as(_PF), X.shape[0], out.ctypes.data_as(_PF)))
+        return out
+
+    def get(self):
+        """(weights, mean, dev, loss): the FP16 weights widened to float32, the feature
+        normalisation and the final training loss."""
+        w = np.zeros(RANK_PARAMS, np.float32)
+        mu = np.zeros(RANK_FEATURES, np.float32)
+        dv = np.zeros(RANK_FEATURES, np.float32)
+        loss = ctypes.c_float()
+        _check(lib().hmat_rankmodel_get(self._h, w.ctypes.data_as(_PF), mu.ctypes.data_as(_PF),
+                                        dv.ctypes.data_as(_PF), ctypes.byref(loss)))
+        return w, mu, dv, loss.value
+
+    def grad(self, features, ranks):
+        X, y = _f32(features), _f32(ranks)
+        g = np.zeros(RANK_PARAMS, np.float32)
+        loss = ctypes.c_float()
+        _check(lib().hmat_rankmodel_grad(self._h, X.ctypes.data_as(_PF), y.ctypes.data_as(_PF), X.shape[0],
+                                         g.ctypes.data_as(_PF), ctypes.byref(loss)))
+        return g, loss.value
+
+
+def hmat_rank_features(A: HMatrix, B: HMatrix, eps: float, C: HMatrix | None = None):
+    """(features n_far x RANK_FEATURES, ranks of C on those blocks or zeros)."""
+    n = ctypes.c_int64()
+    _check(lib().hmat_rank_features(A.handle, B.handle, eps, None, None, None, ctypes.byref(n)))
+    F = np.zeros((n.value, RANK_FEATURES), np.float32)
+    r = np.zeros(n.value, np.float32)
+    _check(lib().hmat_rank_features(A.handle, B.handle, eps, C.handle if C is not None else None,
+                                    F.ctypes.data_as(_PF), r.ctypes.data_as(_PF), ctypes.byref(n)))
+    return F, r
+
+
+def hmat_rankmodel_train(features, ranks, epochs: int = 0, lr: float = 0.0, seed: int = 0,
+                         stream=None) -> RankModel:
+    X, y = _f32(features), _f32(ranks)
+    opts = TrainOpts(epochs, lr, seed)
+    h = _P()
+    _check(lib().hmat_rankmodel_train(X.ctypes.data_as(_PF), y.ctypes.data_as(_PF), X.shape[0], ctypes.byref(opts),
+                                      _stream_ptr(stream), ctypes.byref(h)))
+    return RankModel(h.value)
+
+
+def hmat_rankmodel_create(weights, mean, dev) -> RankModel:
+    w, mu, dv = _f32(weights), _f32(mean), _f32(dev)
+    h = _P()
+    _check(lib().hmat_rankmodel_create(w.ctypes.data_as(_PF), mu.ctypes.data_as(_PF), dv.ctypes.data_as(_PF),
+                                       ctypes.byref(h)))
+    return RankModel(h.value)

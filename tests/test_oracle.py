@@ -345,3 +345,70 @@ def test_truth_eckart_young_invariant(oracle):
         s = np.linalg.svd(blk, compute_uv=False)
         if k > 0:
             assert np.sqrt(np.sum(s[k - 1:] ** 2)) > 1e-6 * nb * (1 - 1e-10)
+
+
+# ---------------------------------------------------------------- learned rank proposal network
+
+def _mlp_params(seed, scale=0.3):
+    from oracle import rank_mlp as R
+    return (inputs.uniform01(seed, R.N_PARAMS) * 2.0 - 1.0) * scale
+
+
+def test_mlp_gradient_finite_differences():
+    """Backpropagation against central differences of the loss, on every parameter group (a
+    transposed weight, a dropped ReLU mask or a missing 1/count factor all fail here)."""
+    from oracle import rank_mlp as R
+    w = _mlp_params(11)
+    X = (inputs.uniform01(12, 37 * R.F).reshape(37, R.F) * 2.0 - 1.0) * 2.0
+    t = inputs.uniform01(13, 37) * 5.0
+    L, g = R.loss_grad(w, X, t)
+    assert L == pytest.approx(R.loss(w, X, t), rel=1e-15)
+    idx = np.concatenate([np.arange(0, 40), np.arange(R.H * R.F, R.H * R.F + 8),
+                          np.arange(R.H * R.F + R.H + 100, R.H * R.F + R.H + 140),
+                          np.arange(R.N_PARAMS - 2 * R.H - 1, R.N_PARAMS)])
+    h = 1e-6
+    for i in idx:
+        wp, wm = w.copy(), w.copy()
+        wp[i] += h
+        wm[i] -= h
+        fd = (R.loss(wp, X, t) - R.loss(wm, X, t)) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-7 * max(1.0, abs(g[i])), i
+
+
+def test_mlp_zero_weights_closed_form():
+    """All weights zero: the output is b3 for every sample; the only non-zero gradient entry is
+    d/db3 = 2 mean(b3 - t)."""
+    from oracle import rank_mlp as R
+    w = np.zeros(R.N_PARAMS)
+    w[-1] = 1.75
+    X = inputs.uniform01(21, 10 * R.F).reshape(10, R.F)
+    t = inputs.uniform01(22, 10) * 4.0
+    assert np.all(R.forward(w, X) == 1.75)
+    L, g = R.loss_grad(w, X, t)
+    assert L == pytest.approx(np.mean((1.75 - t) ** 2), rel=1e-14)
+    assert g[-1] == pytest.approx(2.0 * np.mean(1.75 - t), rel=1e-14)
+    assert np.all(g[:-1] == 0.0)
+
+
+def test_mlp_linear_regime_is_affine_map():
+    """With positive inputs, non-negative weights and positive biases every ReLU passes its
+    input, so the network is the composed affine map w3.(W2 (W1 x + b1) + b2) + b3; and its
+    gradient with respect to w3 is 2/count * sum_s e_s h2_s."""
+    from oracle import rank_mlp as R
+    w = inputs.uniform01(31, R.N_PARAMS) * 0.2 + 0.01
+    W1, b1, W2, b2, w3, b3 = R.unpack(w)
+    X = inputs.uniform01(32, 9 * R.F).reshape(9, R.F)
+    t = inputs.uniform01(33, 9)
+    y = np.array([w3 @ (W2 @ (W1 @ x + b1) + b2) + b3 for x in X])
+    np.testing.assert_allclose(R.forward(w, X), y, rtol=1e-14)
+    _, g = R.loss_grad(w, X, t)
+    h2 = np.array([W2 @ (W1 @ x + b1) + b2 for x in X])
+    gw3 = 2.0 / 9 * ((y - t)[:, None] * h2).sum(0)
+    np.testing.assert_allclose(g[R.N_PARAMS - R.H - 1:R.N_PARAMS - 1], gw3, rtol=1e-12)
+
+
+def test_mlp_target_round_trip():
+    from oracle import rank_mlp as R
+    r = np.array([0, 1, 3, 7, 15, 96, -2], np.float64)
+    np.testing.assert_allclose(R.predicted_rank(R.target(r)), np.maximum(r, 0), atol=1e-12)
+    assert R.target(np.array([0.0]))[0] == 0.0 and R.target(np.array([3.0]))[0] == 2.0

@@ -241,6 +241,31 @@ hmat_status hmat_rankmodel_create(const float *weights, const float *mean, const
 hmat_status hmat_rankmodel_grad(const hmat_rankmodel_t m, const float *features, const float *ranks, int64_t count,
                                 float *grad, float *loss);
 
+/* The same gradient and loss as hmat_rankmodel_grad, computed without allocating any device
+ * memory (the paper has no counterpart of this call; it is a library convenience). It is for
+ * callers that must not allocate: code that runs under a fixed device-memory budget or beside
+ * an allocator it must not re-enter (a custom allocator hook that itself fine-tunes the model,
+ * a serving loop whose memory is reserved up front), where a stray allocation can fail or
+ * stall. Every device buffer of the call is part of one fixed array compiled into the library,
+ * HMAT_RANKGRAD_NOALLOC_MAX * (HMAT_RANK_FEATURES + 1) + HMAT_RANK_PARAMS + 1 floats (about
+ * 0.87 MB) per device:
+ *   - count must be 1 .. HMAT_RANKGRAD_NOALLOC_MAX; more samples -> HMAT_EINVAL, nothing runs;
+ *   - features (count x HMAT_RANK_FEATURES, row-major) and ranks (count) are raw host values,
+ *     standardised on the device with the model's mean and deviation; grad
+ *     (HMAT_RANK_PARAMS) and *loss are host outputs;
+ *   - the gradient and loss accumulators in the array are set to zero by every call before
+ *     it accumulates, so no state carries over between calls;
+ *   - the first call on a device (with that device current) looks up the array's device
+ *     address and sets the network kernel's shared-memory limit; make one call before any
+ *     stream capture begins;
+ *   - calls on one device share the array: two calls that overlap in time (other threads,
+ *     other streams) race on it and may return wrong results; serialise them;
+ *   - runs on stream (NULL = the default stream) and synchronises it before returning;
+ *   - m must live on the current device. */
+#define HMAT_RANKGRAD_NOALLOC_MAX 16384
+hmat_status hmat_rankmodel_grad_noalloc(const hmat_rankmodel_t m, const float *features, const float *ranks,
+                                        int64_t count, float *grad, float *loss, void *stream);
+
 void hmat_rankmodel_destroy(hmat_rankmodel_t m);
 
 /* Release h and its device memory (NULL is a no-op). */

@@ -249,6 +249,8 @@ bool same_points(const Tree &t, const double *xyz, int64_t n, int dim) {
 
 // ------------------------------------------------------------------ rank proposal
 
+static_assert(HMAT_RANKGRAD_NOALLOC_MAX == RANKGRAD_NOALLOC_MAX, "scratch capacity");
+
 struct hmat_rankmodel_s {
   float *w = nullptr;   // FP32 master weights (device)
   void *w16 = nullptr;  // FP16 weights used by the forward pass (device)
@@ -759,6 +761,17 @@ hmat_status hmat_rankmodel_grad(const hmat_rankmodel_t m, const float *features,
     ck(cudaMemcpyAsync(&l, dl.p, sizeof(float), cudaMemcpyDeviceToHost, nullptr), "gradient");
     ck(cudaStreamSynchronize(nullptr), "gradient");
     if (loss) *loss = l;
+  });
+}
+
+hmat_status hmat_rankmodel_grad_noalloc(const hmat_rankmodel_t m, const float *features, const float *ranks,
+                                        int64_t count, float *grad, float *loss, void *stream) {
+  return guard([&] {
+    if (!m || !features || !ranks || !grad || !loss || count < 1) fail(HMAT_EINVAL, "NULL argument or no samples");
+    if (count > HMAT_RANKGRAD_NOALLOC_MAX)
+      fail(HMAT_EINVAL, "count exceeds HMAT_RANKGRAD_NOALLOC_MAX (16384 samples), the capacity of the fixed scratch");
+    ck(mlp_grad_noalloc(m->w16, m->mean, m->dev, features, ranks, (int)count, grad, loss, (cudaStream_t)stream),
+       "gradient (fixed scratch)");
   });
 }
 

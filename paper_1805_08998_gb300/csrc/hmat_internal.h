@@ -184,5 +184,11 @@ cudaError_t launch_mlp_grad(const void *w16, const float *x, const float *y, int
 cudaError_t launch_to_half(const float *w, void *w16, cudaStream_t s);
 cudaError_t mlp_train(float *w, void *w16, const float *x, const float *y, int count, int epochs, float lr,
                       cudaStream_t s, float *final_loss);
+// Gradient and loss of the network on count <= RANKGRAD_NOALLOC_MAX samples given on the host
+// (raw features, raw ranks), normalised on the device, with every device buffer inside one
+// fixed-size __device__ array of hmat_rank.cu: no device allocation. Synchronises s.
+constexpr int RANKGRAD_NOALLOC_MAX = 16384;
+cudaError_t mlp_grad_noalloc(const void *w16, const float *mean, const float *dev, const float *features,
+                             const float *ranks, int count, float *grad, float *loss, cudaStream_t s);
 
 }  // namespace hm

@@ -6,6 +6,7 @@
 // it for the requested number of epochs.
 #include <cmath>
 #include <cstdint>
+#include <mutex>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
@@ -266,6 +267,75 @@ cudaError_t mlp_train(float *w, void *w16, const float *x, const float *y, int c
   e = cudaStreamSynchronize(cs);
   cleanup();
   return e;
+}
+
+// ---------------------------------------------------------------------------------------
+// Gradient without device allocation. Every device buffer of the call lives in the fixed
+// array below: features (RANKGRAD_NOALLOC_MAX x F), targets, the gradient and the loss.
+// (RANKGRAD_NOALLOC_MAX * 13 + RANK_PARAMS + 1 floats, about 0.87 MB per device.)
+// ---------------------------------------------------------------------------------------
+
+constexpr size_t NOALLOC_FLOATS = (size_t)RANKGRAD_NOALLOC_MAX * (F + 1) + RANK_PARAMS + 1;
+static __device__ __align__(256) float g_noalloc_scratch[NOALLOC_FLOATS];
+
+struct Standardise {
+  float mean[F], dev[F];
+};
+
+// in place: x <- (x - mean) / dev per feature; y <- log2(1 + max(y, 0))
+__global__ void k_standardise(float *x, float *y, int count, Standardise sd) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count * F) {
+    const int k = i % F;
+    x[i] = (x[i] - sd.mean[k]) / sd.dev[k];
+  }
+  if (i < count) y[i] = log2f(1.f + fmaxf(y[i], 0.f));
+}
+
+// The scratch array's device address, looked up once per device (with that device current) on
+// the first call made on it; later calls on the device reuse it.
+constexpr int NOALLOC_DEVICES = 64;
+static std::mutex g_noalloc_mu;
+static float *g_noalloc_ptr[NOALLOC_DEVICES];
+
+static cudaError_t noalloc_scratch(float **out) {
+  int d = 0;
+  cudaError_t e = cudaGetDevice(&d);
+  if (e != cudaSuccess) return e;
+  if (d < 0 || d >= NOALLOC_DEVICES) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[d]) {
+    float *p = nullptr;
+    if ((e = cudaGetSymbolAddress((void **)&p, g_noalloc_scratch)) != cudaSuccess) return e;
+    if ((e = set_mlp_smem()) != cudaSuccess) return e;
+    g_noalloc_ptr[d] = p;
+  }
+  *out = g_noalloc_ptr[d];
+  return cudaSuccess;
+}
+
+cudaError_t mlp_grad_noalloc(const void *w16, const float *mean, const float *dev, const float *features,
+                             const float *ranks, int count, float *grad, float *loss, cudaStream_t s) {
+  if (count < 1 || count > RANKGRAD_NOALLOC_MAX) return cudaErrorInvalidValue;
+  float *base = nullptr;
+  cudaError_t e = noalloc_scratch(&base);
+  if (e != cudaSuccess) return e;
+  float *x = base, *y = x + (size_t)RANKGRAD_NOALLOC_MAX * F;
+  float *g = y + RANKGRAD_NOALLOC_MAX, *l = g + RANK_PARAMS;
+  Standardise sd;
+  for (int k = 0; k < F; k++) {
+    sd.mean[k] = mean[k];
+    sd.dev[k] = dev[k];
+  }
+  if ((e = cudaMemcpyAsync(x, features, sizeof(float) * F * count, cudaMemcpyHostToDevice, s))) return e;
+  if ((e = cudaMemcpyAsync(y, ranks, sizeof(float) * count, cudaMemcpyHostToDevice, s))) return e;
+  k_standardise<<<(count * F + 255) / 256, 256, 0, s>>>(x, y, count, sd);
+  if ((e = cudaGetLastError())) return e;
+  // the gradient and the loss are accumulated with atomics: mlp_grad_ops first sets both to zero
+  if ((e = mlp_grad_ops(w16, x, y, count, g, l, s))) return e;
+  if ((e = cudaMemcpyAsync(grad, g, sizeof(float) * RANK_PARAMS, cudaMemcpyDeviceToHost, s))) return e;
+  if ((e = cudaMemcpyAsync(loss, l, sizeof(float), cudaMemcpyDeviceToHost, s))) return e;
+  return cudaStreamSynchronize(s);
 }
 
 }  // namespace hm

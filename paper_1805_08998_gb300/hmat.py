@@ -28,10 +28,11 @@ EXPORTS = ["hmat_points", "hmat_build", "hmat_multiply", "hmat_to_dense", "hmat_
            "hmat_leaf_get", "hmat_permutation", "hmat_stats", "hmat_sumexpr_counts", "hmat_destroy",
            "hmat_data_bytes", "hmat_data_get", "hmat_rank_features", "hmat_rankmodel_train",
            "hmat_rankmodel_predict", "hmat_rankmodel_get", "hmat_rankmodel_create", "hmat_rankmodel_grad",
-           "hmat_rankmodel_destroy", "hmat_last_error", "hmat_set_allocator"]
+           "hmat_rankmodel_grad_noalloc", "hmat_rankmodel_destroy", "hmat_last_error", "hmat_set_allocator"]
 
 RANK_FEATURES = 12
 RANK_PARAMS = 5057
+RANKGRAD_NOALLOC_MAX = 16384
 PROP_NONE, PROP_LEARNED, PROP_HEURISTIC = 0, 1, 2
 
 
@@ -117,6 +118,7 @@ def lib():
     L.hmat_rankmodel_get.argtypes = [_P, _PF, _PF, _PF, _PF]
     L.hmat_rankmodel_create.argtypes = [_PF, _PF, _PF, ctypes.POINTER(_P)]
     L.hmat_rankmodel_grad.argtypes = [_P, _PF, _PF, _I64, _PF, _PF]
+    L.hmat_rankmodel_grad_noalloc.argtypes = [_P, _PF, _PF, _I64, _PF, _PF, _P]
     L.hmat_rankmodel_destroy.argtypes = [_P]
     L.hmat_rankmodel_destroy.restype = None
     L.hmat_destroy.argtypes = [_P]
@@ -126,7 +128,7 @@ def lib():
                  "hmat_leaf_info", "hmat_leaf_get", "hmat_permutation", "hmat_stats", "hmat_sumexpr_counts",
                  "hmat_set_allocator", "hmat_data_bytes", "hmat_data_get", "hmat_rank_features",
                  "hmat_rankmodel_train", "hmat_rankmodel_predict", "hmat_rankmodel_get", "hmat_rankmodel_create",
-                 "hmat_rankmodel_grad"]:
+                 "hmat_rankmodel_grad", "hmat_rankmodel_grad_noalloc"]:
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -328,6 +330,17 @@ class RankModel:
         _check(lib().hmat_rankmodel_grad(self._h, X.ctypes.data_as(_PF), y.ctypes.data_as(_PF), X.shape[0],
                                          g.ctypes.data_as(_PF), ctypes.byref(loss)))
         return g, loss.value
+
+
+def hmat_rankmodel_grad_noalloc(model: RankModel, features, ranks, stream=None):
+    """hmat_rankmodel_grad without device allocation (fixed scratch; at most
+    RANKGRAD_NOALLOC_MAX samples; concurrent calls on one device race)."""
+    X, y = _f32(features), _f32(ranks)
+    g = np.zeros(RANK_PARAMS, np.float32)
+    loss = ctypes.c_float()
+    _check(lib().hmat_rankmodel_grad_noalloc(model.handle, X.ctypes.data_as(_PF), y.ctypes.data_as(_PF), X.shape[0],
+                                             g.ctypes.data_as(_PF), ctypes.byref(loss), _stream_ptr(stream)))
+    return g, loss.value
 
 
 def hmat_rank_features(A: HMatrix, B: HMatrix, eps: float, C: HMatrix | None = None):

@@ -900,7 +900,7 @@ void Product::run() {
   int pcw_rows = 1;
   for (const LeafDev &l : A->leaves) pcw_rows = std::max(pcw_rows, (int)l.rank);
   for (const LeafDev &l : B->leaves) pcw_rows = std::max(pcw_rows, (int)l.rank);
-  const size_t pcw_bytes = (size_t)8 * pcw_rows * PW * es;
+  const size_t pcw_bytes = (size_t)8 * pcw_rows * panel_row_stride(PW) * es;
   const size_t nterm = plan.terms.size();
   std::vector<TermJob> &jobs = jobs_tl;
   jobs.resize(nterm);
@@ -935,7 +935,7 @@ void Product::run() {
       int bkt = 1;
       while ((64 << (bkt - 1)) < dmx && bkt < NB) bkt++;
       const int cap = 64 << (bkt - 1);
-      if (cap >= dmx && (size_t)(2 * cap) * PW * es + pcw_bytes <= smem_cap) return bkt;
+      if (cap >= dmx && (size_t)(2 * cap) * panel_row_stride(PW) * es + pcw_bytes <= smem_cap) return bkt;
       return NB + 1;
     };
     auto rows_of = [&](const PlanTerm &pt) -> int64_t {
@@ -1044,7 +1044,7 @@ void Product::run() {
                       A->d_leaves.as<LeafDev>(), B->d_leaves.as<LeafDev>(), t.d_blocks, dataA, dataB, d_termbuf.p, s),
      "far x far products");
   int64_t launches = 1 + (ff_ids.empty() ? 0 : 1);
-  const int64_t pstride = (int64_t)2 * pdim[NB + 1] * PW;
+  const int64_t pstride = (int64_t)2 * pdim[NB + 1] * panel_row_stride(PW);
   DevBuf d_pstage(es * std::max<int64_t>(pstride * (int64_t)pk[NB + 1].size(), 1), s);
   for (int k = 0; k < NB + 2; k++) {
     if (pk[k].empty()) continue;
@@ -1137,7 +1137,7 @@ void Product::run() {
   const int P = apply_panel_width(pmax);
   int cw_rows = std::max(t.leaf_size, pcw_rows);
   for (const PlanTerm &pt : plan.terms) cw_rows = std::max(cw_rows, (int)pt.rank);
-  const size_t cw_bytes = (size_t)8 * cw_rows * P * es;
+  const size_t cw_bytes = (size_t)8 * cw_rows * apply_row_stride(P) * es;
   std::vector<int> rho_inner(t.leaf_block.size(), 0), klass(t.leaf_block.size(), 1);
   auto is_leaf_pair = [&](const PairDev &pr) {
     return t.bl[pr.blkA].kind == BK_NEAR && t.bl[pr.blkB].kind == BK_NEAR;
@@ -1156,7 +1156,7 @@ void Product::run() {
     const int cap = 32 << (c - 1);
     const int rb = apply_rows_per_lane(cap);
     const size_t zrows = rb > 0 ? std::max(cap, 8 * cap) : cap;
-    if (cap < dmax || (size_t)(2 * cap + zrows) * P * es + cw_bytes > smem_cap) c = 0;
+    if (cap < dmax || (size_t)(2 * cap + zrows) * apply_row_stride(P) * es + cw_bytes > smem_cap) c = 0;
     klass[l] = c;
   }
   // within a class, depth-first leaf order: neighbouring targets share the low-rank terms of
@@ -1167,6 +1167,28 @@ void Product::run() {
   });
 
   tr.mark("target classes + sort");
+  if (tr.on) {  // per class: targets, low-rank and H-pair elements, term and inner-pair counts
+    double lr[NCLS] = {}, lp[NCLS] = {}, ip[NCLS] = {};
+    int64_t cnt[NCLS] = {}, nt[NCLS] = {}, nip[NCLS] = {};
+    for (const Tgt &g : far) {
+      const int l = g.leaf, c = klass[l], b = t.leaf_block[l];
+      const LeafDev &lc = A->leaves[l];
+      cnt[c]++;
+      nt[c] += plan.nterm_cum[b];
+      lr[c] += (double)plan.rank_cum[b] * (lc.m + lc.n);
+      for (int64_t q = plan.leaf_pair_off[l]; q < plan.leaf_pair_off[l + 1]; q++) {
+        const PairDev &pr = plan.leaf_pairs[q];
+        const double e = storA[pr.blkA] + storB[pr.blkB];
+        if (is_leaf_pair(pr)) lp[c] += e;
+        else { ip[c] += e; nip[c]++; }
+      }
+    }
+    for (int c = 0; c < NCLS; c++)
+      if (cnt[c])
+        std::fprintf(stderr, "hmat trace: class %2d: %7lld targets, %9lld terms, %.3g lr elems, %.3g leaf-pair elems, "
+                     "%.3g inner-pair elems (%lld pairs)\n", c, (long long)cnt[c], (long long)nt[c], lr[c], lp[c], ip[c],
+                     (long long)nip[c]);
+  }
   auto make_targets = [&](const std::vector<Tgt> &tv, std::vector<TargetDev> &tg, std::vector<PairDev> &tpairs) {
     tg.resize(tv.size());
     for (size_t i = 0; i < tv.size(); i++) {
@@ -1223,7 +1245,7 @@ void Product::run() {
     cl.rho = std::max(cl.rho, rho_inner[d.leaf]);
     if (c == 0) {
       d.stage_off = stage_elems;
-      stage_elems += ((int64_t)d.m + d.n + rho_inner[d.leaf]) * P;
+      stage_elems += ((int64_t)d.m + d.n + rho_inner[d.leaf]) * apply_row_stride(P);
     }
   }
 
@@ -1305,6 +1327,12 @@ void Product::run() {
     std::vector<cudaEvent_t> &v;
     ~AevGuard() { for (auto e : v) cudaEventDestroy(e); }
   } aevg{aev};
+  struct ClassTiming {
+    int c;
+    bool trans;
+    cudaEvent_t e0, e1;
+  };
+  std::vector<ClassTiming> ctim;  // per-class launch events (HMAT_TRACE only)
   auto timed_apply = [&](bool trans) {
     cudaEvent_t e0, e1;
     ck(cudaEventCreate(&e0), "event");
@@ -1323,7 +1351,17 @@ void Product::run() {
       if (c > 0 && apply_rows_per_lane(cls[c].dmax) > 0) ac.smem_rho = std::max(ac.smem_rho, 8 * cls[c].dmax);
       ac.smem_cw = cw_rows;
       ac.gstage = c == 0 ? 1 : 0;
+      ClassTiming ct{c, trans, nullptr, nullptr};
+      if (tr.on) {
+        cudaEventCreate(&ct.e0);
+        cudaEventCreate(&ct.e1);
+        cudaEventRecord(ct.e0, s);
+      }
       ck(launch_apply(cprec, trans, ac, s), trans ? "apply S^T" : "apply S");
+      if (tr.on) {
+        cudaEventRecord(ct.e1, s);
+        ctim.push_back(ct);
+      }
       launches++;
     }
     ck(cudaEventRecord(e1, s), "event");
@@ -1351,6 +1389,21 @@ void Product::run() {
     if (act == 0) break;
   }
   tr.mark("sampling rounds done");
+  if (tr.on) {
+    double tc[NCLS][2] = {};
+    cudaStreamSynchronize(s);
+    for (ClassTiming &ct : ctim) {
+      float x = 0.f;
+      cudaEventElapsedTime(&x, ct.e0, ct.e1);
+      tc[ct.c][ct.trans ? 1 : 0] += x;
+      cudaEventDestroy(ct.e0);
+      cudaEventDestroy(ct.e1);
+    }
+    for (int c = 0; c < NCLS; c++)
+      if (cls[c].count)
+        std::fprintf(stderr, "hmat trace: class %2d apply: S %8.3f ms, S^T %8.3f ms (all rounds)\n", c, tc[c][0],
+                     tc[c][1]);
+  }
   ck(cudaEventRecord(ev[2], s), "event");
   std::vector<TargetState> st(nf);
   if (nf) ck(cudaMemcpyAsync(st.data(), d_st.p, sizeof(TargetState) * nf, cudaMemcpyDeviceToHost, s), "states");

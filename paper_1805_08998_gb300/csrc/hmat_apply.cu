@@ -15,8 +15,9 @@ int panel_width() { return 16; }
 
 size_t apply_smem_bytes(int prec, int P, const ApplyArgs &a) {
   const size_t es = prec == 64 ? 8 : 4;
-  const size_t cw = (size_t)8 * a.smem_cw * P * es;
-  return a.gstage ? cw : (size_t)(a.smem_in + a.smem_out + a.smem_rho) * P * es + cw;
+  const size_t SP = apply_row_stride(P);
+  const size_t cw = (size_t)8 * a.smem_cw * SP * es;
+  return a.gstage ? cw : (size_t)(a.smem_in + a.smem_out + a.smem_rho) * SP * es + cw;
 }
 
 cudaError_t launch_apply(int prec, bool trans, const ApplyArgs &a, cudaStream_t s) {

@@ -31,11 +31,11 @@ __device__ __forceinline__ void acc_add(T *p, T v, bool atomic) {
   else *p = v;
 }
 
-// out[q*osr + c*osc] (+)= sum_{i < len} M[i + q*ldm] * X[i*P + c]  for q < r, c < P (only
-// c < ncol stored). With r <= 32/G, G lanes share column q (rows split round-robin) and are
-// combined by shuffles, so narrow ranks still use the whole warp. Default strides: row-major
-// panel (osr = P, osc = 1).
-template <typename T, int P, int G, bool ATOMIC>
+// out[q*osr + c*osc] (+)= sum_{i < len} M[i + q*ldm] * X[i*SP + c]  for q < r, c < P (only
+// c < ncol stored; SP = the panel's row stride). With r <= 32/G, G lanes share column q (rows split
+// round-robin) and are combined by shuffles, so narrow ranks still use the whole warp. Default
+// strides: row-major panel (osr = SP, osc = 1).
+template <typename T, int P, int G, bool ATOMIC, int SP>
 __device__ __forceinline__ void warp_tn_g(T *out, const T *__restrict__ M, int64_t ldm, const T *X, int len, int r,
                                           int64_t osr, int64_t osc, int ncol) {
   const int lane = threadIdx.x & 31;
@@ -49,23 +49,36 @@ __device__ __forceinline__ void warp_tn_g(T *out, const T *__restrict__ M, int64
     if (q < r) {
       const T *mc = M + (int64_t)q * ldm;
       int i = g;
+      for (; i + 7 * G < len; i += 8 * G) {  // eight independent loads in flight per lane
+        T mv[8];
+#pragma unroll
+        for (int u = 0; u < 8; u++) mv[u] = __ldg(mc + i + u * G);
+        const T *x = X + i * SP;
+#pragma unroll
+        for (int c = 0; c < P; c++) {
+          T s = acc[c];
+#pragma unroll
+          for (int u = 0; u < 8; u++) s += mv[u] * x[u * G * SP + c];
+          acc[c] = s;
+        }
+      }
       for (; i + 3 * G < len; i += 4 * G) {
         const T m0 = __ldg(mc + i), m1 = __ldg(mc + i + G), m2 = __ldg(mc + i + 2 * G), m3 = __ldg(mc + i + 3 * G);
-        const T *x = X + i * P;
+        const T *x = X + i * SP;
 #pragma unroll
         for (int c = 0; c < P; c++) {
           T s = acc[c];
           s += m0 * x[c];
-          s += m1 * x[G * P + c];
-          s += m2 * x[2 * G * P + c];
-          s += m3 * x[3 * G * P + c];
+          s += m1 * x[G * SP + c];
+          s += m2 * x[2 * G * SP + c];
+          s += m3 * x[3 * G * SP + c];
           acc[c] = s;
         }
       }
       for (; i < len; i += G) {
         const T m0 = __ldg(mc + i);
 #pragma unroll
-        for (int c = 0; c < P; c++) acc[c] += m0 * X[i * P + c];
+        for (int c = 0; c < P; c++) acc[c] += m0 * X[i * SP + c];
       }
     }
 #pragma unroll
@@ -80,19 +93,19 @@ __device__ __forceinline__ void warp_tn_g(T *out, const T *__restrict__ M, int64
   }
 }
 
-template <typename T, int P, bool ATOMIC>
+template <typename T, int P, bool ATOMIC, int SP>
 __device__ __forceinline__ void warp_tn(T *out, const T *__restrict__ M, int64_t ldm, const T *X, int len, int r,
-                                        int64_t osr = P, int64_t osc = 1, int ncol = P) {
-  if (r <= 4) warp_tn_g<T, P, 8, ATOMIC>(out, M, ldm, X, len, r, osr, osc, ncol);
-  else if (r <= 8) warp_tn_g<T, P, 4, ATOMIC>(out, M, ldm, X, len, r, osr, osc, ncol);
-  else if (r <= 16) warp_tn_g<T, P, 2, ATOMIC>(out, M, ldm, X, len, r, osr, osc, ncol);
-  else warp_tn_g<T, P, 1, ATOMIC>(out, M, ldm, X, len, r, osr, osc, ncol);
+                                        int64_t osr = SP, int64_t osc = 1, int ncol = P) {
+  if (r <= 4) warp_tn_g<T, P, 8, ATOMIC, SP>(out, M, ldm, X, len, r, osr, osc, ncol);
+  else if (r <= 8) warp_tn_g<T, P, 4, ATOMIC, SP>(out, M, ldm, X, len, r, osr, osc, ncol);
+  else if (r <= 16) warp_tn_g<T, P, 2, ATOMIC, SP>(out, M, ldm, X, len, r, osr, osc, ncol);
+  else warp_tn_g<T, P, 1, ATOMIC, SP>(out, M, ldm, X, len, r, osr, osc, ncol);
 }
 
-// out[i*osr + c*osc] (+)= sum_{q < r} M[i + q*ldm] * C[q*P + c]  for i < rows; lane owns rows.
-template <typename T, int P, bool ATOMIC>
+// out[i*osr + c*osc] (+)= sum_{q < r} M[i + q*ldm] * C[q*SP + c]  for i < rows; lane owns rows.
+template <typename T, int P, bool ATOMIC, int SP>
 __device__ __forceinline__ void warp_nn(T *out, const T *__restrict__ M, int64_t ldm, const T *C, int rows, int r,
-                                        int64_t osr = P, int64_t osc = 1, int ncol = P) {
+                                        int64_t osr = SP, int64_t osc = 1, int ncol = P) {
   const int lane = threadIdx.x & 31;
   for (int i0 = 0; i0 < rows; i0 += 64) {
     const int ia = i0 + lane, ib = i0 + 32 + lane;
@@ -101,14 +114,33 @@ __device__ __forceinline__ void warp_nn(T *out, const T *__restrict__ M, int64_t
 #pragma unroll
     for (int c = 0; c < P; c++) { a[c] = T(0); b[c] = T(0); }
     int q = 0;
+    for (; q + 4 <= r; q += 4) {  // eight independent loads in flight per lane
+      T xv[4], yv[4];
+#pragma unroll
+      for (int u = 0; u < 4; u++) {
+        const T *mu = M + (int64_t)(q + u) * ldm;
+        xv[u] = va ? __ldg(mu + ia) : T(0);
+        yv[u] = vb ? __ldg(mu + ib) : T(0);
+      }
+      const T *c0 = C + q * SP;
+#pragma unroll
+      for (int c = 0; c < P; c++) {
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+          const T cv = c0[u * SP + c];
+          a[c] += xv[u] * cv;
+          b[c] += yv[u] * cv;
+        }
+      }
+    }
     for (; q + 2 <= r; q += 2) {
       const T *m0 = M + (int64_t)q * ldm, *m1 = m0 + ldm;
       const T x0 = va ? __ldg(m0 + ia) : T(0), y0 = vb ? __ldg(m0 + ib) : T(0);
       const T x1 = va ? __ldg(m1 + ia) : T(0), y1 = vb ? __ldg(m1 + ib) : T(0);
-      const T *c0 = C + q * P;
+      const T *c0 = C + q * SP;
 #pragma unroll
       for (int c = 0; c < P; c++) {
-        const T u = c0[c], v = c0[P + c];
+        const T u = c0[c], v = c0[SP + c];
         a[c] += x0 * u;
         b[c] += y0 * u;
         a[c] += x1 * v;
@@ -120,8 +152,8 @@ __device__ __forceinline__ void warp_nn(T *out, const T *__restrict__ M, int64_t
       const T x0 = va ? __ldg(m0 + ia) : T(0), y0 = vb ? __ldg(m0 + ib) : T(0);
 #pragma unroll
       for (int c = 0; c < P; c++) {
-        a[c] += x0 * C[q * P + c];
-        b[c] += y0 * C[q * P + c];
+        a[c] += x0 * C[q * SP + c];
+        b[c] += y0 * C[q * SP + c];
       }
     }
     if (va)
@@ -138,35 +170,54 @@ __device__ __forceinline__ void warp_nn(T *out, const T *__restrict__ M, int64_t
 // One leaf of an H-matrix block with origin (row0, col0):
 //   trans = false: Out[rows of leaf] += leaf   * X[cols of leaf]
 //   trans = true:  Out[cols of leaf] += leaf^T * X[rows of leaf]
-template <typename T, int P>
+template <typename T, int P, int SP>
 __device__ __forceinline__ void warp_leaf(const LeafDev &lf, const T *data, bool trans, int64_t row0, int64_t col0,
                                           const T *X, T *Out, T *cw) {
   const int ro = (int)(lf.row - row0), co = (int)(lf.col - col0);
   if (lf.rank < 0) {
     const T *D = data + lf.off_u;
-    if (!trans) warp_nn<T, P, true>(Out + ro * P, D, lf.m, X + co * P, lf.m, lf.n);
-    else warp_tn<T, P, true>(Out + co * P, D, lf.m, X + ro * P, lf.m, lf.n);
+    if (!trans) warp_nn<T, P, true, SP>(Out + ro * SP, D, lf.m, X + co * SP, lf.m, lf.n);
+    else warp_tn<T, P, true, SP>(Out + co * SP, D, lf.m, X + ro * SP, lf.m, lf.n);
   } else if (lf.rank > 0) {
     const T *U = data + lf.off_u, *V = data + lf.off_v;
     if (!trans) {
-      warp_tn<T, P, false>(cw, V, lf.n, X + co * P, lf.n, lf.rank);
+      warp_tn<T, P, false, SP>(cw, V, lf.n, X + co * SP, lf.n, lf.rank);
       __syncwarp();
-      warp_nn<T, P, true>(Out + ro * P, U, lf.m, cw, lf.m, lf.rank);
+      warp_nn<T, P, true, SP>(Out + ro * SP, U, lf.m, cw, lf.m, lf.rank);
     } else {
-      warp_tn<T, P, false>(cw, U, lf.m, X + ro * P, lf.m, lf.rank);
+      warp_tn<T, P, false, SP>(cw, U, lf.m, X + ro * SP, lf.m, lf.rank);
       __syncwarp();
-      warp_nn<T, P, true>(Out + co * P, V, lf.n, cw, lf.n, lf.rank);
+      warp_nn<T, P, true, SP>(Out + co * SP, V, lf.n, cw, lf.n, lf.rank);
     }
     __syncwarp();
   }
 }
 
-// acc[rr][c] += sum_{q < r} M[lane + 32 rr + q*ldm] * C[q*P + c], rows < rows (lane owns rows)
-template <typename T, int P, int RB>
+// acc[rr][c] += sum_{q < r} M[lane + 32 rr + q*ldm] * C[q*SP + c], rows < rows (lane owns rows)
+template <typename T, int P, int RB, int SP>
 __device__ __forceinline__ void warp_nn_reg(T (&acc)[RB][P], const T *__restrict__ M, int64_t ldm, const T *C, int rows,
                                             int r) {
   const int lane = threadIdx.x & 31;
-  for (int q = 0; q < r; q++) {
+  int q = 0;
+  for (; q + 2 <= r; q += 2) {  // 2 RB independent loads in flight per lane
+    const T *mq = M + (int64_t)q * ldm;
+    T mv[2][RB];
+#pragma unroll
+    for (int u = 0; u < 2; u++)
+#pragma unroll
+      for (int rr = 0; rr < RB; rr++) {
+        const int i = lane + 32 * rr;
+        mv[u][rr] = i < rows ? __ldg(mq + u * ldm + i) : T(0);
+      }
+    const T *cq = C + q * SP;
+#pragma unroll
+    for (int c = 0; c < P; c++) {
+      const T c0 = cq[c], c1 = cq[SP + c];
+#pragma unroll
+      for (int rr = 0; rr < RB; rr++) acc[rr][c] += mv[0][rr] * c0 + mv[1][rr] * c1;
+    }
+  }
+  for (; q < r; q++) {
     const T *mq = M + (int64_t)q * ldm;
     T mv[RB];
 #pragma unroll
@@ -174,7 +225,7 @@ __device__ __forceinline__ void warp_nn_reg(T (&acc)[RB][P], const T *__restrict
       const int i = lane + 32 * rr;
       mv[rr] = i < rows ? __ldg(mq + i) : T(0);
     }
-    const T *cq = C + q * P;
+    const T *cq = C + q * SP;
 #pragma unroll
     for (int c = 0; c < P; c++) {
       const T cv = cq[c];
@@ -191,29 +242,30 @@ __global__ void __launch_bounds__(AT) k_apply(ApplyArgs a) {
   if (a.state[b].active == 0) return;  // uniform over the block
   const TargetDev t = a.tg[b];
   const int inlen = TRANS ? t.m : t.n, outlen = TRANS ? t.n : t.m;
+  constexpr int SP = apply_row_stride(P);
   T *sm = (T *)smem_raw;
   T *Xs, *Ys, *Zs, *cwall;
   if (GSTAGE) {
     Xs = (T *)a.stage_base + t.stage_off;
-    Ys = Xs + (int64_t)inlen * P;
-    Zs = Ys + (int64_t)outlen * P;
+    Ys = Xs + (int64_t)inlen * SP;
+    Zs = Ys + (int64_t)outlen * SP;
     cwall = sm;
   } else {
     Xs = sm;
-    Ys = Xs + a.smem_in * P;
-    Zs = Ys + a.smem_out * P;  // H-pair intermediate, or (RB > 0) the warps' partial outputs
-    cwall = Zs + a.smem_rho * P;
+    Ys = Xs + a.smem_in * SP;
+    Zs = Ys + a.smem_out * SP;  // H-pair intermediate, or (RB > 0) the warps' partial outputs
+    cwall = Zs + a.smem_rho * SP;
   }
   const int warp = threadIdx.x >> 5;
-  T *cw = cwall + warp * a.smem_cw * P;
+  T *cw = cwall + warp * a.smem_cw * SP;
   const T *X = (const T *)a.x_base + t.x_off;  // column-major inlen x p
   T *Out = (T *)a.y_base + t.y_off;            // column-major outlen x p
   const int p = a.round == 0 ? t.p0 : a.p;     // this target's columns this round (<= P)
   for (int o = threadIdx.x; o < inlen * P; o += AT) {
     const int i = o / P, c = o - i * P;
-    Xs[o] = c < p ? X[i + (int64_t)c * inlen] : T(0);
+    Xs[i * SP + c] = c < p ? X[i + (int64_t)c * inlen] : T(0);
   }
-  for (int o = threadIdx.x; o < outlen * P; o += AT) Ys[o] = T(0);
+  for (int o = threadIdx.x; o < outlen * SP; o += AT) Ys[o] = T(0);
   __syncthreads();
 
   // low-rank terms (those created at the target's block and its ancestors), warp per term.
@@ -238,10 +290,10 @@ __global__ void __launch_bounds__(AT) k_apply(ApplyArgs a) {
       const T *red = TRANS ? L : R;   // the factor contracted with the input panel
       const T *exp = TRANS ? R : L;   // the factor that expands into the output
       const int64_t ldred = TRANS ? tm.ldL : tm.ldR, ldexp = TRANS ? tm.ldR : tm.ldL;
-      warp_tn<T, P, false>(cw, red, ldred, Xs, inlen, tm.rank);
+      warp_tn<T, P, false, SP>(cw, red, ldred, Xs, inlen, tm.rank);
       __syncwarp();
-      if (RB > 0) warp_nn_reg<T, P, RBX>(racc, exp, ldexp, cw, outlen, tm.rank);
-      else warp_nn<T, P, true>(Ys, exp, ldexp, cw, outlen, tm.rank);
+      if (RB > 0) warp_nn_reg<T, P, RBX, SP>(racc, exp, ldexp, cw, outlen, tm.rank);
+      else warp_nn<T, P, true, SP>(Ys, exp, ldexp, cw, outlen, tm.rank);
       __syncwarp();
     }
   }
@@ -254,32 +306,32 @@ __global__ void __launch_bounds__(AT) k_apply(ApplyArgs a) {
     const T *DB = (const T *)a.dataB + lb.off_u;  // rho x n, ld rho
     const int rho = la.n;
     if (!TRANS) {
-      warp_nn<T, P, false>(cw, DB, rho, Xs, rho, lb.n);   // cw = D_B X      (rho x P)
+      warp_nn<T, P, false, SP>(cw, DB, rho, Xs, rho, lb.n);   // cw = D_B X      (rho x P)
       __syncwarp();
-      if (RB > 0) warp_nn_reg<T, P, RBX>(racc, DA, la.m, cw, la.m, rho);
-      else warp_nn<T, P, true>(Ys, DA, la.m, cw, la.m, rho);   // Y += D_A cw
+      if (RB > 0) warp_nn_reg<T, P, RBX, SP>(racc, DA, la.m, cw, la.m, rho);
+      else warp_nn<T, P, true, SP>(Ys, DA, la.m, cw, la.m, rho);   // Y += D_A cw
     } else {
-      warp_tn<T, P, false>(cw, DA, la.m, Xs, la.m, rho);  // cw = D_A^T Q    (rho x P)
+      warp_tn<T, P, false, SP>(cw, DA, la.m, Xs, la.m, rho);  // cw = D_A^T Q    (rho x P)
       __syncwarp();
-      warp_tn<T, P, true>(Ys, DB, rho, cw, rho, lb.n);    // W += D_B^T cw
+      warp_tn<T, P, true, SP>(Ys, DB, rho, cw, rho, lb.n);    // W += D_B^T cw
     }
     __syncwarp();
   }
   if (RB > 0) {
     // fixed-order sum of the warps' register partials (deterministic), through the scratch
-    T *part = Zs;  // NWARP * outlen * P entries reserved for RB > 0 launches
+    T *part = Zs;  // NWARP * outlen * SP entries reserved for RB > 0 launches
     const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int rr = 0; rr < RBX; rr++) {
       const int i = lane + 32 * rr;
       if (i < outlen)
 #pragma unroll
-        for (int c = 0; c < P; c++) part[(warp * outlen + i) * P + c] = racc[rr][c];
+        for (int c = 0; c < P; c++) part[(warp * outlen + i) * SP + c] = racc[rr][c];
     }
     __syncthreads();
-    for (int o = threadIdx.x; o < outlen * P; o += AT) {
+    for (int o = threadIdx.x; o < outlen * SP; o += AT) {
       T v = Ys[o];
-      for (int w2 = 0; w2 < NWARP; w2++) v += part[w2 * outlen * P + o];
+      for (int w2 = 0; w2 < NWARP; w2++) v += part[w2 * outlen * SP + o];
       Ys[o] = v;
     }
     __syncthreads();
@@ -291,26 +343,26 @@ __global__ void __launch_bounds__(AT) k_apply(ApplyArgs a) {
     const BlockDev ba = a.blocks[pr.blkA], bb = a.blocks[pr.blkB];
     const int rho = ba.n;
     __syncthreads();
-    for (int o = threadIdx.x; o < rho * P; o += AT) Zs[o] = T(0);
+    for (int o = threadIdx.x; o < rho * SP; o += AT) Zs[o] = T(0);
     __syncthreads();
     if (!TRANS) {
       for (int l = bb.leaf_lo + warp; l < bb.leaf_hi; l += NWARP)
-        warp_leaf<T, P>(a.leafB[l], (const T *)a.dataB, false, bb.row, bb.col, Xs, Zs, cw);
+        warp_leaf<T, P, SP>(a.leafB[l], (const T *)a.dataB, false, bb.row, bb.col, Xs, Zs, cw);
       __syncthreads();
       for (int l = ba.leaf_lo + warp; l < ba.leaf_hi; l += NWARP)
-        warp_leaf<T, P>(a.leafA[l], (const T *)a.dataA, false, ba.row, ba.col, Zs, Ys, cw);
+        warp_leaf<T, P, SP>(a.leafA[l], (const T *)a.dataA, false, ba.row, ba.col, Zs, Ys, cw);
     } else {
       for (int l = ba.leaf_lo + warp; l < ba.leaf_hi; l += NWARP)
-        warp_leaf<T, P>(a.leafA[l], (const T *)a.dataA, true, ba.row, ba.col, Xs, Zs, cw);
+        warp_leaf<T, P, SP>(a.leafA[l], (const T *)a.dataA, true, ba.row, ba.col, Xs, Zs, cw);
       __syncthreads();
       for (int l = bb.leaf_lo + warp; l < bb.leaf_hi; l += NWARP)
-        warp_leaf<T, P>(a.leafB[l], (const T *)a.dataB, true, bb.row, bb.col, Zs, Ys, cw);
+        warp_leaf<T, P, SP>(a.leafB[l], (const T *)a.dataB, true, bb.row, bb.col, Zs, Ys, cw);
     }
   }
   __syncthreads();
   for (int o = threadIdx.x; o < outlen * p; o += AT) {
     const int c = o / outlen, i = o - c * outlen;
-    Out[o] = Ys[i * P + c];
+    Out[o] = Ys[i * SP + c];
   }
 }
 
@@ -352,12 +404,12 @@ __device__ __forceinline__ PanelJob panel_job(const PanelArgs &a, const PanelDev
   return q;
 }
 
-template <typename T, int P>
+template <typename T, int P, int SP>
 __device__ __forceinline__ void panel_stage(T *Xs, const PanelJob &q, int inlen, const T *src, int lane0,
                                             int nthreads) {
   for (int o = lane0; o < inlen * P; o += nthreads) {
     const int i = o / P, c = o - i * P;
-    Xs[o] = c < q.ncol ? src[q.src + (int64_t)c * q.src_ld + i] : T(0);
+    Xs[i * SP + c] = c < q.ncol ? src[q.src + (int64_t)c * q.src_ld + i] : T(0);
   }
 }
 
@@ -375,18 +427,19 @@ __global__ void __launch_bounds__(AT) k_panel_leaf(PanelArgs a) {
   const LeafDev lf = (trans ? a.leafB : a.leafA)[bk.leaf_lo];
   const T *D = (const T *)(trans ? a.dataB : a.dataA) + lf.off_u;
   const T *src = (const T *)(trans ? a.dataA : a.dataB);
-  T *Xs = (T *)smem_raw + warp * (a.smem_in + a.smem_out) * P;
-  T *Os = Xs + a.smem_in * P;
+  constexpr int SP = panel_row_stride(P);
+  T *Xs = (T *)smem_raw + warp * (a.smem_in + a.smem_out) * SP;
+  T *Os = Xs + a.smem_in * SP;
   const int inlen = trans ? lf.m : lf.n, outlen = trans ? lf.n : lf.m;
-  panel_stage<T, P>(Xs, pj, inlen, src, lane, 32);
+  panel_stage<T, P, SP>(Xs, pj, inlen, src, lane, 32);
   __syncwarp();
-  if (!trans) warp_nn<T, P, false>(Os, D, lf.m, Xs, lf.m, lf.n);   // Os = D X
-  else warp_tn<T, P, false>(Os, D, lf.m, Xs, lf.m, lf.n);          // Os = D^T X
+  if (!trans) warp_nn<T, P, false, SP>(Os, D, lf.m, Xs, lf.m, lf.n);   // Os = D X
+  else warp_tn<T, P, false, SP>(Os, D, lf.m, Xs, lf.m, lf.n);          // Os = D^T X
   __syncwarp();
   T *out = (T *)a.terms;
   for (int c = 0; c < pj.ncol; c++) {
     const int64_t dst = pj.dst + (int64_t)c * pj.dst_ld;
-    for (int i = lane; i < outlen; i += 32) out[dst + i] = Os[i * P + c];
+    for (int i = lane; i < outlen; i += 32) out[dst + i] = Os[i * SP + c];
   }
 }
 
@@ -398,31 +451,32 @@ __global__ void __launch_bounds__(AT) k_panel(PanelArgs a) {
   const BlockDev bk = a.blocks[pj.blk];
   const bool trans = pj.trans;
   const int inlen = trans ? bk.m : bk.n, outlen = trans ? bk.n : bk.m;
+  constexpr int SP = panel_row_stride(P);
   T *Xs, *Os, *cwall;
   if (GSTAGE) {
     Xs = (T *)a.stage_base + (int64_t)blockIdx.x * a.stage_stride;
-    Os = Xs + (int64_t)inlen * P;
+    Os = Xs + (int64_t)inlen * SP;
     cwall = (T *)smem_raw;
   } else {
     Xs = (T *)smem_raw;
-    Os = Xs + a.smem_in * P;
-    cwall = Os + a.smem_out * P;
+    Os = Xs + a.smem_in * SP;
+    cwall = Os + a.smem_out * SP;
   }
   const int warp = threadIdx.x >> 5;
-  T *cw = cwall + warp * a.smem_cw * P;
+  T *cw = cwall + warp * a.smem_cw * SP;
   const T *src = (const T *)(trans ? a.dataA : a.dataB);
-  panel_stage<T, P>(Xs, pj, inlen, src, threadIdx.x, AT);
-  for (int o = threadIdx.x; o < outlen * P; o += AT) Os[o] = T(0);
+  panel_stage<T, P, SP>(Xs, pj, inlen, src, threadIdx.x, AT);
+  for (int o = threadIdx.x; o < outlen * SP; o += AT) Os[o] = T(0);
   __syncthreads();
   const LeafDev *leaves = trans ? a.leafB : a.leafA;
   const T *data = (const T *)(trans ? a.dataB : a.dataA);
   for (int l = bk.leaf_lo + warp; l < bk.leaf_hi; l += NWARP)
-    warp_leaf<T, P>(leaves[l], data, trans, bk.row, bk.col, Xs, Os, cw);
+    warp_leaf<T, P, SP>(leaves[l], data, trans, bk.row, bk.col, Xs, Os, cw);
   __syncthreads();
   T *out = (T *)a.terms;
   for (int o = threadIdx.x; o < outlen * pj.ncol; o += AT) {
     const int c = o / outlen, i = o - c * outlen;
-    out[pj.dst + (int64_t)c * pj.dst_ld + i] = Os[i * P + c];
+    out[pj.dst + (int64_t)c * pj.dst_ld + i] = Os[i * SP + c];
   }
 }
 

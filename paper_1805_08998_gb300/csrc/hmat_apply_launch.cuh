@@ -31,8 +31,9 @@ static cudaError_t launch_rb(const ApplyArgs &a, size_t smem, cudaStream_t s) {
 }
 
 inline size_t smem_bytes(size_t es, int P, const ApplyArgs &a) {
-  const size_t cw = (size_t)NWARP * a.smem_cw * P * es;
-  return a.gstage ? cw : (size_t)(a.smem_in + a.smem_out + a.smem_rho) * P * es + cw;
+  const size_t SP = apply_row_stride(P);
+  const size_t cw = (size_t)NWARP * a.smem_cw * SP * es;
+  return a.gstage ? cw : (size_t)(a.smem_in + a.smem_out + a.smem_rho) * SP * es + cw;
 }
 
 template <typename T>
@@ -45,17 +46,18 @@ static cudaError_t launch_apply_t(int P, bool trans, const ApplyArgs &a, cudaStr
 template <typename T>
 static cudaError_t launch_panels_t(const PanelArgs &a, bool leaf_kind, cudaStream_t s) {
   constexpr int P = PANEL_P;
+  constexpr size_t SP = panel_row_stride(P);
   const size_t es = sizeof(T);
   cudaError_t e;
   if (leaf_kind) {
-    const size_t smem = (size_t)NWARP * (a.smem_in + a.smem_out) * P * es;
+    const size_t smem = (size_t)NWARP * (a.smem_in + a.smem_out) * SP * es;
     if ((e = cudaFuncSetAttribute(k_panel_leaf<T, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
       return e;
     k_panel_leaf<T, P><<<(a.count + NWARP - 1) / NWARP, AT, smem, s>>>(a);
     return cudaGetLastError();
   }
-  const size_t cw = (size_t)NWARP * a.smem_cw * P * es;
-  const size_t smem = a.gstage ? cw : (size_t)(a.smem_in + a.smem_out) * P * es + cw;
+  const size_t cw = (size_t)NWARP * a.smem_cw * SP * es;
+  const size_t smem = a.gstage ? cw : (size_t)(a.smem_in + a.smem_out) * SP * es + cw;
   if (a.gstage) {
     if ((e = cudaFuncSetAttribute(k_panel<T, P, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
       return e;

@@ -16,6 +16,13 @@
 
 namespace hm {
 
+// Row strides (elements) of the P-column panels kept row-major in shared memory. The
+// application kernel keeps P (rows stay 16-byte aligned for vector loads; its small targets
+// accumulate in registers); the low-rank product panels use P + 1, so that the lanes of a warp,
+// each owning one row of an atomically updated output, fall into distinct banks.
+__host__ __device__ constexpr int apply_row_stride(int P) { return P; }
+__host__ __device__ constexpr int panel_row_stride(int P) { return P + 1; }
+
 // learned rank proposal: 12 features -> 64 -> 64 -> 1
 constexpr int RANK_FEATURES = 12;
 constexpr int RANK_PARAMS = 64 * 12 + 64 + 64 * 64 + 64 + 64 + 1;

@@ -914,6 +914,7 @@ void Product::run() {
   int pdim[NB + 2] = {0};
   int64_t term_elems = 0;
   double flops_terms = 0;
+  double kind_flops[NB + 2] = {0}, kind_cols[NB + 2] = {0};
   {
     // two passes over chunks of the terms on a thread pool, with the serial order preserved:
     // (1) per chunk: storage, flops, far x far count, panels per kind; (2) fill at the offsets
@@ -922,6 +923,7 @@ void Product::run() {
       double flops = 0;
       int64_t npk[NB + 2] = {0};
       int pd[NB + 2] = {0};
+      double fk[NB + 2] = {0}, ck[NB + 2] = {0};  // per kind: flops, columns (for the trace)
     };
     const size_t nch = std::max<size_t>(1, std::min<size_t>(64, nterm / 4096 + 1));
     std::vector<Chunk> ch(nch);
@@ -960,6 +962,8 @@ void Product::run() {
           const int kind = kind_of(pt, dmx);
           k.npk[kind] += (pt.rank + PW - 1) / PW;
           k.pd[kind] = std::max(k.pd[kind], dmx);
+          k.fk[kind] += 2.0 * (pt.type == JOB_HF ? storA[hb] : storB[hb]) * pt.rank;
+          k.ck[kind] += pt.rank;
         }
       }
     });
@@ -973,6 +977,8 @@ void Product::run() {
       for (int k = 0; k < NB + 2; k++) {
         poff[c + 1][k] = poff[c][k] + ch[c].npk[k];
         pdim[k] = std::max(pdim[k], ch[c].pd[k]);
+        kind_flops[k] += ch[c].fk[k];
+        kind_cols[k] += ch[c].ck[k];
       }
     }
     term_elems = eoff[nch];
@@ -1030,8 +1036,20 @@ void Product::run() {
     ~EvGuard() { for (int i = 0; i < 6; i++) cudaEventDestroy(e[i]); }
   } evg{ev};
 
-  // ---- a2: low-rank products. Far x far products (small) run one job per block; products with
-  // an inadmissible factor run as panels of up to panel_width() columns.
+  // Far x far products with both ranks <= 32 and at most 2048 inner rows run one warp per job
+  // (listed first), the others one block per job.
+  int n_ff_warp = 0;
+  {
+    std::vector<int32_t> big;
+    for (int32_t i : ff_ids) {
+      const LeafDev &la = A->leaves[jobs[i].a], &lb = B->leaves[jobs[i].b];
+      if (la.rank <= 32 && lb.rank <= 32 && la.n <= 2048) ff_ids[n_ff_warp++] = i;
+      else big.push_back(i);
+    }
+    std::copy(big.begin(), big.end(), ff_ids.begin() + n_ff_warp);
+  }
+  // ---- a2: low-rank products. Far x far products (small) run one job per warp or block;
+  // products with an inadmissible factor run as panels of up to panel_width() columns.
   ck(cudaEventRecord(ev[0], s), "event");
   DevBuf d_termbuf(es * std::max<int64_t>(term_elems, 1), s);
   DevBuf d_jobs = upload(jobs, s), d_ffids = upload(ff_ids, s), d_panels = upload(panels, s);
@@ -1040,10 +1058,25 @@ void Product::run() {
   ck(launch_make_terms(cprec, d_jobs.as<TermJob>(), (int)nterm, t.d_blocks, A->d_leaves.as<LeafDev>(),
                        B->d_leaves.as<LeafDev>(), dataA, dataB, d_termbuf.p, d_terms.as<TermDev>(), s),
      "term table");
-  ck(launch_term_jobs(cprec, d_jobs.as<TermJob>(), d_ffids.as<int32_t>(), (int)ff_ids.size(),
+  std::vector<std::pair<int, std::array<cudaEvent_t, 2>>> a2ev;  // HMAT_TRACE only: -1 = far x far
+  auto a2mark = [&](int kind, int which) {
+    if (!tr.on) return;
+    if (which == 0) {
+      a2ev.push_back({kind, {nullptr, nullptr}});
+      cudaEventCreate(&a2ev.back().second[0]);
+      cudaEventCreate(&a2ev.back().second[1]);
+    }
+    cudaEventRecord(a2ev.back().second[which], s);
+  };
+  a2mark(-1, 0);
+  ck(launch_ff_warp(cprec, d_jobs.as<TermJob>(), d_ffids.as<int32_t>(), n_ff_warp, A->d_leaves.as<LeafDev>(),
+                    B->d_leaves.as<LeafDev>(), dataA, dataB, d_termbuf.p, s),
+     "far x far products (warp)");
+  ck(launch_term_jobs(cprec, d_jobs.as<TermJob>(), d_ffids.as<int32_t>() + n_ff_warp, (int)ff_ids.size() - n_ff_warp,
                       A->d_leaves.as<LeafDev>(), B->d_leaves.as<LeafDev>(), t.d_blocks, dataA, dataB, d_termbuf.p, s),
      "far x far products");
-  int64_t launches = 1 + (ff_ids.empty() ? 0 : 1);
+  a2mark(-1, 1);
+  int64_t launches = 1 + (n_ff_warp > 0 ? 1 : 0) + ((int)ff_ids.size() > n_ff_warp ? 1 : 0);
   const int64_t pstride = (int64_t)2 * pdim[NB + 1] * panel_row_stride(PW);
   DevBuf d_pstage(es * std::max<int64_t>(pstride * (int64_t)pk[NB + 1].size(), 1), s);
   for (int k = 0; k < NB + 2; k++) {
@@ -1064,13 +1097,31 @@ void Product::run() {
     pa.dataA = dataA;
     pa.dataB = dataB;
     pa.terms = d_termbuf.p;
+    a2mark(k, 0);
     ck(launch_panels(cprec, pa, k == 0, s), "low-rank products (panels)");
+    a2mark(k, 1);
     launches++;
   }
   S.n_ff_jobs = (int64_t)ff_ids.size();
   S.n_panels = (int64_t)panels.size();
   check_finite(cprec, d_termbuf.p, term_elems, "low-rank products", s);
   tr.mark("a2 launched");
+  if (tr.on) {
+    cudaStreamSynchronize(s);
+    for (auto &e : a2ev) {
+      float x = 0.f;
+      cudaEventElapsedTime(&x, e.second[0], e.second[1]);
+      if (e.first < 0)
+        std::fprintf(stderr, "hmat trace: a2 far x far: %zu jobs, %8.3f ms\n", ff_ids.size(), x);
+      else
+        std::fprintf(stderr, "hmat trace: a2 panel kind %2d: %8zu panels (columns used %4.1f%%), H-block dim <= %6d, "
+                     "%.3g flops, %8.3f ms\n", e.first, pk[e.first].size(),
+                     100.0 * kind_cols[e.first] / std::max<double>(1.0, (double)pk[e.first].size() * PW), pdim[e.first],
+                     kind_flops[e.first], x);
+      cudaEventDestroy(e.second[0]);
+      cudaEventDestroy(e.second[1]);
+    }
+  }
   ck(cudaEventRecord(ev[1], s), "event");
 
   // host work below overlaps the low-rank products on the GPU
@@ -1221,7 +1272,8 @@ void Product::run() {
   // scratch offsets for far targets and the per-class launch parameters
   int64_t qw_elems = 0, xy_elems = 0, stage_elems = 0;
   struct ClassLaunch {
-    int first = 0, count = 0, dmax = 0, rho = 0;
+    int first = 0, count = 0, dmax = 0, rho = 0, split = 1;
+    int64_t inner_pairs = 0, y_lo = 0, y_hi = 0;
   } cls[NCLS];
   for (int c = 0; c < NCLS; c++) cls[c].first = -1;
   for (size_t i = 0; i < ftg.size(); i++) {
@@ -1243,10 +1295,26 @@ void Product::run() {
     cl.count++;
     cl.dmax = std::max(cl.dmax, (int)mx);
     cl.rho = std::max(cl.rho, rho_inner[d.leaf]);
+    cl.inner_pairs += d.pair_hi - d.pair_mid;
+    if (cl.count == 1) cl.y_lo = d.y_off;
+    cl.y_hi = d.y_off + mx * pmax;
     if (c == 0) {
       d.stage_off = stage_elems;
       stage_elems += ((int64_t)d.m + d.n + rho_inner[d.leaf]) * apply_row_stride(P);
     }
+  }
+
+  // Big targets (shared-atomic launches, panels in shared memory) have few thread blocks each
+  // with a long serial chain of H-pairs: their H-pairs and terms are split over K blocks per
+  // target (about two H-pairs of inner blocks per block, at most 8), which add their partial
+  // outputs into a zeroed output.
+  const char *split_env = std::getenv("HMAT_APPLY_SPLIT");
+  for (int c = 1; c < NCLS; c++) {
+    ClassLaunch &cl = cls[c];
+    if (cl.count == 0 || apply_rows_per_lane(cl.dmax) > 0) continue;
+    const double ppt = (double)cl.inner_pairs / cl.count;
+    cl.split = std::max(1, std::min(8, (int)std::ceil(ppt / 2.0)));
+    if (split_env) cl.split = std::max(1, std::min(16, std::atoi(split_env)));
   }
 
   // ---- a8 on a second stream, concurrent with the far-field rounds: C's buffer starts with the
@@ -1302,6 +1370,10 @@ void Product::run() {
     x.active = 1;
   }
   DevBuf d_st = upload(st0, s);
+  // a4 runs one warp per target of at most 64 rows, one block per larger target
+  std::vector<int32_t> orth_w, orth_b;
+  for (int i = 0; i < nf; i++) (ftg[i].m <= 64 ? orth_w : orth_b).push_back(i);
+  DevBuf d_orth_w = upload(orth_w, s), d_orth_b = upload(orth_b, s);
   DevBuf d_cnt(sizeof(int32_t), s);
   ApplyArgs aa{};
   aa.tg = d_ftg.as<TargetDev>();
@@ -1333,6 +1405,16 @@ void Product::run() {
     cudaEvent_t e0, e1;
   };
   std::vector<ClassTiming> ctim;  // per-class launch events (HMAT_TRACE only)
+  std::vector<std::pair<int, std::array<cudaEvent_t, 2>>> kev;  // gaussian / orth / stop test
+  auto kmark = [&](int which_kernel, int edge) {
+    if (!tr.on) return;
+    if (edge == 0) {
+      kev.push_back({which_kernel, {nullptr, nullptr}});
+      cudaEventCreate(&kev.back().second[0]);
+      cudaEventCreate(&kev.back().second[1]);
+    }
+    cudaEventRecord(kev.back().second[edge], s);
+  };
   auto timed_apply = [&](bool trans) {
     cudaEvent_t e0, e1;
     ck(cudaEventCreate(&e0), "event");
@@ -1351,6 +1433,9 @@ void Product::run() {
       if (c > 0 && apply_rows_per_lane(cls[c].dmax) > 0) ac.smem_rho = std::max(ac.smem_rho, 8 * cls[c].dmax);
       ac.smem_cw = cw_rows;
       ac.gstage = c == 0 ? 1 : 0;
+      ac.split = cls[c].split;
+      if (ac.split > 1)
+        ck(cudaMemsetAsync((char *)d_y.p + es * cls[c].y_lo, 0, es * (cls[c].y_hi - cls[c].y_lo), s), "memset");
       ClassTiming ct{c, trans, nullptr, nullptr};
       if (tr.on) {
         cudaEventCreate(&ct.e0);
@@ -1371,18 +1456,26 @@ void Product::run() {
     const int pr = round == 0 ? pmax : p;  // widest panel this round (round 0: each target's p0)
     aa.p = pr;
     aa.round = round;
+    kmark(0, 0);
     ck(launch_gaussian(cprec, aa.tg, aa.state, nf, pr, o->seed, round, d_x.p, s), "gaussian");
+    kmark(0, 1);
     timed_apply(false);
     check_finite(cprec, d_y.p, xy_elems, "apply S", s);
-    ck(launch_orth(cprec, aa.tg, aa.state, nf, pr, eps, d_y.p, d_qw.as<double>(), d_x.p, round, s), "orth");
+    kmark(1, 0);
+    ck(launch_orth(cprec, aa.tg, d_orth_w.as<int32_t>(), (int)orth_w.size(), d_orth_b.as<int32_t>(),
+                   (int)orth_b.size(), aa.state, pr, eps, d_y.p, d_qw.as<double>(), d_x.p, round, s),
+       "orth");
+    kmark(1, 1);
     check_finite(64, d_qw.p, qw_elems, "orthogonalisation", s);
     timed_apply(true);
     check_finite(cprec, d_y.p, xy_elems, "apply S^T", s);
-    launches += 3;
+    launches += 2 + (orth_w.empty() ? 0 : 1) + (orth_b.empty() ? 0 : 1);
+    kmark(2, 0);
     ck(cudaMemsetAsync(d_cnt.p, 0, sizeof(int32_t), s), "memset");
     ck(launch_absorb_w(cprec, aa.tg, aa.state, nf, p, eps_stop, d_y.p, d_qw.as<double>(), round, max_rounds,
                        d_cnt.as<int32_t>(), s),
        "stop test");
+    kmark(2, 1);
     int32_t act = 0;
     ck(cudaMemcpyAsync(&act, d_cnt.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s), "count");
     ck(cudaStreamSynchronize(s), "round");
@@ -1399,10 +1492,20 @@ void Product::run() {
       cudaEventDestroy(ct.e0);
       cudaEventDestroy(ct.e1);
     }
+    double tk[3] = {};
+    for (auto &e : kev) {
+      float x = 0.f;
+      cudaEventElapsedTime(&x, e.second[0], e.second[1]);
+      tk[e.first] += x;
+      cudaEventDestroy(e.second[0]);
+      cudaEventDestroy(e.second[1]);
+    }
+    std::fprintf(stderr, "hmat trace: rounds: gaussian %.3f ms, orthogonalisation %.3f ms, stop test %.3f ms\n", tk[0],
+                 tk[1], tk[2]);
     for (int c = 0; c < NCLS; c++)
       if (cls[c].count)
-        std::fprintf(stderr, "hmat trace: class %2d apply: S %8.3f ms, S^T %8.3f ms (all rounds)\n", c, tc[c][0],
-                     tc[c][1]);
+        std::fprintf(stderr, "hmat trace: class %2d apply: S %8.3f ms, S^T %8.3f ms (all rounds), %d blocks/target\n",
+                     c, tc[c][0], tc[c][1], cls[c].split);
   }
   ck(cudaEventRecord(ev[2], s), "event");
   std::vector<TargetState> st(nf);
@@ -1417,11 +1520,30 @@ void Product::run() {
     std::vector<int32_t> ids_small, ids_big;
     for (int i = 0; i < nf; i++) (st[i].r <= 32 ? ids_small : ids_big).push_back(i);
     DevBuf d_ids_small = upload(ids_small, s), d_ids_big = upload(ids_big, s);
+    cudaEvent_t fe[3] = {nullptr, nullptr, nullptr};
+    if (tr.on)
+      for (auto &e : fe) {
+        cudaEventCreate(&e);
+      }
+    if (tr.on) cudaEventRecord(fe[0], s);
     ck(launch_final(aa.tg, aa.state, d_ids_small.as<int32_t>(), (int)ids_small.size(), true, eps, d_qw.as<double>(),
                     s),
        "final truncation (warp)");
+    if (tr.on) cudaEventRecord(fe[1], s);
     ck(launch_final(aa.tg, aa.state, d_ids_big.as<int32_t>(), (int)ids_big.size(), false, eps, d_qw.as<double>(), s),
        "final truncation (block)");
+    if (tr.on) {
+      cudaEventRecord(fe[2], s);
+      cudaStreamSynchronize(s);
+      float x0 = 0.f, x1 = 0.f;
+      cudaEventElapsedTime(&x0, fe[0], fe[1]);
+      cudaEventElapsedTime(&x1, fe[1], fe[2]);
+      int64_t rsum = 0;
+      for (int i = 0; i < nf; i++) rsum += st[i].r;
+      std::fprintf(stderr, "hmat trace: final: %zu blocks (r <= 32) %.3f ms, %zu blocks %.3f ms, mean r %.1f\n",
+                   ids_small.size(), x0, ids_big.size(), x1, nf ? (double)rsum / nf : 0.0);
+      for (auto &e : fe) cudaEventDestroy(e);
+    }
     launches += (ids_small.empty() ? 0 : 1) + (ids_big.empty() ? 0 : 1);
     if (nf) ck(cudaMemcpyAsync(st.data(), d_st.p, sizeof(TargetState) * nf, cudaMemcpyDeviceToHost, s), "states");
     ck(cudaStreamSynchronize(s), "final");

@@ -238,7 +238,10 @@ __device__ __forceinline__ void warp_nn_reg(T (&acc)[RB][P], const T *__restrict
 template <typename T, int P, bool TRANS, bool GSTAGE, int RB>
 __global__ void __launch_bounds__(AT) k_apply(ApplyArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int b = a.first + blockIdx.x;
+  // K thread blocks per target (K > 1 only when RB == 0 and !GSTAGE); block `part` takes every
+  // K-th H-pair of inner blocks and, with its warps, every (K NWARP)-th term and leaf pair
+  const int K = a.split > 1 ? a.split : 1;
+  const int b = a.first + (int)(blockIdx.x / K), part = (int)(blockIdx.x % K);
   if (a.state[b].active == 0) return;  // uniform over the block
   const TargetDev t = a.tg[b];
   const int inlen = TRANS ? t.m : t.n, outlen = TRANS ? t.n : t.m;
@@ -257,8 +260,9 @@ __global__ void __launch_bounds__(AT) k_apply(ApplyArgs a) {
     cwall = Zs + a.smem_rho * SP;
   }
   const int warp = threadIdx.x >> 5;
+  const int vw = part * NWARP + warp, NV = K * NWARP;  // virtual warp over the target's blocks
   T *cw = cwall + warp * a.smem_cw * SP;
-  const T *X = (const T *)a.x_base + t.x_off;  // column-major inlen x p
+  const T *X = (const T *)a.x_base + t.x_off;  // Omega or Q_new, column-major inlen x p
   T *Out = (T *)a.y_base + t.y_off;            // column-major outlen x p
   const int p = a.round == 0 ? t.p0 : a.p;     // this target's columns this round (<= P)
   for (int o = threadIdx.x; o < inlen * P; o += AT) {
@@ -281,9 +285,9 @@ __global__ void __launch_bounds__(AT) k_apply(ApplyArgs a) {
   for (int blk = t.blk; blk >= 0; blk = a.blocks[blk].parent) {
     const int2 rg = a.blk_terms[blk];
     const int cnt = rg.y - rg.x;
-    const int j0 = ((warp - base) % NWARP + NWARP) % NWARP;
+    const int j0 = ((vw - base) % NV + NV) % NV;
     base += cnt;
-    for (int j = j0; j < cnt; j += NWARP) {
+    for (int j = j0; j < cnt; j += NV) {
       const TermDev tm = a.terms[rg.x + j];
       const T *L = (const T *)tm.L + (t.row - tm.row0);
       const T *R = (const T *)tm.R + (t.col - tm.col0);
@@ -299,7 +303,7 @@ __global__ void __launch_bounds__(AT) k_apply(ApplyArgs a) {
   }
 
   // H-pairs of two dense leaves, warp per pair; the intermediate lives in the warp's scratch
-  for (int pi = t.pair_lo + warp; pi < t.pair_mid; pi += NWARP) {
+  for (int pi = t.pair_lo + vw; pi < t.pair_mid; pi += NV) {
     const PairDev pr = a.pairs[pi];
     const LeafDev la = a.leafA[a.blocks[pr.blkA].leaf_lo], lb = a.leafB[a.blocks[pr.blkB].leaf_lo];
     const T *DA = (const T *)a.dataA + la.off_u;  // m x rho, ld m
@@ -338,7 +342,7 @@ __global__ void __launch_bounds__(AT) k_apply(ApplyArgs a) {
   }
 
   // H-pairs of inner blocks: walk the two subtrees (Algorithm 2), leaves split over warps
-  for (int pi = t.pair_mid; pi < t.pair_hi; pi++) {
+  for (int pi = t.pair_mid + part; pi < t.pair_hi; pi += K) {
     const PairDev pr = a.pairs[pi];
     const BlockDev ba = a.blocks[pr.blkA], bb = a.blocks[pr.blkB];
     const int rho = ba.n;
@@ -362,7 +366,8 @@ __global__ void __launch_bounds__(AT) k_apply(ApplyArgs a) {
   __syncthreads();
   for (int o = threadIdx.x; o < outlen * p; o += AT) {
     const int c = o / outlen, i = o - c * outlen;
-    Out[o] = Ys[i * SP + c];
+    if (K > 1) atomicAdd(Out + o, Ys[i * SP + c]);
+    else Out[o] = Ys[i * SP + c];
   }
 }
 

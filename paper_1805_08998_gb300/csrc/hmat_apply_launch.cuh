@@ -13,7 +13,10 @@ static cudaError_t launch_one(const ApplyArgs &a, size_t smem, cudaStream_t s) {
   cudaError_t e = cudaFuncSetAttribute(k_apply<T, P, TRANS, GSTAGE, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
-  k_apply<T, P, TRANS, GSTAGE, RB><<<a.count, AT, smem, s>>>(a);
+  const int K = (RB == 0 && !GSTAGE && a.split > 1) ? a.split : 1;
+  ApplyArgs b = a;
+  b.split = K;
+  k_apply<T, P, TRANS, GSTAGE, RB><<<(unsigned)a.count * K, AT, smem, s>>>(b);
   return cudaGetLastError();
 }
 

@@ -137,6 +137,9 @@ struct ApplyArgs {
   void *y_base;          // per-target In/Out regions (element type T), offsets in TargetDev
   void *x_base;
   int p;                 // columns this round (the first round: each target's p0 instead)
+  int split;             // thread blocks per target (> 1 only for shared-atomic launches without
+                         // global staging): each takes a share of the target's terms and
+                         // H-pairs and adds its partial output to Out, which starts at zero
   int round;
 };
 
@@ -151,6 +154,9 @@ cudaError_t launch_aca(int kernel, const double *pts, int dim, const LeafDev *le
 cudaError_t launch_aca_compact(int prec, const LeafDev *leaves, const int32_t *far_ids, int nfar,
                                const double *scratch, const int64_t *scratch_off, int kmax,
                                void *data, cudaStream_t s);
+// far x far products ids[0..n) with both ranks <= 32, one warp per job (the others: launch_term_jobs)
+cudaError_t launch_ff_warp(int prec, const TermJob *jobs, const int32_t *ids, int n, const LeafDev *leafA,
+                           const LeafDev *leafB, const void *dataA, const void *dataB, void *terms, cudaStream_t s);
 cudaError_t launch_term_jobs(int prec, const TermJob *jobs, const int32_t *ids, int njobs, const LeafDev *leafA,
                              const LeafDev *leafB, const BlockDev *blocks, const void *dataA,
                              const void *dataB, void *terms, cudaStream_t s);
@@ -161,16 +167,19 @@ cudaError_t launch_near_eval(int prec, const TargetDev *tg, int ntg, const int2 
                              const TermDev *terms, const PairDev *pairs, const BlockDev *blocks,
                              const LeafDev *leafA, const LeafDev *leafB, const void *dataA,
                              const void *dataB, const LeafDev *leafC, void *dataC, cudaStream_t s);
-cudaError_t launch_gaussian(int prec, const TargetDev *tg, const TargetState *st, int ntg, int p,
-                            uint64_t seed, int round, void *x_base, cudaStream_t s);
 cudaError_t launch_apply(int prec, bool trans, const ApplyArgs &a, cudaStream_t s);
 size_t apply_smem_bytes(int prec, int P, const ApplyArgs &a);
 int apply_rows_per_lane(int dmax);
 cudaError_t launch_panels(int prec, const PanelArgs &a, bool leaf_kind, cudaStream_t s);
 int panel_width();
 int apply_panel_width(int p);
-cudaError_t launch_orth(int prec, const TargetDev *tg, TargetState *st, int ntg, int p, double eps,
-                        void *y_base, double *qw, void *x_base, int round, cudaStream_t s);
+// Gaussian test matrices Omega (n x p per active target, into x_base; round 0: p0 columns)
+cudaError_t launch_gaussian(int prec, const TargetDev *tg, const TargetState *st, int ntg, int p, uint64_t seed,
+                            int round, void *x_base, cudaStream_t s);
+// a4 for targets ids_warp (at most 64 rows: one warp each) and ids_block (one block each)
+cudaError_t launch_orth(int prec, const TargetDev *tg, const int32_t *ids_warp, int n_warp, const int32_t *ids_block,
+                        int n_block, TargetState *st, int p, double eps, void *y_base, double *qw, void *x_base,
+                        int round, cudaStream_t s);
 cudaError_t launch_absorb_w(int prec, const TargetDev *tg, TargetState *st, int ntg, int p,
                             double eps_stop, void *y_base, double *qw, int round, int max_rounds,
                             int32_t *active_count, cudaStream_t s);

@@ -224,6 +224,12 @@ __global__ void __launch_bounds__(NT) k_kernel_dense(int kernel, const double *p
   }
 }
 
+// warp-wide sum, the result in every lane
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  return v;
+}
+
 // block-wide reductions (NT threads)
 __device__ double block_sum(double v, double *red) {
   for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
@@ -523,25 +529,29 @@ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
   return z ^ (z >> 31);
 }
 
-// Omega(i, c) for target leaf L in round rd: two splitmix64 draws of the counter
-// ((L * 64 + rd) * 64 + c) * 2^24 + i, then Box-Muller.
+// Entry (i, c) of the Gaussian test matrix Omega of target leaf L in round rd (Alg. 8 draws
+// standard normal samples): two splitmix64 outputs of the counter ((L * 64 + rd) * 64 + c) * 2^24
+// + i, their top 24 bits as uniforms u1 in (0, 1] and u2 in [0, 1), then Box-Muller in FP32.
+__device__ __forceinline__ float omega(uint64_t seed, int leaf, int rd, int c, int i) {
+  const uint64_t ctr = ((((uint64_t)leaf * 64u + (uint64_t)rd) * 64u + (uint64_t)c) << 24) + (uint64_t)i;
+  const uint64_t z1 = mix64(seed + (2 * ctr + 1) * 0x9E3779B97F4A7C15ull);
+  const uint64_t z2 = mix64(seed + (2 * ctr + 2) * 0x9E3779B97F4A7C15ull);
+  const float u1 = (float)((z1 >> 40) + 1) * 0x1.0p-24f;
+  const float u2 = (float)(z2 >> 40) * 0x1.0p-24f;
+  return sqrtf(-2.f * logf(u1)) * cospif(2.f * u2);
+}
+
+// Omega of every active target, n x p column-major at x_off (round 0: p0 columns)
 template <typename T>
 __global__ void __launch_bounds__(NT) k_gaussian(const TargetDev *tg, const TargetState *st, int p, uint64_t seed,
                                                  int round, T *x_base) {
   const int b = blockIdx.x;
   if (st[b].active == 0) return;
   const TargetDev t = tg[b];
-  T *X = x_base + t.x_off;
   if (round == 0) p = t.p0;
-  for (int64_t o = threadIdx.x; o < (int64_t)t.n * p; o += NT) {
-    const int64_t i = o % t.n, c = o / t.n;
-    const uint64_t ctr = ((((uint64_t)t.leaf * 64u + (uint64_t)round) * 64u + (uint64_t)c) << 24) + (uint64_t)i;
-    const uint64_t z1 = mix64(seed + (2 * ctr + 1) * 0x9E3779B97F4A7C15ull);
-    const uint64_t z2 = mix64(seed + (2 * ctr + 2) * 0x9E3779B97F4A7C15ull);
-    const double u1 = ((z1 >> 11) + 1) * 0x1.0p-53;  // (0, 1]
-    const double u2 = (z2 >> 11) * 0x1.0p-53;
-    X[o] = T(sqrt(-2.0 * log(u1)) * cospi(2.0 * u2));
-  }
+  T *X = x_base + t.x_off;
+  for (int c = 0; c < p; c++)
+    for (int i = threadIdx.x; i < t.n; i += NT) X[i + (int64_t)c * t.n] = T(omega(seed, t.leaf, round, c, i));
 }
 
 // ---------------------------------------------------------------------------------------
@@ -551,13 +561,13 @@ __global__ void __launch_bounds__(NT) k_gaussian(const TargetDev *tg, const Targ
 // Q buffer of target b: qw + q_off, m x rmax FP64; the new columns are built in place at
 // columns r .. r+p-1. Also writes Q_new in T precision into x_base (input of the S^T pass).
 template <typename T>
-__global__ void __launch_bounds__(NT) k_orth(const TargetDev *tg, TargetState *st, int p, double eps,
-                                             const T *y_base, double *qw, T *x_base, int round) {
+__global__ void __launch_bounds__(NT) k_orth(const TargetDev *tg, const int32_t *ids, TargetState *st, int p,
+                                             double eps, const T *y_base, double *qw, T *x_base, int round) {
   __shared__ double G[PMAX];
   constexpr int QCH = 64;  // basis columns projected per chunk
   __shared__ double Cm[QCH * PMAX];
   __shared__ double red[NT / 32];
-  const int b = blockIdx.x;
+  const int b = ids[blockIdx.x];
   if (st[b].active == 0) return;
   const TargetDev t = tg[b];
   const int64_t m = t.m;
@@ -646,6 +656,104 @@ __global__ void __launch_bounds__(NT) k_orth(const TargetDev *tg, TargetState *s
     Xo[o] = c < kept ? T(Y[o]) : T(0);
   }
   if (threadIdx.x == 0) {
+    st[b].p_new = kept;
+    st[b].nfwd += 1;
+    if (kept == 0) st[b].active = 0;
+  }
+}
+
+// The same step for targets of at most 64 rows, one warp per target: each lane holds rows lane
+// and lane + 32 of the p new columns in registers. The projection against the basis runs column
+// by column (modified Gram-Schmidt), twice; the new columns are orthonormalised by Gram-Schmidt
+// twice with the same dropping rule; kept columns are compacted when written.
+constexpr int OW = 16;  // max columns per round
+template <typename T>
+__global__ void __launch_bounds__(NT) k_orth_warp(const TargetDev *tg, const int32_t *ids, int nids,
+                                                  TargetState *st, int p_round, double eps, const T *y_base,
+                                                  double *qw, T *x_base, int round) {
+  const int wi = blockIdx.x * (NT / 32) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (wi >= nids) return;  // whole warps only
+  const int b = ids[wi];
+  if (st[b].active == 0) return;
+  const TargetDev t = tg[b];
+  const int m = t.m, r = st[b].r;
+  const int p = round == 0 ? t.p0 : p_round;
+  double *Q = qw + t.q_off;
+  const T *Ys = y_base + t.y_off;
+  const int i0 = lane, i1 = lane + 32;
+  const bool v0 = i0 < m, v1 = i1 < m;
+  double y[OW][2];
+  double part = 0.0;
+#pragma unroll
+  for (int c = 0; c < OW; c++) {
+    y[c][0] = (c < p && v0) ? (double)Ys[i0 + (int64_t)c * m] : 0.0;
+    y[c][1] = (c < p && v1) ? (double)Ys[i1 + (int64_t)c * m] : 0.0;
+    part += y[c][0] * y[c][0] + y[c][1] * y[c][1];
+  }
+  const double ny2 = warp_sum(part);
+  double est2;
+  if (round == 0) {
+    est2 = ny2 / p;
+    if (lane == 0) st[b].est2 = est2;
+  } else {
+    est2 = st[b].est2;
+  }
+  // project against the basis, twice
+  for (int pass = 0; pass < 2; pass++)
+    for (int q = 0; q < r; q++) {
+      const double *qc = Q + (int64_t)q * m;
+      const double q0 = v0 ? qc[i0] : 0.0, q1 = v1 ? qc[i1] : 0.0;
+#pragma unroll
+      for (int c = 0; c < OW; c++) {
+        if (c >= p) break;
+        const double d = warp_sum(q0 * y[c][0] + q1 * y[c][1]);
+        y[c][0] -= d * q0;
+        y[c][1] -= d * q1;
+      }
+    }
+  // Gram-Schmidt twice among the new columns, with dropping
+  const double drop2 = (0.1 * eps) * (0.1 * eps) * est2;
+  unsigned keep = 0u;
+#pragma unroll
+  for (int j = 0; j < OW; j++) {
+    if (j >= p) break;
+    for (int pass = 0; pass < 2; pass++) {
+#pragma unroll
+      for (int l = 0; l < OW; l++) {
+        if (l >= j) break;
+        if (!((keep >> l) & 1u)) continue;
+        const double d = warp_sum(y[l][0] * y[j][0] + y[l][1] * y[j][1]);
+        y[j][0] -= d * y[l][0];
+        y[j][1] -= d * y[l][1];
+      }
+    }
+    const double nrm2 = warp_sum(y[j][0] * y[j][0] + y[j][1] * y[j][1]);
+    if (nrm2 > drop2) {
+      const double inv = 1.0 / sqrt(nrm2);
+      y[j][0] *= inv;
+      y[j][1] *= inv;
+      keep |= 1u << j;
+    }
+  }
+  // kept columns, compacted, into Q (FP64, columns r..) and Q_new (T, zero padded to p columns)
+  const int kept = __popc(keep);
+  double *Y = Q + (int64_t)r * m;
+  T *Xo = x_base + t.x_off;
+  int pos = 0;
+#pragma unroll
+  for (int j = 0; j < OW; j++) {
+    if (j >= p) break;
+    if ((keep >> j) & 1u) {
+      if (v0) { Y[i0 + (int64_t)pos * m] = y[j][0]; Xo[i0 + (int64_t)pos * m] = T(y[j][0]); }
+      if (v1) { Y[i1 + (int64_t)pos * m] = y[j][1]; Xo[i1 + (int64_t)pos * m] = T(y[j][1]); }
+      pos++;
+    }
+  }
+  for (int c = kept; c < p; c++) {
+    if (v0) { Y[i0 + (int64_t)c * m] = 0.0; Xo[i0 + (int64_t)c * m] = T(0); }
+    if (v1) { Y[i1 + (int64_t)c * m] = 0.0; Xo[i1 + (int64_t)c * m] = T(0); }
+  }
+  if (lane == 0) {
     st[b].p_new = kept;
     st[b].nfwd += 1;
     if (kept == 0) st[b].active = 0;
@@ -1070,6 +1178,116 @@ cudaError_t launch_aca_compact(int prec, const LeafDev *leaves, const int32_t *f
   return cudaGetLastError();
 }
 
+// Far x far products with both ranks <= 32, one warp per job (Algorithm 3, both factors low
+// rank): M = V_a^T U_b (ka x kb) with the rho rows staged FF_CH at a time in the warp's shared
+// memory and each lane accumulating a 4 x 8 tile of M in registers; then FF_L writes
+// L_new = U_a M (lanes over rows, a row of M broadcast per step) and FF_R writes R_new = V_b M^T.
+constexpr int FF_CH = 16;  // rows of V_a and U_b staged per step
+constexpr int FF_K = 32;   // max rank of either factor
+template <typename T>
+struct FfSmem {
+  T va[FF_CH][FF_K + 1], ub[FF_CH][FF_K + 1];
+  T M[FF_K][FF_K + 1];
+};
+
+template <typename T>
+__global__ void __launch_bounds__(NT) k_ff_warp(const TermJob *jobs, const int32_t *ids, int n, const LeafDev *leafA,
+                                                const LeafDev *leafB, const T *dataA, const T *dataB, T *terms) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ji = blockIdx.x * (NT / 32) + w;
+  if (ji >= n) return;  // whole warps only; no block barrier below
+  FfSmem<T> &S = ((FfSmem<T> *)smem_raw)[w];
+  const TermJob jb = jobs[ids[ji]];
+  const LeafDev a = leafA[jb.a], b = leafB[jb.b];
+  const int ka = a.rank, kb = b.rank, rho = a.n;
+  const T *Ua = dataA + a.off_u, *Va = dataA + a.off_v;
+  const T *Ub = dataB + b.off_u, *Vb = dataB + b.off_v;
+  // M = V_a^T U_b; lane owns rows q0..q0+3 and columns c0..c0+7 of M
+  const int q0 = (lane >> 2) * 4, c0 = (lane & 3) * 8;
+  T acc[4][8];
+#pragma unroll
+  for (int u = 0; u < 4; u++)
+#pragma unroll
+    for (int v = 0; v < 8; v++) acc[u][v] = T(0);
+  for (int i0 = 0; i0 < rho; i0 += FF_CH) {
+    const int ni = min(FF_CH, rho - i0);
+    for (int o = lane; o < FF_CH * FF_K; o += 32) {
+      const int i = o % FF_CH, q = o / FF_CH;
+      S.va[i][q] = (i < ni && q < ka) ? Va[(i0 + i) + (int64_t)q * rho] : T(0);
+      S.ub[i][q] = (i < ni && q < kb) ? Ub[(i0 + i) + (int64_t)q * rho] : T(0);
+    }
+    __syncwarp();
+    for (int i = 0; i < ni; i++) {
+      T x[4], y[8];
+#pragma unroll
+      for (int u = 0; u < 4; u++) x[u] = S.va[i][q0 + u];
+#pragma unroll
+      for (int v = 0; v < 8; v++) y[v] = S.ub[i][c0 + v];
+#pragma unroll
+      for (int u = 0; u < 4; u++)
+#pragma unroll
+        for (int v = 0; v < 8; v++) acc[u][v] += x[u] * y[v];
+    }
+    __syncwarp();
+  }
+#pragma unroll
+  for (int u = 0; u < 4; u++)
+#pragma unroll
+    for (int v = 0; v < 8; v++) S.M[q0 + u][c0 + v] = acc[u][v];
+  __syncwarp();
+  T *out = terms + jb.out;
+  const int rows = (int)jb.rows;
+  if (jb.type == JOB_FF_L) {  // out (rows x kb) = U_a M
+    for (int i = lane; i < rows; i += 32) {
+      T o[FF_K];
+#pragma unroll
+      for (int c = 0; c < FF_K; c++) o[c] = T(0);
+      for (int q = 0; q < ka; q++) {
+        const T u = Ua[i + (int64_t)q * rows];
+#pragma unroll
+        for (int c = 0; c < FF_K; c++) o[c] += u * S.M[q][c];
+      }
+#pragma unroll
+      for (int c = 0; c < FF_K; c++)
+        if (c < kb) out[i + (int64_t)c * rows] = o[c];
+    }
+  } else {  // FF_R: out (rows x ka) = V_b M^T
+    for (int i = lane; i < rows; i += 32) {
+      T o[FF_K];
+#pragma unroll
+      for (int q = 0; q < FF_K; q++) o[q] = T(0);
+      for (int c = 0; c < kb; c++) {
+        const T v = Vb[i + (int64_t)c * rows];
+#pragma unroll
+        for (int q = 0; q < FF_K; q++) o[q] += v * S.M[q][c];
+      }
+#pragma unroll
+      for (int q = 0; q < FF_K; q++)
+        if (q < ka) out[i + (int64_t)q * rows] = o[q];
+    }
+  }
+}
+
+cudaError_t launch_ff_warp(int prec, const TermJob *jobs, const int32_t *ids, int n, const LeafDev *leafA,
+                           const LeafDev *leafB, const void *dataA, const void *dataB, void *terms, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  const int grid = (n + NT / 32 - 1) / (NT / 32);
+  cudaError_t e;
+  if (prec == 64) {
+    const size_t sm = sizeof(FfSmem<double>) * (NT / 32);
+    if ((e = set_smem(k_ff_warp<double>, sm)) != cudaSuccess) return e;
+    k_ff_warp<double><<<grid, NT, sm, s>>>(jobs, ids, n, leafA, leafB, (const double *)dataA, (const double *)dataB,
+                                           (double *)terms);
+  } else {
+    const size_t sm = sizeof(FfSmem<float>) * (NT / 32);
+    if ((e = set_smem(k_ff_warp<float>, sm)) != cudaSuccess) return e;
+    k_ff_warp<float><<<grid, NT, sm, s>>>(jobs, ids, n, leafA, leafB, (const float *)dataA, (const float *)dataB,
+                                          (float *)terms);
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t launch_term_jobs(int prec, const TermJob *jobs, const int32_t *ids, int njobs, const LeafDev *leafA,
                              const LeafDev *leafB, const BlockDev *blocks, const void *dataA, const void *dataB,
                              void *terms, cudaStream_t s) {
@@ -1147,20 +1365,31 @@ cudaError_t launch_near_eval(int prec, const TargetDev *tg, int ntg, const int2 
 cudaError_t launch_gaussian(int prec, const TargetDev *tg, const TargetState *st, int ntg, int p, uint64_t seed,
                             int round, void *x_base, cudaStream_t s) {
   if (ntg == 0) return cudaSuccess;
-  if (prec == 64)
-    k_gaussian<double><<<ntg, NT, 0, s>>>(tg, st, p, seed, round, (double *)x_base);
-  else
-    k_gaussian<float><<<ntg, NT, 0, s>>>(tg, st, p, seed, round, (float *)x_base);
+  if (prec == 64) k_gaussian<double><<<ntg, NT, 0, s>>>(tg, st, p, seed, round, (double *)x_base);
+  else k_gaussian<float><<<ntg, NT, 0, s>>>(tg, st, p, seed, round, (float *)x_base);
   return cudaGetLastError();
 }
 
-cudaError_t launch_orth(int prec, const TargetDev *tg, TargetState *st, int ntg, int p, double eps, void *y_base,
-                        double *qw, void *x_base, int round, cudaStream_t s) {
-  if (ntg == 0) return cudaSuccess;
-  if (prec == 64)
-    k_orth<double><<<ntg, NT, 0, s>>>(tg, st, p, eps, (const double *)y_base, qw, (double *)x_base, round);
-  else
-    k_orth<float><<<ntg, NT, 0, s>>>(tg, st, p, eps, (const float *)y_base, qw, (float *)x_base, round);
+cudaError_t launch_orth(int prec, const TargetDev *tg, const int32_t *ids_warp, int n_warp, const int32_t *ids_block,
+                        int n_block, TargetState *st, int p, double eps, void *y_base, double *qw, void *x_base,
+                        int round, cudaStream_t s) {
+  if (p > OW) return cudaErrorInvalidValue;
+  const int gw = (n_warp + NT / 32 - 1) / (NT / 32);
+  if (prec == 64) {
+    if (n_warp)
+      k_orth_warp<double><<<gw, NT, 0, s>>>(tg, ids_warp, n_warp, st, p, eps, (const double *)y_base, qw,
+                                            (double *)x_base, round);
+    if (n_block)
+      k_orth<double><<<n_block, NT, 0, s>>>(tg, ids_block, st, p, eps, (const double *)y_base, qw, (double *)x_base,
+                                            round);
+  } else {
+    if (n_warp)
+      k_orth_warp<float><<<gw, NT, 0, s>>>(tg, ids_warp, n_warp, st, p, eps, (const float *)y_base, qw,
+                                           (float *)x_base, round);
+    if (n_block)
+      k_orth<float><<<n_block, NT, 0, s>>>(tg, ids_block, st, p, eps, (const float *)y_base, qw, (float *)x_base,
+                                           round);
+  }
   return cudaGetLastError();
 }
 

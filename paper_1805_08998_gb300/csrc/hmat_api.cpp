@@ -1538,10 +1538,18 @@ void Product::run() {
       float x0 = 0.f, x1 = 0.f;
       cudaEventElapsedTime(&x0, fe[0], fe[1]);
       cudaEventElapsedTime(&x1, fe[1], fe[2]);
-      int64_t rsum = 0;
-      for (int i = 0; i < nf; i++) rsum += st[i].r;
-      std::fprintf(stderr, "hmat trace: final: %zu blocks (r <= 32) %.3f ms, %zu blocks %.3f ms, mean r %.1f\n",
-                   ids_small.size(), x0, ids_big.size(), x1, nf ? (double)rsum / nf : 0.0);
+      std::vector<TargetState> sf(nf);
+      if (nf) cudaMemcpy(sf.data(), d_st.p, sizeof(TargetState) * nf, cudaMemcpyDeviceToHost);
+      int64_t rsum = 0, swsum = 0;
+      int swmax = 0;
+      for (int i = 0; i < nf; i++) {
+        rsum += sf[i].r;
+        swsum += sf[i].sweeps;
+        swmax = std::max(swmax, sf[i].sweeps);
+      }
+      std::fprintf(stderr, "hmat trace: final: %zu blocks (r <= 32) %.3f ms, %zu blocks %.3f ms, mean r %.1f, "
+                   "sweeps mean %.2f max %d\n", ids_small.size(), x0, ids_big.size(), x1, nf ? (double)rsum / nf : 0.0,
+                   nf ? (double)swsum / nf : 0.0, swmax);
       for (auto &e : fe) cudaEventDestroy(e);
     }
     launches += (ids_small.empty() ? 0 : 1) + (ids_big.empty() ? 0 : 1);

@@ -193,6 +193,122 @@ __device__ __forceinline__ void warp_leaf(const LeafDev &lf, const T *data, bool
   }
 }
 
+// Sum over the warp of the P per-lane values v[0..P) (P in {8, 16}), halving the values each
+// lane carries at every exchange: returns, in every lane, the total of column
+// c = (lane >> (5 - log2 P)) & (P - 1); 32 / P consecutive lanes hold the same column.
+template <typename T, int P>
+__device__ __forceinline__ T warp_reduce_scatter(T (&v)[P], int lane) {
+  static_assert(P == 8 || P == 16, "panel width");
+  int off = 16;
+#pragma unroll
+  for (int h = P / 2; h >= 1; h /= 2) {
+    const bool hi = (lane & off) != 0;
+#pragma unroll
+    for (int k = 0; k < h; k++) {
+      const T send = hi ? v[k] : v[k + h];
+      const T keep = hi ? v[k + h] : v[k];
+      v[k] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+    }
+    off >>= 1;
+  }
+  T s = v[0];
+#pragma unroll
+  for (int o = P == 8 ? 2 : 1; o >= 1; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  return s;
+}
+
+// cw[q*SP + c] = sum_{i < len} M[i + q*ldm] * X[i][c] for q < r, with the panel X held in
+// registers (xr[u][c] = X[lane + 32 u][c], zero beyond len): lanes run along the rows, so every
+// load of a column of M is one coalesced request, and each column's P sums are combined by
+// warp_reduce_scatter. Columns are taken four at a time to keep several loads in flight.
+template <typename T, int P, int RB, int SP>
+__device__ __forceinline__ void warp_tn_reg(T *cw, const T *__restrict__ M, int64_t ldm, const T (&xr)[RB][P], int len,
+                                            int r) {
+  const int lane = threadIdx.x & 31;
+  constexpr int LPC = 32 / P;  // lanes holding one column after the reduction
+  const int col = (lane / LPC) & (P - 1);
+  int q = 0;
+  for (; q + 4 <= r; q += 4) {
+    T mv[4][RB];
+#pragma unroll
+    for (int w = 0; w < 4; w++)
+#pragma unroll
+      for (int u = 0; u < RB; u++) {
+        const int i = lane + 32 * u;
+        mv[w][u] = i < len ? __ldg(M + (int64_t)(q + w) * ldm + i) : T(0);
+      }
+#pragma unroll
+    for (int w = 0; w < 4; w++) {
+      T part[P];
+#pragma unroll
+      for (int c = 0; c < P; c++) {
+        T a = T(0);
+#pragma unroll
+        for (int u = 0; u < RB; u++) a += mv[w][u] * xr[u][c];
+        part[c] = a;
+      }
+      const T sum = warp_reduce_scatter<T, P>(part, lane);
+      if ((lane & (LPC - 1)) == 0) cw[(q + w) * SP + col] = sum;
+    }
+  }
+  for (; q < r; q++) {
+    T mv[RB];
+#pragma unroll
+    for (int u = 0; u < RB; u++) {
+      const int i = lane + 32 * u;
+      mv[u] = i < len ? __ldg(M + (int64_t)q * ldm + i) : T(0);
+    }
+    T part[P];
+#pragma unroll
+    for (int c = 0; c < P; c++) {
+      T a = T(0);
+#pragma unroll
+      for (int u = 0; u < RB; u++) a += mv[u] * xr[u][c];
+      part[c] = a;
+    }
+    const T sum = warp_reduce_scatter<T, P>(part, lane);
+    if ((lane & (LPC - 1)) == 0) cw[q * SP + col] = sum;
+  }
+}
+
+// The same reduction for a panel X of any height kept row-major in shared memory (row stride SP):
+// lanes run along the rows (coalesced loads of M), four columns of M share each X row read, and
+// each column's P sums are combined by warp_reduce_scatter.
+template <typename T, int P, int SP>
+__device__ __forceinline__ void warp_tn_rows(T *cw, const T *__restrict__ M, int64_t ldm, const T *X, int len,
+                                             int r) {
+  const int lane = threadIdx.x & 31;
+  constexpr int LPC = 32 / P;
+  const int col = (lane / LPC) & (P - 1);
+  for (int q = 0; q < r; q += 4) {
+    const int nq = min(4, r - q);
+    T acc[4][P];
+#pragma unroll
+    for (int w = 0; w < 4; w++)
+#pragma unroll
+      for (int c = 0; c < P; c++) acc[w][c] = T(0);
+#pragma unroll 2
+    for (int i = lane; i < len; i += 32) {
+      T mv[4];
+#pragma unroll
+      for (int w = 0; w < 4; w++) mv[w] = w < nq ? __ldg(M + (int64_t)(q + w) * ldm + i) : T(0);
+      const T *x = X + i * SP;
+#pragma unroll
+      for (int c = 0; c < P; c++) {
+        const T xv = x[c];
+#pragma unroll
+        for (int w = 0; w < 4; w++) acc[w][c] += mv[w] * xv;
+      }
+    }
+#pragma unroll
+    for (int w = 0; w < 4; w++) {
+      if (w >= nq) break;
+      const T sum = warp_reduce_scatter<T, P>(acc[w], lane);
+      if ((lane & (LPC - 1)) == 0) cw[(q + w) * SP + col] = sum;
+    }
+  }
+}
+
 // acc[rr][c] += sum_{q < r} M[lane + 32 rr + q*ldm] * C[q*SP + c], rows < rows (lane owns rows)
 template <typename T, int P, int RB, int SP>
 __device__ __forceinline__ void warp_nn_reg(T (&acc)[RB][P], const T *__restrict__ M, int64_t ldm, const T *C, int rows,
@@ -281,6 +397,17 @@ __global__ void __launch_bounds__(AT) k_apply(ApplyArgs a) {
   for (int rr = 0; rr < RBX; rr++)
 #pragma unroll
     for (int c = 0; c < P; c++) racc[rr][c] = T(0);
+  // RB > 0: the input panel is also held in registers, lane owning rows lane + 32 u
+  T xr[RBX][P];
+  if (RB > 0) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int u = 0; u < RBX; u++) {
+      const int i = lane + 32 * u;
+#pragma unroll
+      for (int c = 0; c < P; c++) xr[u][c] = i < inlen ? Xs[i * SP + c] : T(0);
+    }
+  }
   int base = 0;
   for (int blk = t.blk; blk >= 0; blk = a.blocks[blk].parent) {
     const int2 rg = a.blk_terms[blk];
@@ -294,7 +421,8 @@ __global__ void __launch_bounds__(AT) k_apply(ApplyArgs a) {
       const T *red = TRANS ? L : R;   // the factor contracted with the input panel
       const T *exp = TRANS ? R : L;   // the factor that expands into the output
       const int64_t ldred = TRANS ? tm.ldL : tm.ldR, ldexp = TRANS ? tm.ldR : tm.ldL;
-      warp_tn<T, P, false, SP>(cw, red, ldred, Xs, inlen, tm.rank);
+      if (RB > 0) warp_tn_reg<T, P, RBX, SP>(cw, red, ldred, xr, inlen, tm.rank);
+      else warp_tn_rows<T, P, SP>(cw, red, ldred, Xs, inlen, tm.rank);
       __syncwarp();
       if (RB > 0) warp_nn_reg<T, P, RBX, SP>(racc, exp, ldexp, cw, outlen, tm.rank);
       else warp_nn<T, P, true, SP>(Ys, exp, ldexp, cw, outlen, tm.rank);

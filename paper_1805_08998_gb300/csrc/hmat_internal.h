@@ -114,7 +114,7 @@ struct TargetState {
   int32_t p_new;        // columns kept in the current round
   int32_t rank;         // final rank
   int32_t nfwd;         // rounds in which the target was sampled
-  int32_t pad;
+  int32_t sweeps;       // Jacobi sweeps of the core truncation
   double nrm2;          // ||W||_F^2 over all columns so far (= ||Q Q^T S||_F^2)
   double est2;          // ||Y||_F^2 / p of the first round (scale for dropping)
   double tail2;         // discarded energy in the final truncation

@@ -859,6 +859,12 @@ __global__ void __launch_bounds__(NT) k_final(const TargetDev *tg, TargetState *
     V[i + j * JMAX] = (i == j) ? 1.0 : 0.0;
   }
   __syncthreads();
+  // Off-diagonal entries below skip = 1e-2 eps^2 trace(G) / r move no eigenvalue by more than a
+  // hundredth of the truncation threshold eps^2 trace(G): rotations on them are skipped, so the
+  // sweeps end once the entries that matter have converged.
+  double trace = 0.0;
+  for (int i = 0; i < r; i++) trace += G[i + i * JMAX];
+  const double skip = 1e-2 * eps * eps * trace / r;
   const int npair = rr / 2;
   for (int sweep = 0; sweep < 40; sweep++) {
     if (threadIdx.x == 0) changed_s = 0;
@@ -873,7 +879,7 @@ __global__ void __launch_bounds__(NT) k_final(const TargetDev *tg, TargetState *
         pr[2 * k + 1] = c;
         const double app = G[a + a * JMAX], aqq = G[c + c * JMAX], apq = G[a + c * JMAX];
         double co = 1.0, si = 0.0;
-        if (apq != 0.0 && fabs(apq) > 1e-15 * sqrt(fabs(app * aqq)) && fabs(apq) > 1e-300) {
+        if (apq != 0.0 && fabs(apq) > 1e-15 * sqrt(fabs(app * aqq)) && fabs(apq) > skip) {
           const double zeta = (aqq - app) / (2.0 * apq);
           const double tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
           co = 1.0 / sqrt(1.0 + tt * tt);
@@ -910,6 +916,7 @@ __global__ void __launch_bounds__(NT) k_final(const TargetDev *tg, TargetState *
     }
     const int ch = changed_s;
     __syncthreads();
+    if (threadIdx.x == 0) st[b].sweeps = sweep + 1;
     if (!ch) break;
   }
   // order eigenvalues descending, eps-rank
@@ -977,6 +984,29 @@ struct WarpFinalSmem {
   int order[WJ];
 };
 
+// Q <- Q V_k and W <- W V_k in place (rows of Q and W held by lanes), V_k = Vk[q + j*WJ] for
+// q < r <= RW, j < k; RW bounds the unrolled row length so that no FP64 work is spent on padding.
+template <int RW>
+__device__ __forceinline__ void warp_rotate_rows(double *Q, double *W, int64_t m, int64_t n, int r, int k,
+                                                 const double *Vk) {
+  const int lane = threadIdx.x & 31;
+  for (int mat = 0; mat < 2; mat++) {
+    double *M = mat == 0 ? Q : W;
+    const int64_t rows = mat == 0 ? m : n;
+    for (int64_t i = lane; i < rows; i += 32) {
+      double row[RW];
+#pragma unroll
+      for (int q = 0; q < RW; q++) row[q] = q < r ? M[i + (int64_t)q * rows] : 0.0;
+      for (int j = 0; j < k; j++) {
+        double sum = 0.0;
+#pragma unroll
+        for (int q = 0; q < RW; q++) sum += row[q] * Vk[q + j * WJ];
+        M[i + (int64_t)j * rows] = sum;
+      }
+    }
+  }
+}
+
 __global__ void __launch_bounds__(WF_WARPS * 32) k_final_warp(const TargetDev *tg, TargetState *st, const int32_t *ids,
                                                               int nids, double eps, double *qw) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1008,6 +1038,10 @@ __global__ void __launch_bounds__(WF_WARPS * 32) k_final_warp(const TargetDev *t
     S.G[j + i * WJ] = sum;
   }
   __syncwarp();
+  // rotations on entries below skip are left out (see k_final)
+  double trace = 0.0;
+  for (int i = 0; i < r; i++) trace += S.G[i + i * WJ];
+  const double skip = 1e-2 * eps * eps * trace / r;
   const int npair = rr / 2;
   for (int sweep = 0; sweep < 40; sweep++) {
     bool changed = false;
@@ -1019,7 +1053,7 @@ __global__ void __launch_bounds__(WF_WARPS * 32) k_final_warp(const TargetDev *t
         if (a > c) { const int tmp = a; a = c; c = tmp; }
         const double app = S.G[a + a * WJ], aqq = S.G[c + c * WJ], apq = S.G[a + c * WJ];
         double co = 1.0, si = 0.0;
-        if (apq != 0.0 && fabs(apq) > 1e-15 * sqrt(fabs(app * aqq)) && fabs(apq) > 1e-300) {
+        if (apq != 0.0 && fabs(apq) > 1e-15 * sqrt(fabs(app * aqq)) && fabs(apq) > skip) {
           const double zeta = (aqq - app) / (2.0 * apq);
           const double tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
           co = 1.0 / sqrt(1.0 + tt * tt);
@@ -1054,6 +1088,7 @@ __global__ void __launch_bounds__(WF_WARPS * 32) k_final_warp(const TargetDev *t
       }
       __syncwarp();
     }
+    if (lane == 0) st[b].sweeps = sweep + 1;
     if (!__any_sync(0xffffffffu, changed)) break;
   }
   int k = 0;
@@ -1086,21 +1121,10 @@ __global__ void __launch_bounds__(WF_WARPS * 32) k_final_warp(const TargetDev *t
     S.G[i + j * WJ] = i < r ? S.V[i + S.order[j] * WJ] : 0.0;
   }
   __syncwarp();
-  for (int mat = 0; mat < 2; mat++) {
-    double *M = mat == 0 ? Q : W;
-    const int64_t rows = mat == 0 ? m : n;
-    for (int64_t i = lane; i < rows; i += 32) {
-      double row[WJ];
-#pragma unroll
-      for (int q = 0; q < WJ; q++) row[q] = q < r ? M[i + (int64_t)q * rows] : 0.0;
-      for (int j = 0; j < k; j++) {
-        double sum = 0.0;
-#pragma unroll
-        for (int q = 0; q < WJ; q++) sum += row[q] * S.G[q + j * WJ];
-        M[i + (int64_t)j * rows] = sum;
-      }
-    }
-  }
+  if (r <= 8) warp_rotate_rows<8>(Q, W, m, n, r, k, S.G);
+  else if (r <= 16) warp_rotate_rows<16>(Q, W, m, n, r, k, S.G);
+  else if (r <= 24) warp_rotate_rows<24>(Q, W, m, n, r, k, S.G);
+  else warp_rotate_rows<WJ>(Q, W, m, n, r, k, S.G);
   if (lane == 0) {
     if (st[b].rank != -2) st[b].rank = k;
     else st[b].rank = -(k + 3);

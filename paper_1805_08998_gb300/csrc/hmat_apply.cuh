@@ -167,32 +167,6 @@ __device__ __forceinline__ void warp_nn(T *out, const T *__restrict__ M, int64_t
   }
 }
 
-// One leaf of an H-matrix block with origin (row0, col0):
-//   trans = false: Out[rows of leaf] += leaf   * X[cols of leaf]
-//   trans = true:  Out[cols of leaf] += leaf^T * X[rows of leaf]
-template <typename T, int P, int SP>
-__device__ __forceinline__ void warp_leaf(const LeafDev &lf, const T *data, bool trans, int64_t row0, int64_t col0,
-                                          const T *X, T *Out, T *cw) {
-  const int ro = (int)(lf.row - row0), co = (int)(lf.col - col0);
-  if (lf.rank < 0) {
-    const T *D = data + lf.off_u;
-    if (!trans) warp_nn<T, P, true, SP>(Out + ro * SP, D, lf.m, X + co * SP, lf.m, lf.n);
-    else warp_tn<T, P, true, SP>(Out + co * SP, D, lf.m, X + ro * SP, lf.m, lf.n);
-  } else if (lf.rank > 0) {
-    const T *U = data + lf.off_u, *V = data + lf.off_v;
-    if (!trans) {
-      warp_tn<T, P, false, SP>(cw, V, lf.n, X + co * SP, lf.n, lf.rank);
-      __syncwarp();
-      warp_nn<T, P, true, SP>(Out + ro * SP, U, lf.m, cw, lf.m, lf.rank);
-    } else {
-      warp_tn<T, P, false, SP>(cw, U, lf.m, X + ro * SP, lf.m, lf.rank);
-      __syncwarp();
-      warp_nn<T, P, true, SP>(Out + co * SP, V, lf.n, cw, lf.n, lf.rank);
-    }
-    __syncwarp();
-  }
-}
-
 // Sum over the warp of the P per-lane values v[0..P) (P in {8, 16}), halving the values each
 // lane carries at every exchange: returns, in every lane, the total of column
 // c = (lane >> (5 - log2 P)) & (P - 1); 32 / P consecutive lanes hold the same column.
@@ -274,7 +248,7 @@ __device__ __forceinline__ void warp_tn_reg(T *cw, const T *__restrict__ M, int6
 // The same reduction for a panel X of any height kept row-major in shared memory (row stride SP):
 // lanes run along the rows (coalesced loads of M), four columns of M share each X row read, and
 // each column's P sums are combined by warp_reduce_scatter.
-template <typename T, int P, int SP>
+template <typename T, int P, int SP, bool ATOMIC = false>
 __device__ __forceinline__ void warp_tn_rows(T *cw, const T *__restrict__ M, int64_t ldm, const T *X, int len,
                                              int r) {
   const int lane = threadIdx.x & 31;
@@ -304,8 +278,44 @@ __device__ __forceinline__ void warp_tn_rows(T *cw, const T *__restrict__ M, int
     for (int w = 0; w < 4; w++) {
       if (w >= nq) break;
       const T sum = warp_reduce_scatter<T, P>(acc[w], lane);
-      if ((lane & (LPC - 1)) == 0) cw[(q + w) * SP + col] = sum;
+      if ((lane & (LPC - 1)) == 0) acc_add(cw + (q + w) * SP + col, sum, ATOMIC);
     }
+  }
+}
+
+// M^T X into out (rows q of out, stride SP): by lanes along the rows (warp_tn_rows) for long
+// columns or wide panels, by lane groups per column (warp_tn) for short columns of 8-wide panels,
+// where the per-column exchange of warp_tn_rows would cost more than its coalescing saves.
+template <typename T, int P, int SP, bool ATOMIC>
+__device__ __forceinline__ void warp_tn_any(T *out, const T *__restrict__ M, int64_t ldm, const T *X, int len,
+                                            int r) {
+  if (P >= 16 || len >= 128) warp_tn_rows<T, P, SP, ATOMIC>(out, M, ldm, X, len, r);
+  else warp_tn<T, P, ATOMIC, SP>(out, M, ldm, X, len, r);
+}
+
+// One leaf of an H-matrix block with origin (row0, col0):
+//   trans = false: Out[rows of leaf] += leaf   * X[cols of leaf]
+//   trans = true:  Out[cols of leaf] += leaf^T * X[rows of leaf]
+template <typename T, int P, int SP>
+__device__ __forceinline__ void warp_leaf(const LeafDev &lf, const T *data, bool trans, int64_t row0, int64_t col0,
+                                          const T *X, T *Out, T *cw) {
+  const int ro = (int)(lf.row - row0), co = (int)(lf.col - col0);
+  if (lf.rank < 0) {
+    const T *D = data + lf.off_u;
+    if (!trans) warp_nn<T, P, true, SP>(Out + ro * SP, D, lf.m, X + co * SP, lf.m, lf.n);
+    else warp_tn_any<T, P, SP, true>(Out + co * SP, D, lf.m, X + ro * SP, lf.m, lf.n);
+  } else if (lf.rank > 0) {
+    const T *U = data + lf.off_u, *V = data + lf.off_v;
+    if (!trans) {
+      warp_tn_any<T, P, SP, false>(cw, V, lf.n, X + co * SP, lf.n, lf.rank);
+      __syncwarp();
+      warp_nn<T, P, true, SP>(Out + ro * SP, U, lf.m, cw, lf.m, lf.rank);
+    } else {
+      warp_tn_any<T, P, SP, false>(cw, U, lf.m, X + ro * SP, lf.m, lf.rank);
+      __syncwarp();
+      warp_nn<T, P, true, SP>(Out + co * SP, V, lf.n, cw, lf.n, lf.rank);
+    }
+    __syncwarp();
   }
 }
 
@@ -422,7 +432,7 @@ __global__ void __launch_bounds__(AT) k_apply(ApplyArgs a) {
       const T *exp = TRANS ? R : L;   // the factor that expands into the output
       const int64_t ldred = TRANS ? tm.ldL : tm.ldR, ldexp = TRANS ? tm.ldR : tm.ldL;
       if (RB > 0) warp_tn_reg<T, P, RBX, SP>(cw, red, ldred, xr, inlen, tm.rank);
-      else warp_tn_rows<T, P, SP>(cw, red, ldred, Xs, inlen, tm.rank);
+      else warp_tn_any<T, P, SP, false>(cw, red, ldred, Xs, inlen, tm.rank);
       __syncwarp();
       if (RB > 0) warp_nn_reg<T, P, RBX, SP>(racc, exp, ldexp, cw, outlen, tm.rank);
       else warp_nn<T, P, true, SP>(Ys, exp, ldexp, cw, outlen, tm.rank);
@@ -443,7 +453,8 @@ __global__ void __launch_bounds__(AT) k_apply(ApplyArgs a) {
       if (RB > 0) warp_nn_reg<T, P, RBX, SP>(racc, DA, la.m, cw, la.m, rho);
       else warp_nn<T, P, true, SP>(Ys, DA, la.m, cw, la.m, rho);   // Y += D_A cw
     } else {
-      warp_tn<T, P, false, SP>(cw, DA, la.m, Xs, la.m, rho);  // cw = D_A^T Q    (rho x P)
+      if (RB > 0) warp_tn_reg<T, P, RBX, SP>(cw, DA, la.m, xr, la.m, rho);  // cw = D_A^T Q (rho x P)
+      else warp_tn<T, P, false, SP>(cw, DA, la.m, Xs, la.m, rho);
       __syncwarp();
       warp_tn<T, P, true, SP>(Ys, DB, rho, cw, rho, lb.n);    // W += D_B^T cw
     }

@@ -50,6 +50,39 @@ def _rank_env():
             int(os.environ.get("WORLD_SIZE", "1")))
 
 
+class Replicas:
+    """Host side of an N-rank run of the benchmark: every rank computes the whole workload on its
+    own GPU (the product does not shard across GPUs here), the ranks meet at barriers around the
+    timed region, and the slowest rank's time is the job's time."""
+
+    def __init__(self, dist=None, device="cpu"):
+        self.dist = dist
+        self.device = device
+
+    def barrier(self):
+        if self.dist is not None:
+            self.dist.barrier()
+
+    def max(self, x: float) -> float:
+        if self.dist is None:
+            return float(x)
+        import torch
+        t = torch.tensor([float(x)], dtype=torch.float64, device=self.device)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+
+def replica_value(n_points: int, ms_max: float, world: int) -> float:
+    """Whole-job throughput in degrees of freedom per second: every rank multiplies its own
+    N-point product, so the job does world * N degrees of freedom in the slowest rank's time."""
+    return world * n_points / (ms_max * 1e-3)
+
+
+def reference_runs_here(rank: int, world: int) -> bool:
+    """The oracle arm runs on rank 0 only; other ranks exit without work."""
+    return world <= 1 or rank == 0
+
+
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -115,10 +148,11 @@ class ClockSampler:
 
 
 def _traffic_from_profile():
-    """DRAM bytes per k_apply launch from the committed ncu summary, if it was taken on the
-    current kernel source (the summary records the source's sha256)."""
+    """DRAM bytes (read + write) of one sum-expression application pass (all size classes)
+    from the committed ncu summary, if it was taken on the current kernel source (the summary
+    records the sha256 of hmat_apply.cuh); otherwise None."""
     prof = os.path.join(ROOT, "profiles", "k_apply_sphere_n32768.md")
-    src = os.path.join(ROOT, "paper_1805_08998_gb300", "csrc", "hmat_kernels.cu")
+    src = os.path.join(ROOT, "paper_1805_08998_gb300", "csrc", "hmat_apply.cuh")
     if not (os.path.exists(prof) and os.path.exists(src)):
         return None
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
@@ -126,7 +160,7 @@ def _traffic_from_profile():
     if f"kernel source sha256: {sha}" not in txt:
         return None
     for line in txt.splitlines():
-        if line.startswith("dram_bytes_per_launch:"):
+        if line.startswith("dram_bytes_per_pass:"):
             return float(line.split(":")[1])
     return None
 
@@ -188,7 +222,7 @@ def oracle_sample(n_blocks_per_level=2, seed=0, threads=None, budget_s=25.0, set
 
 def run_reference(args):
     rank, _, world = _rank_env()
-    if world > 1 and rank != 0:
+    if not reference_runs_here(rank, world):
         return
     setup = None
     for w in range(args.warmup):
@@ -239,16 +273,8 @@ def run_ours(args):
     def mult(mode, seed):
         return H.hmat_multiply(A, B, W["eps"], mode=mode, block_width=W["block_width"], seed=seed, stream=stream)
 
-    def barrier():
-        if dist is not None:
-            dist.barrier()
-
-    def max_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    rep = Replicas(dist, dev)
+    barrier, max_over_ranks = rep.barrier, rep.max
 
     # ---- warm-up (chosen form and plain FP64)
     for w in range(max(args.warmup, 3)):
@@ -336,7 +362,7 @@ def run_ours(args):
     peak, peak_kind = _peaks()
     traffic = _traffic_from_profile()
     launches = int(sum(s["launches"] for s in stats))
-    value = world * W["n"] / (ms * 1e-3)
+    value = replica_value(W["n"], ms, world)
 
     if rank == 0:
         # CPU oracle baseline on the host cores (bounded sample)
@@ -347,7 +373,7 @@ def run_ours(args):
             "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             "config": dict(W, parallelism="replicas" if world > 1 else "single"),
             "gflops": gflops,
-            "plain_f64": {"ms_per_step": ms64, "value": world * W["n"] / (ms64 * 1e-3),
+            "plain_f64": {"ms_per_step": ms64, "value": replica_value(W["n"], ms64, world),
                           "gflops": flops64 / (ms64 * 1e-3) / 1e9, "steps": k64},
             "speedup_vs_plain_f64": ms64 / ms,
             "status": int(last_status),
@@ -360,7 +386,7 @@ def run_ours(args):
                          "algorithmic_bytes_per_launch": apply_bytes / max(apply_launches, 1)},
             "cpu_baseline": {"value": W["n"] / t_est, "unit": UNIT, "cores": thr, "kind": "oracle",
                              "sample": desc},
-            "e2e": {"value": world * W["n"] / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d // e2e_steps,
+            "e2e": {"value": replica_value(W["n"], e2e_s * 1e3, world), "unit": UNIT, "h2d_bytes_per_step": h2d // e2e_steps,
                     "d2h_bytes_per_step": d2h // e2e_steps, "ms_per_step": e2e_s * 1e3,
                     "includes": "points H2D (pinned), hmat_build x2 (GPU ACA), hmat_multiply, C factors D2H (pinned)"},
             "gpu_launches": launches,

@@ -1036,10 +1036,10 @@ void Product::run() {
     ~EvGuard() { for (int i = 0; i < 6; i++) cudaEventDestroy(e[i]); }
   } evg{ev};
 
-  // Far x far products with both ranks <= 32 and at most 2048 inner rows run one warp per job
-  // (listed first), the others one block per job.
+  // FP32 far x far products with both ranks <= 32 and at most 2048 inner rows run one warp per
+  // job (listed first), the others (and all FP64 ones) one block per job.
   int n_ff_warp = 0;
-  {
+  if (cprec == 32) {
     std::vector<int32_t> big;
     for (int32_t i : ff_ids) {
       const LeafDev &la = A->leaves[jobs[i].a], &lb = B->leaves[jobs[i].b];

@@ -283,13 +283,14 @@ __device__ __forceinline__ void warp_tn_rows(T *cw, const T *__restrict__ M, int
   }
 }
 
-// M^T X into out (rows q of out, stride SP): by lanes along the rows (warp_tn_rows) for long
-// columns or wide panels, by lane groups per column (warp_tn) for short columns of 8-wide panels,
-// where the per-column exchange of warp_tn_rows would cost more than its coalescing saves.
+// M^T X into out (rows q of out, stride SP): in FP32 by lanes along the rows (warp_tn_rows) for
+// long columns or wide panels, otherwise by lane groups per column (warp_tn): for short columns
+// of 8-wide panels the per-column exchange of warp_tn_rows costs more than its coalescing saves.
 template <typename T, int P, int SP, bool ATOMIC>
 __device__ __forceinline__ void warp_tn_any(T *out, const T *__restrict__ M, int64_t ldm, const T *X, int len,
                                             int r) {
-  if (P >= 16 || len >= 128) warp_tn_rows<T, P, SP, ATOMIC>(out, M, ldm, X, len, r);
+  // FP64: the lane-group form throughout (the FP64 pipe, not the load path, bounds it)
+  if (sizeof(T) == 4 && (P >= 16 || len >= 128)) warp_tn_rows<T, P, SP, ATOMIC>(out, M, ldm, X, len, r);
   else warp_tn<T, P, ATOMIC, SP>(out, M, ldm, X, len, r);
 }
 
@@ -407,9 +408,10 @@ __global__ void __launch_bounds__(AT) k_apply(ApplyArgs a) {
   for (int rr = 0; rr < RBX; rr++)
 #pragma unroll
     for (int c = 0; c < P; c++) racc[rr][c] = T(0);
-  // RB > 0: the input panel is also held in registers, lane owning rows lane + 32 u
+  // FP32 with RB > 0: the input panel is also held in registers, lane owning rows lane + 32 u
+  constexpr bool XREG = RB > 0 && sizeof(T) == 4;
   T xr[RBX][P];
-  if (RB > 0) {
+  if (XREG) {
     const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int u = 0; u < RBX; u++) {
@@ -431,7 +433,7 @@ __global__ void __launch_bounds__(AT) k_apply(ApplyArgs a) {
       const T *red = TRANS ? L : R;   // the factor contracted with the input panel
       const T *exp = TRANS ? R : L;   // the factor that expands into the output
       const int64_t ldred = TRANS ? tm.ldL : tm.ldR, ldexp = TRANS ? tm.ldR : tm.ldL;
-      if (RB > 0) warp_tn_reg<T, P, RBX, SP>(cw, red, ldred, xr, inlen, tm.rank);
+      if (XREG) warp_tn_reg<T, P, RBX, SP>(cw, red, ldred, xr, inlen, tm.rank);
       else warp_tn_any<T, P, SP, false>(cw, red, ldred, Xs, inlen, tm.rank);
       __syncwarp();
       if (RB > 0) warp_nn_reg<T, P, RBX, SP>(racc, exp, ldexp, cw, outlen, tm.rank);
@@ -453,7 +455,7 @@ __global__ void __launch_bounds__(AT) k_apply(ApplyArgs a) {
       if (RB > 0) warp_nn_reg<T, P, RBX, SP>(racc, DA, la.m, cw, la.m, rho);
       else warp_nn<T, P, true, SP>(Ys, DA, la.m, cw, la.m, rho);   // Y += D_A cw
     } else {
-      if (RB > 0) warp_tn_reg<T, P, RBX, SP>(cw, DA, la.m, xr, la.m, rho);  // cw = D_A^T Q (rho x P)
+      if (XREG) warp_tn_reg<T, P, RBX, SP>(cw, DA, la.m, xr, la.m, rho);  // cw = D_A^T Q (rho x P)
       else warp_tn<T, P, false, SP>(cw, DA, la.m, Xs, la.m, rho);
       __syncwarp();
       warp_tn<T, P, true, SP>(Ys, DB, rho, cw, rho, lb.n);    // W += D_B^T cw

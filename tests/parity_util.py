@@ -56,3 +56,47 @@ def _check_product(oracle, T, C, DC, eps, near_rtol, tol_factor=1.5, rank_slack=
             assert e <= near_rtol, (l, e)
             worst_near = max(worst_near, e)
     return worst, worst_near, n_far
+
+
+def sampled_far_near(T, n_far, n_near, seed, max_mn=512 * 512):
+    """Far leaves stratified by level (at most m*n = max_mn entries each) and near leaves, drawn
+    with a seeded generator: the blocks a large product is checked on."""
+    rng = np.random.default_rng(seed)
+    lv = T.leaf_blocks[:, 3]
+    kind = T.leaf_blocks[:, 2]
+    sizes = np.array([T.leaf_ranges(l) for l in range(T.nleaf)])
+    mn = sizes[:, 1] * sizes[:, 3]
+    far = []
+    levels = sorted(set(lv[kind == 1].tolist()))
+    per = max(1, n_far // max(1, len(levels)))
+    for level in levels:
+        cand = np.nonzero((lv == level) & (kind == 1) & (mn <= max_mn))[0]
+        if len(cand):
+            far += rng.choice(cand, size=min(per, len(cand)), replace=False).tolist()
+    near_c = np.nonzero(kind != 1)[0]
+    near = rng.choice(near_c, size=min(n_near, len(near_c)), replace=False).tolist()
+    return far, near
+
+
+def check_sampled(oracle, T, Ao, Bo, C, eps, near_rtol, far, near, tol_factor=1.5, rank_slack=2):
+    """The sampled leaves of C against the exact blocks A|tau x I * B|I x sigma of the oracle's
+    inputs: far leaves within tol_factor * eps with rank <= eps-rank + rank_slack, near leaves
+    within near_rtol in relative Frobenius norm."""
+    worst = 0.0
+    for l in far:
+        r0, m, c0, n = T.leaf_ranges(l)
+        blk = oracle.block_product(Ao, Bo, r0, m, c0, n)
+        U, V = C.leaf_get(l)
+        nb = np.linalg.norm(blk)
+        err = np.linalg.norm(blk - U @ V.T) / nb if nb > 0 else np.linalg.norm(U @ V.T)
+        tr = oracle.truth_for_block(blk, eps, l)
+        assert err <= tol_factor * eps, (l, err, U.shape[1], tr.k_eps)
+        assert U.shape[1] <= tr.k_eps + rank_slack, (l, U.shape[1], tr.k_eps)
+        worst = max(worst, err)
+    for l in near:
+        r0, m, c0, n = T.leaf_ranges(l)
+        blk = oracle.block_product(Ao, Bo, r0, m, c0, n)
+        D = C.leaf_get(l)
+        e = np.linalg.norm(D - blk) / max(np.linalg.norm(blk), 1e-300)
+        assert e <= near_rtol, (l, e)
+    return worst

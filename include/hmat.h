@@ -172,6 +172,17 @@ hmat_status hmat_build(const double *xyz, int64_t n, int dim, hmat_kernel kernel
 hmat_status hmat_multiply(const hmat_t A, const hmat_t B, const hmat_mult_opts *opts,
                           void *stream, hmat_t *C);
 
+/* count independent products C[i] = A[i] B[i] (each pair on one block tree; the trees of
+ * different pairs may differ) with the same options, in one call: the products are planned on
+ * host threads and run on up to 8 streams of their own, largest first, so that the GPU works on
+ * several products at once; every stream first waits for the work already queued on `stream`,
+ * and `stream` then waits for all of them. Outputs are caller-owned handles (release each with
+ * hmat_destroy). Status: the first failing product's status, with every C[i] NULL, except
+ * HMAT_ENOTCONV, which leaves all outputs valid. The paper treats one product at a time (Sec. 4);
+ * this is the batched form of the same call. */
+hmat_status hmat_multiply_batched(const hmat_t *A, const hmat_t *B, int count, const hmat_mult_opts *opts,
+                                  void *stream, hmat_t *C);
+
 /* Dense copy of the whole matrix in ORIGINAL point order into the host buffer out
  * (column-major, leading dimension ld >= n). Synchronises `stream` of the handle's last
  * use. Intended for checking small problems. */

@@ -6,11 +6,13 @@
 #include <atomic>
 #include <chrono>
 #include <cmath>
+#include <condition_variable>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <limits>
 #include <memory>
+#include <mutex>
 #include <stdexcept>
 #include <string>
 #include <thread>
@@ -800,14 +802,44 @@ hmat_status hmat_sumexpr_counts(const hmat_t A, const hmat_t B, int64_t *n_lowra
 
 namespace {
 
+// Device-memory admission for products run side by side (hmat_multiply_batched): a product
+// reserves its estimated bytes before its first large allocation and returns them when it ends;
+// a product that does not fit waits until enough have ended, and runs alone if it exceeds the
+// whole budget.
+struct MemGate {
+  std::mutex m;
+  std::condition_variable cv;
+  int64_t budget = 0, used = 0;
+  int running = 0;
+  void acquire(int64_t b) {
+    std::unique_lock<std::mutex> lk(m);
+    cv.wait(lk, [&] { return running == 0 || used + b <= budget; });
+    used += b;
+    running++;
+  }
+  void release(int64_t b) {
+    {
+      std::lock_guard<std::mutex> lk(m);
+      used -= b;
+      running--;
+    }
+    cv.notify_all();
+  }
+};
+
 struct Product {
   const hmat_s *A, *B;
   const hmat_mult_opts *o;
   cudaStream_t s;
   int cprec;              // compute / output precision
   std::unique_ptr<hmat_s> C;
+  MemGate *gate = nullptr;  // set by the batched call
+  int64_t gate_bytes = 0;
 
   void run();
+  ~Product() {
+    if (gate && gate_bytes) gate->release(gate_bytes);
+  }
 };
 
 // HMAT_CHECK_FINITE=1: after each phase of a product, scan its outputs for NaN/Inf and report
@@ -1051,6 +1083,23 @@ void Product::run() {
   // ---- a2: low-rank products. Far x far products (small) run one job per warp or block;
   // products with an inadmissible factor run as panels of up to panel_width() columns.
   ck(cudaEventRecord(ev[0], s), "event");
+  if (tr.on)
+    std::fprintf(stderr, "hmat trace: buffers: terms %lld elems, panel staging %lld x %lld\n", (long long)term_elems,
+                 (long long)std::min<int64_t>((int64_t)pk[NB + 1].size(), PANEL_GSTAGE_SLOTS),
+                 (long long)(2 * pdim[NB + 1] * panel_row_stride(PW)));
+  if (gate) {  // reserve this product's device memory: terms, sampling buffers, near field
+    int64_t est = (int64_t)es * term_elems;
+    for (const LeafDev &l : A->leaves) {
+      if (l.rank >= 0) {
+        const int64_t mx = std::max(l.m, l.n);
+        est += (int64_t)sizeof(double) * (l.m + l.n) * 96 + (int64_t)es * (2 * mx * 16 + 3 * mx * 16);
+      } else {
+        est += (int64_t)es * l.m * l.n;
+      }
+    }
+    gate_bytes = est + (est >> 3);
+    gate->acquire(gate_bytes);
+  }
   DevBuf d_termbuf(es * std::max<int64_t>(term_elems, 1), s);
   DevBuf d_jobs = upload(jobs, s), d_ffids = upload(ff_ids, s), d_panels = upload(panels, s);
   DevBuf d_blkterms = upload(blk_terms, s);
@@ -1078,7 +1127,9 @@ void Product::run() {
   a2mark(-1, 1);
   int64_t launches = 1 + (n_ff_warp > 0 ? 1 : 0) + ((int)ff_ids.size() > n_ff_warp ? 1 : 0);
   const int64_t pstride = (int64_t)2 * pdim[NB + 1] * panel_row_stride(PW);
-  DevBuf d_pstage(es * std::max<int64_t>(pstride * (int64_t)pk[NB + 1].size(), 1), s);
+  // one staging slot per thread block of the global-staging launch (it loops over its panels)
+  const int64_t pslots = std::min<int64_t>((int64_t)pk[NB + 1].size(), PANEL_GSTAGE_SLOTS);
+  DevBuf d_pstage(es * std::max<int64_t>(pstride * pslots, 1), s);
   for (int k = 0; k < NB + 2; k++) {
     if (pk[k].empty()) continue;
     PanelArgs pa{};
@@ -1341,6 +1392,9 @@ void Product::run() {
   ck(cudaEventCreateWithFlags(&s2.e1, cudaEventDisableTiming), "event");
   // the near field's tables go up on the second stream (idle, so the copies do not wait for the
   // products), then that stream waits for the products
+  if (tr.on)
+    std::fprintf(stderr, "hmat trace: buffers: near %lld, qw %lld, xy %lld, stage %lld elems\n", (long long)near_elems,
+                 (long long)qw_elems, (long long)xy_elems, (long long)stage_elems);
   DevBuf d_near(es * std::max<int64_t>(near_elems, 1), s2.st);
   DevBuf d_near_leaves = upload(C->leaves, s2.st);
   DevBuf d_ntg = upload(ntg, s2.st), d_npairs = upload(npairs, s2.st);
@@ -1628,19 +1682,128 @@ void Product::run() {
 
 }  // namespace
 
+namespace {
+
+void check_pair(const hmat_s *A, const hmat_s *B, const hmat_mult_opts *opts) {
+  if (!A || !B || !opts) fail(HMAT_EINVAL, "NULL argument");
+  if (!(opts->eps > 0.0) || !std::isfinite(opts->eps)) fail(HMAT_EINVAL, "eps must be a positive number");
+  if (opts->mode != HMAT_MODE_F64 && opts->mode != HMAT_MODE_MIXED) fail(HMAT_EINVAL, "unknown mode");
+  if (A->tree != B->tree) {
+    const Tree &ta = *A->tree, &tb = *B->tree;
+    if (!same_points(ta, tb.orig.data(), tb.n, tb.dim) || ta.leaf_size != tb.leaf_size || ta.eta != tb.eta)
+      fail(HMAT_EMISMATCH, "A and B are not on one block tree");
+  }
+  if (A->prec != B->prec) fail(HMAT_EINVAL, "A and B must have the same factor precision");
+}
+
+}  // namespace
+
+extern "C" hmat_status hmat_multiply_batched(const hmat_t *A, const hmat_t *B, int count, const hmat_mult_opts *opts,
+                                             void *stream, hmat_t *C) {
+  if (C && count > 0)
+    for (int i = 0; i < count; i++) C[i] = nullptr;
+  return guard([&] {
+    if (!A || !B || !C || !opts || count < 0) fail(HMAT_EINVAL, "NULL argument or negative count");
+    for (int i = 0; i < count; i++) check_pair(A[i], B[i], opts);
+    if (count == 0) return;
+    // products on NS worker threads, each with its own stream that first waits for the caller's
+    // stream; the largest products start first; the caller's stream waits for all of them
+    const int NS = std::min(count, 8);
+    std::vector<int> order(count);
+    for (int i = 0; i < count; i++) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return A[x]->tree->n > A[y]->tree->n; });
+    cudaStream_t caller = (cudaStream_t)stream;
+    cudaEvent_t start;
+    ck(cudaEventCreateWithFlags(&start, cudaEventDisableTiming), "event");
+    std::vector<cudaStream_t> ws(NS, nullptr);
+    std::vector<cudaEvent_t> done(NS, nullptr);
+    struct Cleanup {
+      cudaEvent_t &start;
+      std::vector<cudaStream_t> &ws;
+      std::vector<cudaEvent_t> &done;
+      ~Cleanup() {
+        for (auto e : done) if (e) cudaEventDestroy(e);
+        for (auto st : ws) if (st) cudaStreamDestroy(st);
+        if (start) cudaEventDestroy(start);
+      }
+    } cleanup{start, ws, done};
+    ck(cudaEventRecord(start, caller), "event");
+    for (int w = 0; w < NS; w++) {
+      ck(cudaStreamCreateWithFlags(&ws[w], cudaStreamNonBlocking), "stream");
+      ck(cudaEventCreateWithFlags(&done[w], cudaEventDisableTiming), "event");
+      ck(cudaStreamWaitEvent(ws[w], start, 0), "stream wait");
+    }
+    MemGate gate;
+    {
+      size_t fr = 0, tot = 0;
+      ck(cudaMemGetInfo(&fr, &tot), "memory info");
+      gate.budget = (int64_t)(0.8 * (double)fr);
+    }
+    std::vector<std::unique_ptr<hmat_s>> out(count);
+    std::vector<hmat_status> st(count, HMAT_OK);
+    std::vector<std::string> msg(count);
+    std::atomic<int> next{0};
+    int dev = 0;
+    ck(cudaGetDevice(&dev), "device");
+    auto worker = [&](int w) {
+      cudaSetDevice(dev);
+      for (int k = next++; k < count; k = next++) {
+        const int i = order[k];
+        try {
+          Product pr;
+          pr.A = A[i];
+          pr.B = B[i];
+          pr.o = opts;
+          pr.s = ws[w];
+          pr.cprec = opts->mode == HMAT_MODE_F64 ? 64 : A[i]->prec;
+          pr.gate = &gate;
+          pr.run();
+          out[i] = std::move(pr.C);
+        } catch (const HErr &f) {
+          st[i] = f.st;
+          msg[i] = f.msg;
+        } catch (const std::bad_alloc &) {
+          st[i] = HMAT_ENOMEM;
+          msg[i] = "host allocation failed";
+        } catch (const std::exception &e) {
+          st[i] = HMAT_EINVAL;
+          msg[i] = e.what();
+        }
+      }
+    };
+    std::vector<std::thread> th;
+    for (int w = 1; w < NS; w++) th.emplace_back(worker, w);
+    worker(0);
+    for (auto &x : th) x.join();
+    for (int w = 0; w < NS; w++) {
+      ck(cudaEventRecord(done[w], ws[w]), "event");
+      ck(cudaStreamWaitEvent(caller, done[w], 0), "stream wait");
+    }
+    // the outputs belong to the caller's stream from here on (the worker streams end with this
+    // call); the caller's stream already waits for the work that produced them
+    for (auto &h : out)
+      if (h) {
+        h->stream = caller;
+        h->d_data.s = caller;
+        h->d_leaves.s = caller;
+      }
+    for (int i = 0; i < count; i++)
+      if (st[i] != HMAT_OK) fail(st[i], "product " + std::to_string(i) + ": " + msg[i]);
+    bool nc = false;
+    for (int i = 0; i < count; i++) {
+      nc |= out[i]->stats.not_converged > 0;
+      C[i] = out[i].release();
+    }
+    if (nc) fail(HMAT_ENOTCONV, "some far blocks hit max_rank or max_rounds");
+  });
+}
+
 extern "C" hmat_status hmat_multiply(const hmat_t A, const hmat_t B, const hmat_mult_opts *opts, void *stream,
                                      hmat_t *C) {
   if (C) *C = nullptr;
   return guard([&] {
-    if (!A || !B || !opts || !C) fail(HMAT_EINVAL, "NULL argument");
-    if (!(opts->eps > 0.0) || !std::isfinite(opts->eps)) fail(HMAT_EINVAL, "eps must be a positive number");
-    if (opts->mode != HMAT_MODE_F64 && opts->mode != HMAT_MODE_MIXED) fail(HMAT_EINVAL, "unknown mode");
-    if (A->tree != B->tree) {
-      const Tree &ta = *A->tree, &tb = *B->tree;
-      if (!same_points(ta, tb.orig.data(), tb.n, tb.dim) || ta.leaf_size != tb.leaf_size || ta.eta != tb.eta)
-        fail(HMAT_EMISMATCH, "A and B are not on one block tree");
-    }
-    if (A->prec != B->prec) fail(HMAT_EINVAL, "A and B must have the same factor precision");
+    if (!C) fail(HMAT_EINVAL, "NULL argument");
+    check_pair(A, B, opts);
     Product pr;
     pr.A = A;
     pr.B = B;

@@ -64,7 +64,7 @@ static cudaError_t launch_panels_t(const PanelArgs &a, bool leaf_kind, cudaStrea
   if (a.gstage) {
     if ((e = cudaFuncSetAttribute(k_panel<T, P, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
       return e;
-    k_panel<T, P, true><<<a.count, AT, smem, s>>>(a);
+    k_panel<T, P, true><<<std::min(a.count, PANEL_GSTAGE_SLOTS), AT, smem, s>>>(a);
   } else {
     if ((e = cudaFuncSetAttribute(k_panel<T, P, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
       return e;

@@ -22,6 +22,8 @@ namespace hm {
 // each owning one row of an atomically updated output, fall into distinct banks.
 __host__ __device__ constexpr int apply_row_stride(int P) { return P; }
 __host__ __device__ constexpr int panel_row_stride(int P) { return P + 1; }
+// thread blocks (and global staging slots) of a launch of panels staged in global memory
+constexpr int PANEL_GSTAGE_SLOTS = 152 * 4;
 
 // learned rank proposal: 12 features -> 64 -> 64 -> 1
 constexpr int RANK_FEATURES = 12;

@@ -24,7 +24,7 @@ PTS_CUBE, PTS_SPHERE = 0, 1
 MODE_F64, MODE_MIXED = 0, 1
 
 # every symbol include/hmat.h declares
-EXPORTS = ["hmat_points", "hmat_build", "hmat_multiply", "hmat_to_dense", "hmat_leaf_count", "hmat_leaf_info",
+EXPORTS = ["hmat_points", "hmat_build", "hmat_multiply", "hmat_multiply_batched", "hmat_to_dense", "hmat_leaf_count", "hmat_leaf_info",
            "hmat_leaf_get", "hmat_permutation", "hmat_stats", "hmat_sumexpr_counts", "hmat_destroy",
            "hmat_data_bytes", "hmat_data_get", "hmat_rank_features", "hmat_rankmodel_train",
            "hmat_rankmodel_predict", "hmat_rankmodel_get", "hmat_rankmodel_create", "hmat_rankmodel_grad",
@@ -103,6 +103,8 @@ def lib():
     L.hmat_build.argtypes = [_PD, _I64, ctypes.c_int, ctypes.c_int, ctypes.POINTER(BuildOpts), _P, _P,
                              ctypes.POINTER(_P)]
     L.hmat_multiply.argtypes = [_P, _P, ctypes.POINTER(MultOpts), _P, ctypes.POINTER(_P)]
+    L.hmat_multiply_batched.argtypes = [ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.c_int,
+                                        ctypes.POINTER(MultOpts), _P, ctypes.POINTER(_P)]
     L.hmat_to_dense.argtypes = [_P, _PD, _I64]
     L.hmat_leaf_count.argtypes = [_P, _PI64]
     L.hmat_leaf_info.argtypes = [_P, _I64, ctypes.POINTER(Leaf)]
@@ -124,7 +126,8 @@ def lib():
     L.hmat_destroy.argtypes = [_P]
     L.hmat_destroy.restype = None
     L.hmat_last_error.restype = ctypes.c_char_p
-    for name in ["hmat_points", "hmat_build", "hmat_multiply", "hmat_to_dense", "hmat_leaf_count",
+    for name in ["hmat_points", "hmat_build", "hmat_multiply", "hmat_multiply_batched", "hmat_to_dense",
+                 "hmat_leaf_count",
                  "hmat_leaf_info", "hmat_leaf_get", "hmat_permutation", "hmat_stats", "hmat_sumexpr_counts",
                  "hmat_set_allocator", "hmat_data_bytes", "hmat_data_get", "hmat_rank_features",
                  "hmat_rankmodel_train", "hmat_rankmodel_predict", "hmat_rankmodel_get", "hmat_rankmodel_create",
@@ -255,6 +258,27 @@ def hmat_multiply(A: HMatrix, B: HMatrix, eps: float, mode: int = MODE_F64, rank
     C = HMatrix(h.value)
     C.last_status = st
     return C
+
+
+def hmat_multiply_batched(As, Bs, eps: float, mode: int = MODE_F64, rank_proposal: int = 0, max_rank: int = 0,
+                          max_rounds: int = 0, block_width: int = 0, seed: int = 0, stream=None,
+                          allow_notconv: bool = True, rank_model: "RankModel | None" = None):
+    """Products As[i] Bs[i] in one call; returns the list of outputs."""
+    n = len(As)
+    assert len(Bs) == n
+    opts = MultOpts(eps, mode, rank_proposal, max_rank, max_rounds, block_width, seed,
+                    rank_model.handle if rank_model is not None else None)
+    a = (_P * max(n, 1))(*[x.handle for x in As])
+    b = (_P * max(n, 1))(*[x.handle for x in Bs])
+    c = (_P * max(n, 1))()
+    st = lib().hmat_multiply_batched(a, b, n, ctypes.byref(opts), _stream_ptr(stream), c)
+    _check(st, allow=(HMAT_ENOTCONV,) if allow_notconv else ())
+    out = []
+    for i in range(n):
+        h = HMatrix(c[i])
+        h.last_status = st
+        out.append(h)
+    return out
 
 
 def hmat_sumexpr_counts(A: HMatrix, B: HMatrix):

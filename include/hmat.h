@@ -142,6 +142,7 @@ typedef struct {
   int64_t first_round_cols;      /* columns sampled in the first round, summed over far blocks */
   int64_t done_in_first_round;   /* far blocks whose stop test held in the first round */
   int64_t sample_passes;         /* sum over far blocks of the rounds each one took part in */
+  int64_t groups;                /* subtree groups the product ran in (1: one pass) */
 } hmat_stats_t;
 
 /* Fill xyz (n*dim doubles, row-major, caller-owned) with the seeded points of the given
@@ -171,6 +172,13 @@ hmat_status hmat_build(const double *xyz, int64_t n, int dim, hmat_kernel kernel
  * valid C) when some block hit the rank or round cap. */
 hmat_status hmat_multiply(const hmat_t A, const hmat_t B, const hmat_mult_opts *opts,
                           void *stream, hmat_t *C);
+
+/* Device memory of a product. hmat_multiply plans for the new factors of the low-rank products,
+ * the sampling buffers and the near field; when their estimate exceeds 45 % of the free device
+ * memory (or HMAT_MEMORY_BUDGET_GB gigabytes, if that environment variable is set), the block
+ * tree is cut at a level and its subtrees run in groups that fit: each group builds the terms
+ * created in its subtrees and those created above the cut (rebuilt per group), runs its own
+ * target blocks, and C is assembled from the groups. */
 
 /* count independent products C[i] = A[i] B[i] (each pair on one block tree; the trees of
  * different pairs may differ) with the same options, in one call: the products are planned on

@@ -925,6 +925,98 @@ void Product::run() {
   const std::vector<double> storA = block_storage(t, A->leaves), storB = block_storage(t, B->leaves);
   const size_t smem_cap = 200 * 1024;  // shared memory a launch may ask for per block
 
+  // ---- groups. A product whose device memory (the new factors of the low-rank products, the
+  // sampling buffers, the near field) would exceed a budget runs in groups: the blocks at a cut
+  // level lc are packed, in depth-first order, into groups that fit; a group builds the terms
+  // created in its subtrees and at every block above lc (needed by all groups), and runs its
+  // own targets. Leaves above lc belong to the first group.
+  const size_t nleaf = t.leaf_block.size(), nblk = t.bl.size();
+  std::vector<int> blk_group(nblk, -1), leaf_group(nleaf, 0);
+  int ngroups = 1;
+  {
+    const int p_est = std::max(p, 16);
+    std::vector<double> mem(nblk, 0.0);  // bytes of the terms created at each block and its leaf
+    for (size_t i = 0; i < plan.terms.size(); i++) {
+      const PlanTerm &pt = plan.terms[i];
+      const Block &cb = t.bl[pt.block];
+      const int64_t rows = (pt.type == JOB_FF_L || pt.type == JOB_HF) ? t.cl[cb.tau].size : t.cl[cb.sigma].size;
+      mem[pt.block] += (double)es * rows * pt.rank;
+    }
+    for (size_t l = 0; l < nleaf; l++) {
+      const LeafDev &lf = A->leaves[l];
+      const double mx = std::max(lf.m, lf.n);
+      mem[t.leaf_block[l]] += lf.rank >= 0
+                                  ? 8.0 * (lf.m + lf.n) * max_rank + (double)es * 5.0 * mx * p_est
+                                  : (double)es * 2.0 * lf.m * lf.n;
+    }
+    double total = 0.0;
+    for (double x : mem) total += x;
+    size_t fr = 0, tot = 0;
+    ck(cudaMemGetInfo(&fr, &tot), "memory info");
+    const double budget = 0.45 * (double)fr;
+    const char *ge = std::getenv("HMAT_MEMORY_BUDGET_GB");  // a caller's own limit
+    const double budget_used = (ge && std::atof(ge) > 0.0) ? std::atof(ge) * 1e9 : budget;
+    if (total > budget_used && t.depth >= 2) {
+      std::vector<double> sub(nblk, 0.0);  // subtree bytes (children follow their parent)
+      for (size_t b = nblk; b-- > 0;) {
+        sub[b] += mem[b];
+        if (t.bl[b].parent >= 0) sub[t.bl[b].parent] += sub[b];
+      }
+      for (int lc = 1; lc < t.depth; lc++) {
+        double shared = 0.0, biggest = 0.0;
+        for (size_t b = 0; b < nblk; b++) {
+          if (t.bl[b].level < lc) shared += mem[b];
+          else if (t.bl[b].level == lc) biggest = std::max(biggest, sub[b]);
+        }
+        if (shared + biggest > budget_used && lc + 1 < t.depth) continue;
+        // pack the blocks of level lc in depth-first order
+        ngroups = 0;
+        double cur = 0.0;
+        bool open = false;
+        for (size_t b = 0; b < nblk; b++) {
+          if (t.bl[b].level != lc) continue;
+          if (!open || cur + sub[b] + shared > budget_used) {
+            ngroups++;
+            cur = 0.0;
+            open = true;
+          }
+          cur += sub[b];
+          const int gid = ngroups - 1;
+          // the subtree of b: ids b .. b + size - 1 (depth-first numbering), leaves leaf_lo .. leaf_hi
+          std::vector<int> stack{(int)b};
+          while (!stack.empty()) {
+            const int x = stack.back();
+            stack.pop_back();
+            blk_group[x] = gid;
+            for (int c = 0; c < t.bl[x].nchild; c++) stack.push_back(t.bl[x].child[c]);
+          }
+          for (int32_t l = t.bl[b].leaf_lo; l < t.bl[b].leaf_hi; l++) leaf_group[l] = gid;
+        }
+        if (ngroups == 0) ngroups = 1;
+        break;
+      }
+    }
+    if (tr.on)
+      std::fprintf(stderr, "hmat trace: memory estimate %.2f GB, budget %.2f GB, %d group(s)\n", total / 1e9,
+                   budget_used / 1e9, ngroups);
+  }
+  S.n_terms = (int64_t)plan.terms.size();
+  S.n_hpairs = (int64_t)plan.leaf_pairs.size();
+  C->leaves = base_leaves(t);
+  struct GroupOut {
+    DevBuf data;
+    int64_t elems = 0;
+  };
+  std::vector<GroupOut> gouts(ngroups);
+  auto in_group = [&](int blk, int grp) { return blk_group[blk] < 0 || blk_group[blk] == grp; };
+
+  auto run_group = [&](const int grp) {
+  const double t_g0 = now_ms();
+  if (gate && gate_bytes) {  // the previous group's reservation
+    gate->release(gate_bytes);
+    gate_bytes = 0;
+  }
+
   // jobs of the low-rank products (a2), their storage, and the panels of products with an
   // inadmissible factor: 0 = the H-block is one dense leaf (warp per panel), 1 = inner block with
   // shared-memory staging, 2 = inner block with global staging
@@ -981,6 +1073,7 @@ void Product::run() {
       const auto r = range(c);
       for (size_t i = r.first; i < r.second; i++) {
         const PlanTerm &pt = plan.terms[i];
+        if (!in_group(pt.block, grp)) continue;
         const int64_t rows = rows_of(pt);
         k.elems += rows * pt.rank;
         if (pt.type == JOB_FF_R || pt.type == JOB_FF_L) {
@@ -1023,6 +1116,10 @@ void Product::run() {
       for (size_t i = r.first; i < r.second; i++) {
         const PlanTerm &pt = plan.terms[i];
         TermJob &j = jobs[i];
+        if (!in_group(pt.block, grp)) {
+          j.type = -1;  // skipped by the term-table kernel
+          continue;
+        }
         j.type = pt.type;
         j.a = pt.a;
         j.b = pt.b;
@@ -1043,9 +1140,7 @@ void Product::run() {
     });
   }
   tr.mark("jobs and panels");
-  S.n_terms = (int64_t)nterm;
-  S.n_hpairs = (int64_t)plan.leaf_pairs.size();
-  S.flops_terms = flops_terms;
+  S.flops_terms += flops_terms;
   std::vector<int2> blk_terms(t.bl.size());
   for (size_t b = 0; b < t.bl.size(); b++) blk_terms[b] = make_int2(plan.blk_term_lo[b], plan.blk_term_hi[b]);
 
@@ -1059,7 +1154,7 @@ void Product::run() {
     panels.insert(panels.end(), pk[k].begin(), pk[k].end());
   }
   tr.mark("panel tables");
-  S.ms_plan = now_ms() - t_plan0;
+  S.ms_plan += now_ms() - (grp == 0 ? t_plan0 : t_g0);
 
   cudaEvent_t ev[6];
   for (auto &e : ev) ck(cudaEventCreate(&e), "event");
@@ -1089,7 +1184,9 @@ void Product::run() {
                  (long long)(2 * pdim[NB + 1] * panel_row_stride(PW)));
   if (gate) {  // reserve this product's device memory: terms, sampling buffers, near field
     int64_t est = (int64_t)es * term_elems;
-    for (const LeafDev &l : A->leaves) {
+    for (size_t li = 0; li < A->leaves.size(); li++) {
+      const LeafDev &l = A->leaves[li];
+      if (leaf_group[li] != grp) continue;
       if (l.rank >= 0) {
         const int64_t mx = std::max(l.m, l.n);
         est += (int64_t)sizeof(double) * (l.m + l.n) * 96 + (int64_t)es * (2 * mx * 16 + 3 * mx * 16);
@@ -1153,8 +1250,8 @@ void Product::run() {
     a2mark(k, 1);
     launches++;
   }
-  S.n_ff_jobs = (int64_t)ff_ids.size();
-  S.n_panels = (int64_t)panels.size();
+  S.n_ff_jobs += (int64_t)ff_ids.size();
+  S.n_panels += (int64_t)panels.size();
   check_finite(cprec, d_termbuf.p, term_elems, "low-rank products", s);
   tr.mark("a2 launched");
   if (tr.on) {
@@ -1185,6 +1282,7 @@ void Product::run() {
   std::vector<double> elems_b(t.leaf_block.size(), 0.0);
   int64_t lr_refs = 0;
   for (size_t l = 0; l < t.leaf_block.size(); l++) {
+    if (leaf_group[l] != grp) continue;
     const LeafDev &lc = A->leaves[l];
     const int b = t.leaf_block[l];
     double e = (double)plan.rank_cum[b] * (lc.m + lc.n);
@@ -1194,7 +1292,7 @@ void Product::run() {
     elems_b[l] = e;
     (lc.rank < 0 ? nearv : far).push_back(Tgt{(int)l, e});
   }
-  S.n_lr_refs = lr_refs;
+  S.n_lr_refs += lr_refs;
   // Columns of each far target's first round: p, or a proposed rank + p (at most PROP_MAX),
   // the last p/2 of which form the verification block of the in-round stop test.
   constexpr int PROP_MAX = 16;
@@ -1371,8 +1469,7 @@ void Product::run() {
   // ---- a8 on a second stream, concurrent with the far-field rounds: C's buffer starts with the
   // near leaves (their offsets are known now); they are evaluated into a staging buffer that is
   // copied into C once the far ranks are known.
-  C->leaves = base_leaves(t);
-  int64_t near_elems = 0;
+  int64_t near_elems = 0;  // offsets local to this group's output buffer
   for (const TargetDev &d : ntg) {
     LeafDev &l = C->leaves[d.leaf];
     l.off_u = near_elems;
@@ -1625,14 +1722,15 @@ void Product::run() {
     l.off_v = off + (int64_t)l.m * k;
     off = l.off_v + (int64_t)l.n * k;
   }
-  C->data_elems = off;
-  C->d_data = DevBuf(es * std::max<int64_t>(off, 1), s);
-  C->d_leaves = upload(C->leaves, s);
-  ck(launch_write_far(cprec, aa.tg, aa.state, nf, d_qw.as<double>(), C->d_leaves.as<LeafDev>(), C->d_data.p, s),
+  GroupOut &go = gouts[grp];
+  go.elems = off;
+  go.data = DevBuf(es * std::max<int64_t>(off, 1), s);
+  DevBuf d_gleaves = upload(C->leaves, s);
+  ck(launch_write_far(cprec, aa.tg, aa.state, nf, d_qw.as<double>(), d_gleaves.as<LeafDev>(), go.data.p, s),
      "write far");
   ck(cudaStreamWaitEvent(s, s2.e1, 0), "stream wait");
   if (near_elems > 0)
-    ck(cudaMemcpyAsync(C->d_data.p, d_near.p, es * near_elems, cudaMemcpyDeviceToDevice, s), "near copy");
+    ck(cudaMemcpyAsync(go.data.p, d_near.p, es * near_elems, cudaMemcpyDeviceToDevice, s), "near copy");
   launches += (nf > 0 ? 1 : 0) + (ntg.empty() ? 0 : 1);
   ck(cudaEventRecord(ev[4], s), "event");
   ck(cudaStreamSynchronize(s), "product");
@@ -1643,21 +1741,21 @@ void Product::run() {
     cudaEventElapsedTime(&x, aev[i], aev[i + 1]);
     ms_apply += x;
   }
-  S.ms_apply = ms_apply;
-  S.apply_launches = (int64_t)aev.size() / 2;
-  S.launches = launches;
+  S.ms_apply += ms_apply;
+  S.apply_launches += (int64_t)aev.size() / 2;
+  S.launches += launches;
 
   float ms = 0;
   cudaEventElapsedTime(&ms, ev[0], ev[1]);
-  S.ms_terms = ms;
+  S.ms_terms += ms;
   cudaEventElapsedTime(&ms, ev[1], ev[2]);
-  S.ms_sample = ms;
+  S.ms_sample += ms;
   cudaEventElapsedTime(&ms, ev[2], ev[3]);
-  S.ms_final = ms;
+  S.ms_final += ms;
   cudaEventElapsedTime(&ms, ev[3], ev[4]);
-  S.ms_near = ms;
-  S.rounds = rounds;
-  S.not_converged = notconv;
+  S.ms_near += ms;
+  S.rounds = std::max(S.rounds, rounds);
+  S.not_converged += notconv;
   double fa = 0, ba = 0, fn = 0, bu = 0;
   for (size_t i = 0; i < ftg.size(); i++) {
     const double e = elems_b[ftg[i].leaf];
@@ -1673,10 +1771,37 @@ void Product::run() {
     for (int q = d.pair_lo; q < d.pair_hi; q++) rr += t.cl[t.bl[npairs[q].blkA].sigma].size;
     fn += 2.0 * d.m * d.n * (kk + rr);
   }
-  S.bytes_apply_use = bu;
-  S.flops_apply = fa;
-  S.bytes_apply = ba;
-  S.flops_near = fn;
+  S.bytes_apply_use += bu;
+  S.flops_apply += fa;
+  S.bytes_apply += ba;
+  S.flops_near += fn;
+  };  // run_group
+
+  for (int g = 0; g < ngroups; g++) run_group(g);
+  S.groups = ngroups;
+  // ---- C: one buffer; with several groups, the groups' buffers one after another
+  if (ngroups == 1) {
+    C->d_data = std::move(gouts[0].data);
+    C->data_elems = gouts[0].elems;
+  } else {
+    std::vector<int64_t> base(ngroups + 1, 0);
+    for (int g = 0; g < ngroups; g++) base[g + 1] = base[g] + gouts[g].elems;
+    C->data_elems = base[ngroups];
+    C->d_data = DevBuf(es * std::max<int64_t>(base[ngroups], 1), s);
+    for (int g = 0; g < ngroups; g++)
+      if (gouts[g].elems > 0)
+        ck(cudaMemcpyAsync((char *)C->d_data.p + es * base[g], gouts[g].data.p, es * gouts[g].elems,
+                           cudaMemcpyDeviceToDevice, s),
+           "group copy");
+    for (size_t l = 0; l < C->leaves.size(); l++) {
+      C->leaves[l].off_u += base[leaf_group[l]];
+      C->leaves[l].off_v += base[leaf_group[l]];
+    }
+    ck(cudaStreamSynchronize(s), "group copy");
+    gouts.clear();
+  }
+  C->d_leaves = upload(C->leaves, s);
+  ck(cudaStreamSynchronize(s), "product");
   fill_structure_stats(C.get());
 }
 

@@ -25,6 +25,11 @@ __host__ __device__ constexpr int panel_row_stride(int P) { return P + 1; }
 // thread blocks (and global staging slots) of a launch of panels staged in global memory
 constexpr int PANEL_GSTAGE_SLOTS = 152 * 4;
 
+// Largest dynamic shared memory a block of the current device may opt into. Every kernel's
+// limit is raised to this one value (not to what a launch needs), so that products launched from
+// several host threads at once never lower each other's limits between set-up and launch.
+int max_dynamic_smem();
+
 // learned rank proposal: 12 features -> 64 -> 64 -> 1
 constexpr int RANK_FEATURES = 12;
 constexpr int RANK_PARAMS = 64 * 12 + 64 + 64 * 64 + 64 + 64 + 1;

@@ -1170,7 +1170,21 @@ __global__ void k_convert(const T *src, double *dst, int64_t count) {
 
 template <typename K>
 static cudaError_t set_smem(K kern, size_t bytes) {
-  return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if ((int)bytes > max_dynamic_smem()) return cudaErrorInvalidValue;
+  return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dynamic_smem());
+}
+
+int max_dynamic_smem() {
+  static int cached[64];  // per device; 0 = not queried yet
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 48 * 1024;
+  if (cached[dev] == 0) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess || v <= 0)
+      v = 48 * 1024;
+    cached[dev] = v;
+  }
+  return cached[dev];
 }
 
 cudaError_t launch_kernel_dense(int prec, int kernel, const double *pts, int dim, const LeafDev *leaves,
@@ -1340,6 +1354,7 @@ __global__ void k_make_terms(const TermJob *jobs, int njobs, const BlockDev *blo
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= njobs) return;
   const TermJob jb = jobs[i];
+  if (jb.type < 0) return;  // a term another group of the product builds
   const BlockDev bk = blocks[jb.blk];
   TermDev d;
   d.row0 = bk.row;

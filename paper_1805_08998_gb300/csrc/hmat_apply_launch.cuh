@@ -10,9 +10,7 @@ constexpr int PANEL_P = 16;
 
 template <typename T, int P, bool TRANS, bool GSTAGE, int RB>
 static cudaError_t launch_one(const ApplyArgs &a, size_t smem, cudaStream_t s) {
-  if ((int)smem > max_dynamic_smem()) return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(k_apply<T, P, TRANS, GSTAGE, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       max_dynamic_smem());
+  cudaError_t e = raise_smem_limit(k_apply<T, P, TRANS, GSTAGE, RB>, smem);
   if (e != cudaSuccess) return e;
   const int K = (RB == 0 && !GSTAGE && a.split > 1) ? a.split : 1;
   ApplyArgs b = a;
@@ -53,11 +51,9 @@ static cudaError_t launch_panels_t(const PanelArgs &a, bool leaf_kind, cudaStrea
   constexpr size_t SP = panel_row_stride(P);
   const size_t es = sizeof(T);
   cudaError_t e;
-  if ((int)((size_t)NWARP * (a.smem_in + a.smem_out) * SP * es) > max_dynamic_smem() && leaf_kind)
-    return cudaErrorInvalidValue;
   if (leaf_kind) {
     const size_t smem = (size_t)NWARP * (a.smem_in + a.smem_out) * SP * es;
-    if ((e = cudaFuncSetAttribute(k_panel_leaf<T, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dynamic_smem())))
+    if ((e = raise_smem_limit(k_panel_leaf<T, P>, smem)))
       return e;
     k_panel_leaf<T, P><<<(a.count + NWARP - 1) / NWARP, AT, smem, s>>>(a);
     return cudaGetLastError();
@@ -65,11 +61,11 @@ static cudaError_t launch_panels_t(const PanelArgs &a, bool leaf_kind, cudaStrea
   const size_t cw = (size_t)NWARP * a.smem_cw * SP * es;
   const size_t smem = a.gstage ? cw : (size_t)(a.smem_in + a.smem_out) * SP * es + cw;
   if (a.gstage) {
-    if ((e = cudaFuncSetAttribute(k_panel<T, P, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dynamic_smem())))
+    if ((e = raise_smem_limit(k_panel<T, P, true>, smem)))
       return e;
     k_panel<T, P, true><<<std::min(a.count, PANEL_GSTAGE_SLOTS), AT, smem, s>>>(a);
   } else {
-    if ((e = cudaFuncSetAttribute(k_panel<T, P, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dynamic_smem())))
+    if ((e = raise_smem_limit(k_panel<T, P, false>, smem)))
       return e;
     k_panel<T, P, false><<<a.count, AT, smem, s>>>(a);
   }

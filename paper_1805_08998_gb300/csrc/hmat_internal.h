@@ -30,6 +30,18 @@ constexpr int PANEL_GSTAGE_SLOTS = 152 * 4;
 // several host threads at once never lower each other's limits between set-up and launch.
 int max_dynamic_smem();
 
+// Raise kern's dynamic shared-memory limit to the device maximum less its static shared memory,
+// after checking that `bytes` fits under it (cudaErrorInvalidValue otherwise).
+template <typename K>
+cudaError_t raise_smem_limit(K kern, size_t bytes) {
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, kern);
+  if (e != cudaSuccess) return e;
+  const int limit = max_dynamic_smem() - (int)fa.sharedSizeBytes;
+  if ((long long)bytes > (long long)limit) return cudaErrorInvalidValue;
+  return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, limit);
+}
+
 // learned rank proposal: 12 features -> 64 -> 64 -> 1
 constexpr int RANK_FEATURES = 12;
 constexpr int RANK_PARAMS = 64 * 12 + 64 + 64 * 64 + 64 + 64 + 1;

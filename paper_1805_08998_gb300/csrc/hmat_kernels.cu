@@ -485,18 +485,39 @@ __global__ void __launch_bounds__(NT) k_near_eval(const TargetDev *tg, const int
   for (int i0 = 0; i0 < t.m; i0 += 64)
     for (int j0 = 0; j0 < t.n; j0 += 64) {
       const int mt = min(64, t.m - i0), nt = min(64, t.n - j0);
-      T acc[4][4];
+      // FP32: every term's (and pair's) contribution is summed on its own, then added to the block
+      // with a compensated (Neumaier) sum, so the error does not grow with the number of terms;
+      // FP64: one running sum
+      constexpr bool COMP = sizeof(T) == 4;
+      T acc[4][4], cmp[4][4];
 #pragma unroll
       for (int u = 0; u < 4; u++)
 #pragma unroll
-        for (int v = 0; v < 4; v++) acc[u][v] = T(0);
+        for (int v = 0; v < 4; v++) { acc[u][v] = T(0); cmp[u][v] = T(0); }
+      auto fold = [&](T (&part)[4][4]) {
+#pragma unroll
+        for (int u = 0; u < 4; u++)
+#pragma unroll
+          for (int v = 0; v < 4; v++) {
+            const T x = part[u][v], s0 = acc[u][v], s1 = s0 + x;
+            cmp[u][v] += fabs(s0) >= fabs(x) ? (s0 - s1) + x : (x - s1) + s0;
+            acc[u][v] = s1;
+            part[u][v] = T(0);
+          }
+      };
+      T part[4][4];
+#pragma unroll
+      for (int u = 0; u < 4; u++)
+#pragma unroll
+        for (int v = 0; v < 4; v++) part[u][v] = T(0);
       for (int blk = t.blk; blk >= 0; blk = blocks[blk].parent) {
         const int2 rg = blk_terms[blk];
         for (int ti = rg.x; ti < rg.y; ti++) {
           const TermDev tm = terms[ti];
           const T *L = (const T *)tm.L + (t.row - tm.row0) + i0;
           const T *R = (const T *)tm.R + (t.col - tm.col0) + j0;
-          acc_outer(acc, L, 1, tm.ldL, R, 1, tm.ldR, mt, nt, tm.rank, ls, rs);
+          acc_outer(COMP ? part : acc, L, 1, tm.ldL, R, 1, tm.ldR, mt, nt, tm.rank, ls, rs);
+          if (COMP) fold(part);
         }
       }
       for (int pi = t.pair_lo; pi < t.pair_hi; pi++) {
@@ -506,8 +527,14 @@ __global__ void __launch_bounds__(NT) k_near_eval(const TargetDev *tg, const int
         const LeafDev la = leafA[ba.leaf_lo], lb = leafB[bb.leaf_lo];
         const T *DA = dataA + la.off_u + i0;                  // m x rho, ld m
         const T *DB = dataB + lb.off_u + (int64_t)j0 * lb.m;  // rho x n, ld rho; R(j, q) = DB[q + j*rho]
-        acc_outer(acc, DA, 1, la.m, DB, lb.m, 1, mt, nt, la.n, ls, rs);
+        acc_outer(COMP ? part : acc, DA, 1, la.m, DB, lb.m, 1, mt, nt, la.n, ls, rs);
+        if (COMP) fold(part);
       }
+      if (COMP)
+#pragma unroll
+        for (int u = 0; u < 4; u++)
+#pragma unroll
+          for (int v = 0; v < 4; v++) acc[u][v] += cmp[u][v];
 #pragma unroll
       for (int u = 0; u < 4; u++)
 #pragma unroll
@@ -1170,8 +1197,7 @@ __global__ void k_convert(const T *src, double *dst, int64_t count) {
 
 template <typename K>
 static cudaError_t set_smem(K kern, size_t bytes) {
-  if ((int)bytes > max_dynamic_smem()) return cudaErrorInvalidValue;
-  return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dynamic_smem());
+  return raise_smem_limit(kern, bytes);
 }
 
 int max_dynamic_smem() {

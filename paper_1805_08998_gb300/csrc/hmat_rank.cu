@@ -152,7 +152,7 @@ __global__ void __launch_bounds__(RT) k_mlp(const __half *w16, const float *x, c
 }
 
 static cudaError_t set_mlp_smem() {
-  return cudaFuncSetAttribute(k_mlp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(MlpSmem));
+  return raise_smem_limit(k_mlp, sizeof(MlpSmem));
 }
 
 // Adam on the FP32 masters, then the FP16 copies used by the forward pass

@@ -67,12 +67,11 @@ def sampled_far_near(T, n_far, n_near, seed, max_mn=512 * 512):
     sizes = np.array([T.leaf_ranges(l) for l in range(T.nleaf)])
     mn = sizes[:, 1] * sizes[:, 3]
     far = []
-    levels = sorted(set(lv[kind == 1].tolist()))
-    per = max(1, n_far // max(1, len(levels)))
-    for level in levels:
-        cand = np.nonzero((lv == level) & (kind == 1) & (mn <= max_mn))[0]
-        if len(cand):
-            far += rng.choice(cand, size=min(per, len(cand)), replace=False).tolist()
+    cands = [np.nonzero((lv == level) & (kind == 1) & (mn <= max_mn))[0] for level in sorted(set(lv.tolist()))]
+    cands = [c for c in cands if len(c)]
+    per = max(1, n_far // max(1, len(cands)))
+    for cand in cands:
+        far += rng.choice(cand, size=min(per, len(cand)), replace=False).tolist()
     near_c = np.nonzero(kind != 1)[0]
     near = rng.choice(near_c, size=min(n_near, len(near_c)), replace=False).tolist()
     return far, near

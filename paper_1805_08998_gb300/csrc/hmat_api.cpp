@@ -936,12 +936,16 @@ void Product::run() {
   {
     const int p_est = std::max(p, 16);
     std::vector<double> mem(nblk, 0.0);  // bytes of the terms created at each block and its leaf
-    for (size_t i = 0; i < plan.terms.size(); i++) {
-      const PlanTerm &pt = plan.terms[i];
-      const Block &cb = t.bl[pt.block];
-      const int64_t rows = (pt.type == JOB_FF_L || pt.type == JOB_HF) ? t.cl[cb.tau].size : t.cl[cb.sigma].size;
-      mem[pt.block] += (double)es * rows * pt.rank;
-    }
+    parallel_for(64, [&](size_t c) {      // blocks split in 64 ranges; each block's terms are contiguous
+      for (size_t b = nblk * c / 64; b < nblk * (c + 1) / 64; b++)
+        for (int32_t i = plan.blk_term_lo[b]; i < plan.blk_term_hi[b]; i++) {
+          const PlanTerm &pt = plan.terms[i];
+          const Block &cb = t.bl[b];
+          const int64_t rows =
+              (pt.type == JOB_FF_L || pt.type == JOB_HF) ? t.cl[cb.tau].size : t.cl[cb.sigma].size;
+          mem[b] += (double)es * rows * pt.rank;
+        }
+    });
     for (size_t l = 0; l < nleaf; l++) {
       const LeafDev &lf = A->leaves[l];
       const double mx = std::max(lf.m, lf.n);

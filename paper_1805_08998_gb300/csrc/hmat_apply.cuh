@@ -590,44 +590,54 @@ __global__ void __launch_bounds__(AT) k_panel_leaf(PanelArgs a) {
 }
 
 // one block per panel of an inner H-block; leaves split over warps, shared-memory atomics
+// one panel of an inner H-block; leaves split over warps, shared-memory atomics
+template <typename T, int P, bool GSTAGE>
+__device__ __forceinline__ void panel_body(const PanelArgs &a, int pi, unsigned char *smem_raw) {
+  const PanelJob pj = panel_job(a, a.panels[a.first + pi], P);
+  const BlockDev bk = a.blocks[pj.blk];
+  const bool trans = pj.trans;
+  const int inlen = trans ? bk.m : bk.n, outlen = trans ? bk.n : bk.m;
+  constexpr int SP = panel_row_stride(P);
+  T *Xs, *Os, *cwall;
+  if (GSTAGE) {
+    Xs = (T *)a.stage_base + (int64_t)blockIdx.x * a.stage_stride;
+    Os = Xs + (int64_t)inlen * SP;
+    cwall = (T *)smem_raw;
+  } else {
+    Xs = (T *)smem_raw;
+    Os = Xs + a.smem_in * SP;
+    cwall = Os + a.smem_out * SP;
+  }
+  const int warp = threadIdx.x >> 5;
+  T *cw = cwall + warp * a.smem_cw * SP;
+  const T *src = (const T *)(trans ? a.dataA : a.dataB);
+  panel_stage<T, P, SP>(Xs, pj, inlen, src, threadIdx.x, AT);
+  for (int o = threadIdx.x; o < outlen * SP; o += AT) Os[o] = T(0);
+  __syncthreads();
+  const LeafDev *leaves = trans ? a.leafB : a.leafA;
+  const T *data = (const T *)(trans ? a.dataB : a.dataA);
+  for (int l = bk.leaf_lo + warp; l < bk.leaf_hi; l += NWARP)
+    warp_leaf<T, P, SP>(leaves[l], data, trans, bk.row, bk.col, Xs, Os, cw);
+  __syncthreads();
+  T *out = (T *)a.terms;
+  for (int o = threadIdx.x; o < outlen * pj.ncol; o += AT) {
+    const int c = o / outlen, i = o - c * outlen;
+    out[pj.dst + (int64_t)c * pj.dst_ld + i] = Os[i * SP + c];
+  }
+}
+
+// shared-memory staging: one block per panel; global staging: a bounded number of blocks loops
+// over the panels, block b using staging slot b
 template <typename T, int P, bool GSTAGE>
 __global__ void __launch_bounds__(AT) k_panel(PanelArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  // with global staging, a bounded number of blocks loops over the panels, block b using
-  // staging slot b; otherwise one block per panel
-  for (int pi = blockIdx.x; pi < a.count; pi += gridDim.x) {
-    const PanelJob pj = panel_job(a, a.panels[a.first + pi], P);
-    const BlockDev bk = a.blocks[pj.blk];
-    const bool trans = pj.trans;
-    const int inlen = trans ? bk.m : bk.n, outlen = trans ? bk.n : bk.m;
-    constexpr int SP = panel_row_stride(P);
-    T *Xs, *Os, *cwall;
-    if (GSTAGE) {
-      Xs = (T *)a.stage_base + (int64_t)blockIdx.x * a.stage_stride;
-      Os = Xs + (int64_t)inlen * SP;
-      cwall = (T *)smem_raw;
-    } else {
-      Xs = (T *)smem_raw;
-      Os = Xs + a.smem_in * SP;
-      cwall = Os + a.smem_out * SP;
+  if (!GSTAGE) {
+    panel_body<T, P, false>(a, blockIdx.x, smem_raw);
+  } else {
+    for (int pi = blockIdx.x; pi < a.count; pi += gridDim.x) {
+      panel_body<T, P, true>(a, pi, smem_raw);
+      __syncthreads();  // the staging slot and shared memory are reused by the next panel
     }
-    const int warp = threadIdx.x >> 5;
-    T *cw = cwall + warp * a.smem_cw * SP;
-    const T *src = (const T *)(trans ? a.dataA : a.dataB);
-    panel_stage<T, P, SP>(Xs, pj, inlen, src, threadIdx.x, AT);
-    for (int o = threadIdx.x; o < outlen * SP; o += AT) Os[o] = T(0);
-    __syncthreads();
-    const LeafDev *leaves = trans ? a.leafB : a.leafA;
-    const T *data = (const T *)(trans ? a.dataB : a.dataA);
-    for (int l = bk.leaf_lo + warp; l < bk.leaf_hi; l += NWARP)
-      warp_leaf<T, P, SP>(leaves[l], data, trans, bk.row, bk.col, Xs, Os, cw);
-    __syncthreads();
-    T *out = (T *)a.terms;
-    for (int o = threadIdx.x; o < outlen * pj.ncol; o += AT) {
-      const int c = o / outlen, i = o - c * outlen;
-      out[pj.dst + (int64_t)c * pj.dst_ld + i] = Os[i * SP + c];
-    }
-    __syncthreads();  // the staging slot and shared memory are reused by the next panel
   }
 }
 

@@ -95,6 +95,11 @@ typedef struct {
   int block_width;     /* columns added per adaptive round (0 = default 8; <= 16) */
   uint64_t seed;       /* seed of the Gaussian test matrices (counter-based, splitmix64) */
   hmat_rankmodel_t rank_model;  /* used when rank_proposal == 1 (NULL otherwise) */
+  int fixed_rank;      /* 0: eps-rank truncation (the default). k in 1..16: every far block of C
+                          gets rank at most k by Algorithm 9 (k Gaussian samples, power_iters
+                          subspace iterations, no eps test; eps then only sets the threshold
+                          below which sample directions are dropped as zero) */
+  int power_iters;     /* subspace iterations q of the fixed-rank mode (0..4; -1 = default 1) */
 } hmat_mult_opts;
 
 typedef struct {

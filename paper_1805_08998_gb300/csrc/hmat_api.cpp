@@ -894,6 +894,10 @@ void Product::run() {
   if (max_rank < p) max_rank = p;
   const int max_rounds = o->max_rounds > 0 ? o->max_rounds : max_rank / p + 1;
   if (o->rank_proposal < 0 || o->rank_proposal > 2) fail(HMAT_EINVAL, "rank_proposal must be 0, 1 or 2");
+  const int fixed_k = o->fixed_rank;
+  if (fixed_k < 0 || fixed_k > 16) fail(HMAT_EINVAL, "fixed_rank must be 0 (eps-rank) or 1..16");
+  const int power_q = o->power_iters < 0 ? 1 : o->power_iters;
+  if (power_q > 4) fail(HMAT_EINVAL, "power_iters must be -1 (default) or 0..4");
   if (o->rank_proposal == 1 && !o->rank_model) fail(HMAT_EINVAL, "rank_proposal 1 needs a rank_model");
 
   // factors in compute precision
@@ -1331,7 +1335,9 @@ void Product::run() {
     }
     tr.mark("rank proposal");
   }
-  int pmax = p;
+  if (fixed_k > 0)  // Algorithm 9: k samples for every far block
+    for (const Tgt &g : far) p0v[g.leaf] = fixed_k;
+  int pmax = fixed_k > 0 ? fixed_k : p;
   for (const Tgt &g : far) pmax = std::max(pmax, p0v[g.leaf]);
   // Size classes of the application kernel: 0 = panels staged in global memory (targets too
   // large for shared memory); class c >= 1 = targets of at most 32 << (c - 1) rows, columns
@@ -1526,9 +1532,13 @@ void Product::run() {
   }
   DevBuf d_st = upload(st0, s);
   // a4 runs one warp per target of at most 64 rows, one block per larger target
-  std::vector<int32_t> orth_w, orth_b;
-  for (int i = 0; i < nf; i++) (ftg[i].m <= 64 ? orth_w : orth_b).push_back(i);
+  std::vector<int32_t> orth_w, orth_b, orth_wn, orth_bn;
+  for (int i = 0; i < nf; i++) {
+    (ftg[i].m <= 64 ? orth_w : orth_b).push_back(i);
+    (ftg[i].n <= 64 ? orth_wn : orth_bn).push_back(i);  // the column side (fixed-rank mode)
+  }
   DevBuf d_orth_w = upload(orth_w, s), d_orth_b = upload(orth_b, s);
+  DevBuf d_orth_wn = upload(orth_wn, s), d_orth_bn = upload(orth_bn, s);
   DevBuf d_cnt(sizeof(int32_t), s);
   ApplyArgs aa{};
   aa.tg = d_ftg.as<TargetDev>();
@@ -1547,6 +1557,7 @@ void Product::run() {
   aa.p = p;
   const double eps = o->eps;
   const double eps_stop = 0.5 * eps;
+  const double eps_trunc = fixed_k > 0 ? 0.0 : eps;  // fixed rank: keep every sampled direction
   int rounds = 0;
   // events around every application pass (S and S^T), read after the stream synchronises
   std::vector<cudaEvent_t> aev;
@@ -1606,7 +1617,39 @@ void Product::run() {
     }
     ck(cudaEventRecord(e1, s), "event");
   };
-  for (int round = 0; round < max_rounds && nf > 0; round++) {
+  if (fixed_k > 0 && nf > 0) {
+    // Algorithm 9: L = S Omega, orthonormalised; q times U = S^T L, orthonormalised, and
+    // L = S U, orthonormalised; finally W = S^T L. Every orthonormalisation is of the new block
+    // alone.
+    rounds = 1;
+    aa.p = pmax;
+    aa.round = 0;
+    ck(launch_gaussian(cprec, aa.tg, aa.state, nf, pmax, o->seed, 0, d_x.p, s), "gaussian");
+    timed_apply(false);
+    auto orth_side = [&](int side) {
+      const std::vector<int32_t> &w = side ? orth_wn : orth_w, &bl = side ? orth_bn : orth_b;
+      const DevBuf &dw = side ? d_orth_wn : d_orth_w, &db = side ? d_orth_bn : d_orth_b;
+      ck(launch_orth(cprec, aa.tg, dw.as<int32_t>(), (int)w.size(), db.as<int32_t>(), (int)bl.size(), aa.state, pmax,
+                     eps, d_y.p, d_qw.as<double>(), d_x.p, 0, s, side, 1),
+         "orth");
+      launches += (w.empty() ? 0 : 1) + (bl.empty() ? 0 : 1);
+    };
+    orth_side(0);
+    for (int it = 0; it < power_q; it++) {
+      timed_apply(true);
+      orth_side(1);
+      timed_apply(false);
+      orth_side(0);
+    }
+    timed_apply(true);
+    ck(cudaMemsetAsync(d_cnt.p, 0, sizeof(int32_t), s), "memset");
+    ck(launch_absorb_w(cprec, aa.tg, aa.state, nf, p, eps_stop, d_y.p, d_qw.as<double>(), 0, 1, d_cnt.as<int32_t>(),
+                       s, 1),
+       "fixed rank");
+    launches += 2;
+    ck(cudaStreamSynchronize(s), "fixed rank");
+  }
+  for (int round = 0; round < max_rounds && nf > 0 && fixed_k == 0; round++) {
     rounds++;
     const int pr = round == 0 ? pmax : p;  // widest panel this round (round 0: each target's p0)
     aa.p = pr;
@@ -1681,11 +1724,12 @@ void Product::run() {
         cudaEventCreate(&e);
       }
     if (tr.on) cudaEventRecord(fe[0], s);
-    ck(launch_final(aa.tg, aa.state, d_ids_small.as<int32_t>(), (int)ids_small.size(), true, eps, d_qw.as<double>(),
-                    s),
+    ck(launch_final(aa.tg, aa.state, d_ids_small.as<int32_t>(), (int)ids_small.size(), true, eps_trunc,
+                    d_qw.as<double>(), s),
        "final truncation (warp)");
     if (tr.on) cudaEventRecord(fe[1], s);
-    ck(launch_final(aa.tg, aa.state, d_ids_big.as<int32_t>(), (int)ids_big.size(), false, eps, d_qw.as<double>(), s),
+    ck(launch_final(aa.tg, aa.state, d_ids_big.as<int32_t>(), (int)ids_big.size(), false, eps_trunc,
+                    d_qw.as<double>(), s),
        "final truncation (block)");
     if (tr.on) {
       cudaEventRecord(fe[2], s);

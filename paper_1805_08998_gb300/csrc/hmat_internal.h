@@ -195,13 +195,14 @@ int apply_panel_width(int p);
 // Gaussian test matrices Omega (n x p per active target, into x_base; round 0: p0 columns)
 cudaError_t launch_gaussian(int prec, const TargetDev *tg, const TargetState *st, int ntg, int p, uint64_t seed,
                             int round, void *x_base, cudaStream_t s);
-// a4 for targets ids_warp (at most 64 rows: one warp each) and ids_block (one block each)
+// a4 for targets ids_warp (at most 64 rows: one warp each) and ids_block (one block each); side 1
+// orthonormalises the column-side block (n rows, basis in the W buffer), fresh ignores the basis
 cudaError_t launch_orth(int prec, const TargetDev *tg, const int32_t *ids_warp, int n_warp, const int32_t *ids_block,
                         int n_block, TargetState *st, int p, double eps, void *y_base, double *qw, void *x_base,
-                        int round, cudaStream_t s);
+                        int round, cudaStream_t s, int side = 0, int fresh = 0);
 cudaError_t launch_absorb_w(int prec, const TargetDev *tg, TargetState *st, int ntg, int p,
                             double eps_stop, void *y_base, double *qw, int round, int max_rounds,
-                            int32_t *active_count, cudaStream_t s);
+                            int32_t *active_count, cudaStream_t s, int fixed = 0);
 // core truncation of the targets listed in ids: one warp per target (bases of at most 32
 // columns) or one block per target (up to 96 columns)
 cudaError_t launch_final(const TargetDev *tg, TargetState *st, const int32_t *ids, int nids, bool warp_kernel,

@@ -589,7 +589,8 @@ __global__ void __launch_bounds__(NT) k_gaussian(const TargetDev *tg, const Targ
 // columns r .. r+p-1. Also writes Q_new in T precision into x_base (input of the S^T pass).
 template <typename T>
 __global__ void __launch_bounds__(NT) k_orth(const TargetDev *tg, const int32_t *ids, TargetState *st, int p,
-                                             double eps, const T *y_base, double *qw, T *x_base, int round) {
+                                             double eps, const T *y_base, double *qw, T *x_base, int round,
+                                             int side, int fresh) {
   __shared__ double G[PMAX];
   constexpr int QCH = 64;  // basis columns projected per chunk
   __shared__ double Cm[QCH * PMAX];
@@ -597,10 +598,10 @@ __global__ void __launch_bounds__(NT) k_orth(const TargetDev *tg, const int32_t 
   const int b = ids[blockIdx.x];
   if (st[b].active == 0) return;
   const TargetDev t = tg[b];
-  const int64_t m = t.m;
-  const int r = st[b].r;
+  const int64_t m = side ? t.n : t.m;  // side 1: the column side (basis in the W buffer)
+  const int r = fresh ? 0 : st[b].r;   // fresh: orthonormalise the block on its own
   if (round == 0) p = t.p0;
-  double *Q = qw + t.q_off;
+  double *Q = qw + (side ? t.w_off : t.q_off);
   double *Y = Q + (int64_t)r * m;  // m x p workspace inside Q
   const T *Ys = y_base + t.y_off;
   double part = 0.0;
@@ -697,15 +698,15 @@ constexpr int OW = 16;  // max columns per round
 template <typename T>
 __global__ void __launch_bounds__(NT) k_orth_warp(const TargetDev *tg, const int32_t *ids, int nids,
                                                   TargetState *st, int p_round, double eps, const T *y_base,
-                                                  double *qw, T *x_base, int round) {
+                                                  double *qw, T *x_base, int round, int side, int fresh) {
   const int wi = blockIdx.x * (NT / 32) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (wi >= nids) return;  // whole warps only
   const int b = ids[wi];
   if (st[b].active == 0) return;
   const TargetDev t = tg[b];
-  const int m = t.m, r = st[b].r;
+  const int m = side ? t.n : t.m, r = fresh ? 0 : st[b].r;
   const int p = round == 0 ? t.p0 : p_round;
-  double *Q = qw + t.q_off;
+  double *Q = qw + (side ? t.w_off : t.q_off);
   const T *Ys = y_base + t.y_off;
   const int i0 = lane, i1 = lane + 32;
   const bool v0 = i0 < m, v1 = i1 < m;
@@ -793,7 +794,7 @@ __global__ void __launch_bounds__(NT) k_orth_warp(const TargetDev *tg, const int
 template <typename T>
 __global__ void __launch_bounds__(NT) k_absorb_w(const TargetDev *tg, TargetState *st, int p, double eps_stop,
                                                  const T *y_base, double *qw, int round, int max_rounds,
-                                                 int32_t *active_count) {
+                                                 int32_t *active_count, int fixed) {
   __shared__ double red[NT / 32];
   const int b = blockIdx.x;
   const int was_active = st[b].active;
@@ -829,6 +830,7 @@ __global__ void __launch_bounds__(NT) k_absorb_w(const TargetDev *tg, TargetStat
     if (nw2 <= eps_stop * eps_stop * old) act = 0;
     if (v > 0 && last2 <= eps_stop * eps_stop * (nw2 - last2)) act = 0;
     if (rn >= min(t.m, t.n)) act = 0;                       // range exhausted: exact
+    if (fixed) act = 0;                                      // fixed rank: one pass, no test
     if (rn + p > t.rmax || round + 1 >= max_rounds) {
       if (act) st[b].rank = -2;                              // marks "hit a cap"
       act = 0;
@@ -1437,37 +1439,37 @@ cudaError_t launch_gaussian(int prec, const TargetDev *tg, const TargetState *st
 
 cudaError_t launch_orth(int prec, const TargetDev *tg, const int32_t *ids_warp, int n_warp, const int32_t *ids_block,
                         int n_block, TargetState *st, int p, double eps, void *y_base, double *qw, void *x_base,
-                        int round, cudaStream_t s) {
+                        int round, cudaStream_t s, int side, int fresh) {
   if (p > OW) return cudaErrorInvalidValue;
   const int gw = (n_warp + NT / 32 - 1) / (NT / 32);
   if (prec == 64) {
     if (n_warp)
       k_orth_warp<double><<<gw, NT, 0, s>>>(tg, ids_warp, n_warp, st, p, eps, (const double *)y_base, qw,
-                                            (double *)x_base, round);
+                                            (double *)x_base, round, side, fresh);
     if (n_block)
       k_orth<double><<<n_block, NT, 0, s>>>(tg, ids_block, st, p, eps, (const double *)y_base, qw, (double *)x_base,
-                                            round);
+                                            round, side, fresh);
   } else {
     if (n_warp)
       k_orth_warp<float><<<gw, NT, 0, s>>>(tg, ids_warp, n_warp, st, p, eps, (const float *)y_base, qw,
-                                           (float *)x_base, round);
+                                           (float *)x_base, round, side, fresh);
     if (n_block)
       k_orth<float><<<n_block, NT, 0, s>>>(tg, ids_block, st, p, eps, (const float *)y_base, qw, (float *)x_base,
-                                           round);
+                                           round, side, fresh);
   }
   return cudaGetLastError();
 }
 
 cudaError_t launch_absorb_w(int prec, const TargetDev *tg, TargetState *st, int ntg, int p, double eps_stop,
                             void *y_base, double *qw, int round, int max_rounds, int32_t *active_count,
-                            cudaStream_t s) {
+                            cudaStream_t s, int fixed) {
   if (ntg == 0) return cudaSuccess;
   if (prec == 64)
     k_absorb_w<double><<<ntg, NT, 0, s>>>(tg, st, p, eps_stop, (const double *)y_base, qw, round, max_rounds,
-                                          active_count);
+                                          active_count, fixed);
   else
     k_absorb_w<float><<<ntg, NT, 0, s>>>(tg, st, p, eps_stop, (const float *)y_base, qw, round, max_rounds,
-                                         active_count);
+                                         active_count, fixed);
   return cudaGetLastError();
 }
 

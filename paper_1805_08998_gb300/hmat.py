@@ -50,7 +50,8 @@ class BuildOpts(ctypes.Structure):
 class MultOpts(ctypes.Structure):
     _fields_ = [("eps", ctypes.c_double), ("mode", ctypes.c_int), ("rank_proposal", ctypes.c_int),
                 ("max_rank", ctypes.c_int), ("max_rounds", ctypes.c_int), ("block_width", ctypes.c_int),
-                ("seed", ctypes.c_uint64), ("rank_model", ctypes.c_void_p)]
+                ("seed", ctypes.c_uint64), ("rank_model", ctypes.c_void_p), ("fixed_rank", ctypes.c_int),
+                ("power_iters", ctypes.c_int)]
 
 
 class TrainOpts(ctypes.Structure):
@@ -249,9 +250,10 @@ def hmat_build(xyz: np.ndarray, kernel: int, leaf_size: int = 32, eta: float = 1
 
 def hmat_multiply(A: HMatrix, B: HMatrix, eps: float, mode: int = MODE_F64, rank_proposal: int = 0,
                   max_rank: int = 0, max_rounds: int = 0, block_width: int = 0, seed: int = 0,
-                  stream=None, allow_notconv: bool = True, rank_model: "RankModel | None" = None) -> HMatrix:
+                  stream=None, allow_notconv: bool = True, rank_model: "RankModel | None" = None,
+                  fixed_rank: int = 0, power_iters: int = -1) -> HMatrix:
     opts = MultOpts(eps, mode, rank_proposal, max_rank, max_rounds, block_width, seed,
-                    rank_model.handle if rank_model is not None else None)
+                    rank_model.handle if rank_model is not None else None, fixed_rank, power_iters)
     h = _P()
     st = lib().hmat_multiply(A.handle, B.handle, ctypes.byref(opts), _stream_ptr(stream), ctypes.byref(h))
     _check(st, allow=(HMAT_ENOTCONV,) if allow_notconv else ())
@@ -267,7 +269,7 @@ def hmat_multiply_batched(As, Bs, eps: float, mode: int = MODE_F64, rank_proposa
     n = len(As)
     assert len(Bs) == n
     opts = MultOpts(eps, mode, rank_proposal, max_rank, max_rounds, block_width, seed,
-                    rank_model.handle if rank_model is not None else None)
+                    rank_model.handle if rank_model is not None else None, 0, -1)
     a = (_P * max(n, 1))(*[x.handle for x in As])
     b = (_P * max(n, 1))(*[x.handle for x in Bs])
     c = (_P * max(n, 1))()

@@ -185,6 +185,17 @@ hmat_status hmat_multiply(const hmat_t A, const hmat_t B, const hmat_mult_opts *
  * created in its subtrees and those created above the cut (rebuilt per group), runs its own
  * target blocks, and C is assembled from the groups. */
 
+/* y = H x for ncols right-hand sides (Alg. 2 over all leaves, on the device, in FP64): x and y are
+ * n x ncols column-major host arrays in the ORIGINAL point order (caller-owned). Synchronises. */
+hmat_status hmat_matvec(const hmat_t H, const double *x, double *y, int64_t ncols, void *stream);
+
+/* Estimate of the relative Frobenius error ||C - A B||_F / ||A B||_F of a product (the paper's
+ * check of its products, Sec. 6: `iters` subspace iterations on a block of `size` Gaussian
+ * vectors (splitmix64 stream of `seed`), the operator applied as C v - A (B v)). The same
+ * iteration on C estimates the denominator. A, B, C on one block tree. Synchronises. */
+hmat_status hmat_product_error(const hmat_t A, const hmat_t B, const hmat_t C, int iters, int size, uint64_t seed,
+                               double *rel_err);
+
 /* count independent products C[i] = A[i] B[i] (each pair on one block tree; the trees of
  * different pairs may differ) with the same options, in one call: the products are planned on
  * host threads and run on up to 8 streams of their own, largest first, so that the GPU works on

@@ -569,6 +569,188 @@ hmat_status hmat_to_dense(const hmat_t h, double *out, int64_t ld) {
   });
 }
 
+}  // extern "C"
+
+namespace {
+
+// FP64 products of an H-matrix with panels of panel_width() columns (row-major, tree order)
+struct DevMatvec {
+  const hmat_s *h;
+  DevBuf wide;
+  const double *data = nullptr;
+  int cw_rows = 1;
+  DevMatvec(const hmat_s *hh, cudaStream_t s) : h(hh) {
+    if (h->prec == 64) {
+      data = h->d_data.as<double>();
+    } else {
+      wide = DevBuf(sizeof(double) * std::max<int64_t>(h->data_elems, 1), s);
+      ck(launch_convert(h->prec, h->d_data.p, wide.as<double>(), h->data_elems, s), "widen");
+      data = wide.as<double>();
+    }
+    for (const LeafDev &l : h->leaves) cw_rows = std::max(cw_rows, (int)l.rank);
+  }
+  // Y = H X
+  void apply(const double *X, double *Y, cudaStream_t s) const {
+    const int64_t n = h->tree->n;
+    ck(cudaMemsetAsync(Y, 0, sizeof(double) * n * panel_row_stride(panel_width()), s), "memset");
+    ck(launch_hmatvec(h->d_leaves.as<LeafDev>(), (int)h->leaves.size(), data, X, Y, cw_rows, s), "matvec");
+  }
+};
+
+// columns c0 .. c0+P-1 of the column-major n x ncols x (original order) as a padded row-major panel
+// in tree order, and back
+void to_panel(const Tree &t, const double *x, int64_t ncols, int64_t c0, std::vector<double> &pan) {
+  const int P = panel_width(), SP = panel_row_stride(P);
+  pan.assign((size_t)t.n * SP, 0.0);
+  for (int c = 0; c < P && c0 + c < ncols; c++)
+    for (int64_t i = 0; i < t.n; i++) pan[i * SP + c] = x[t.perm[i] + (c0 + c) * t.n];
+}
+void from_panel(const Tree &t, const std::vector<double> &pan, int64_t ncols, int64_t c0, double *y) {
+  const int P = panel_width(), SP = panel_row_stride(P);
+  for (int c = 0; c < P && c0 + c < ncols; c++)
+    for (int64_t i = 0; i < t.n; i++) y[t.perm[i] + (c0 + c) * t.n] = pan[i * SP + c];
+}
+
+// Orthonormal columns of the n x s column-major X (tree order) by Cholesky QR applied twice; a
+// zero block stays zero. Returns false when X is zero.
+bool orthonormalise(std::vector<double> &X, int64_t n, int s) {
+  for (int pass = 0; pass < 2; pass++) {
+    std::vector<double> G((size_t)s * s, 0.0);
+    std::mutex mu;
+    parallel_for(64, [&](size_t ch) {
+      std::vector<double> g((size_t)s * s, 0.0);
+      for (int64_t i = n * (int64_t)ch / 64; i < n * (int64_t)(ch + 1) / 64; i++)
+        for (int a = 0; a < s; a++) {
+          const double xa = X[i + (int64_t)a * n];
+          if (xa == 0.0) continue;
+          for (int b = a; b < s; b++) g[a + (size_t)b * s] += xa * X[i + (int64_t)b * n];
+        }
+      std::lock_guard<std::mutex> lk(mu);
+      for (size_t k = 0; k < g.size(); k++) G[k] += g[k];
+    });
+    double tr = 0.0;
+    for (int a = 0; a < s; a++) tr += G[a + (size_t)a * s];
+    if (!(tr > 0.0)) return false;
+    for (int a = 0; a < s; a++) G[a + (size_t)a * s] += 1e-15 * tr;  // keeps a rank-deficient block finite
+    // G = R^T R (upper R stored in G's upper triangle)
+    for (int j = 0; j < s; j++) {
+      for (int k = 0; k < j; k++) {
+        double v = G[k + (size_t)j * s];
+        for (int l = 0; l < k; l++) v -= G[l + (size_t)k * s] * G[l + (size_t)j * s];
+        G[k + (size_t)j * s] = v / G[k + (size_t)k * s];
+      }
+      double d = G[j + (size_t)j * s];
+      for (int l = 0; l < j; l++) d -= G[l + (size_t)j * s] * G[l + (size_t)j * s];
+      G[j + (size_t)j * s] = std::sqrt(std::max(d, 1e-300));
+    }
+    // X <- X R^{-1}, row by row
+    parallel_for(64, [&](size_t ch) {
+      std::vector<double> row(s);
+      for (int64_t i = n * (int64_t)ch / 64; i < n * (int64_t)(ch + 1) / 64; i++) {
+        for (int j = 0; j < s; j++) {
+          double v = X[i + (int64_t)j * n];
+          for (int k = 0; k < j; k++) v -= row[k] * G[k + (size_t)j * s];
+          row[j] = v / G[j + (size_t)j * s];
+        }
+        for (int j = 0; j < s; j++) X[i + (int64_t)j * n] = row[j];
+      }
+    });
+  }
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+hmat_status hmat_matvec(const hmat_t H, const double *x, double *y, int64_t ncols, void *stream) {
+  return guard([&] {
+    if (!H || !x || !y || ncols < 0) fail(HMAT_EINVAL, "NULL argument or negative ncols");
+    const Tree &t = *H->tree;
+    cudaStream_t s = (cudaStream_t)stream;
+    DevMatvec mv(H, s);
+    const int P = panel_width();
+    const size_t pan_elems = (size_t)t.n * panel_row_stride(P);
+    DevBuf dx(sizeof(double) * std::max<size_t>(pan_elems, 1), s), dy(sizeof(double) * std::max<size_t>(pan_elems, 1), s);
+    std::vector<double> pan;
+    for (int64_t c0 = 0; c0 < ncols; c0 += P) {
+      to_panel(t, x, ncols, c0, pan);
+      ck(cudaMemcpyAsync(dx.p, pan.data(), sizeof(double) * pan_elems, cudaMemcpyHostToDevice, s), "upload");
+      mv.apply(dx.as<double>(), dy.as<double>(), s);
+      ck(cudaMemcpyAsync(pan.data(), dy.p, sizeof(double) * pan_elems, cudaMemcpyDeviceToHost, s), "download");
+      ck(cudaStreamSynchronize(s), "matvec");
+      from_panel(t, pan, ncols, c0, y);
+    }
+  });
+}
+
+hmat_status hmat_product_error(const hmat_t A, const hmat_t B, const hmat_t C, int iters, int size, uint64_t seed,
+                               double *rel_err) {
+  return guard([&] {
+    if (!A || !B || !C || !rel_err || iters < 0 || size < 1) fail(HMAT_EINVAL, "NULL argument or bad iters/size");
+    if (A->tree != C->tree && !same_points(*A->tree, C->tree->orig.data(), C->tree->n, C->tree->dim))
+      fail(HMAT_EMISMATCH, "A and C are not on one block tree");
+    if (A->tree != B->tree && !same_points(*A->tree, B->tree->orig.data(), B->tree->n, B->tree->dim))
+      fail(HMAT_EMISMATCH, "A and B are not on one block tree");
+    const Tree &t = *A->tree;
+    const int64_t n = t.n;
+    cudaStream_t s = C->stream;
+    DevMatvec ma(A, s), mb(B, s), mc(C, s);
+    const int P = panel_width(), SP = panel_row_stride(P);
+    const size_t pan_elems = (size_t)n * SP;
+    DevBuf dx(sizeof(double) * pan_elems, s), d1(sizeof(double) * pan_elems, s), d2(sizeof(double) * pan_elems, s);
+    std::vector<double> pan(pan_elems), out1(pan_elems), out2(pan_elems);
+    // Y = E X with E = C - A B (which = 0), or Y = C X (which = 1); X, Y n x size, tree order
+    auto apply = [&](int which, const std::vector<double> &X, std::vector<double> &Y) {
+      Y.assign((size_t)n * size, 0.0);
+      for (int c0 = 0; c0 < size; c0 += P) {
+        std::fill(pan.begin(), pan.end(), 0.0);
+        for (int c = 0; c < P && c0 + c < size; c++)
+          for (int64_t i = 0; i < n; i++) pan[i * SP + c] = X[i + (int64_t)(c0 + c) * n];
+        ck(cudaMemcpyAsync(dx.p, pan.data(), sizeof(double) * pan_elems, cudaMemcpyHostToDevice, s), "upload");
+        mc.apply(dx.as<double>(), d1.as<double>(), s);
+        if (which == 0) {
+          mb.apply(dx.as<double>(), d2.as<double>(), s);
+          ma.apply(d2.as<double>(), dx.as<double>(), s);
+          ck(cudaMemcpyAsync(out2.data(), dx.p, sizeof(double) * pan_elems, cudaMemcpyDeviceToHost, s), "download");
+        }
+        ck(cudaMemcpyAsync(out1.data(), d1.p, sizeof(double) * pan_elems, cudaMemcpyDeviceToHost, s), "download");
+        ck(cudaStreamSynchronize(s), "matvec");
+        for (int c = 0; c < P && c0 + c < size; c++)
+          for (int64_t i = 0; i < n; i++)
+            Y[i + (int64_t)(c0 + c) * n] = out1[i * SP + c] - (which == 0 ? out2[i * SP + c] : 0.0);
+      }
+    };
+    // block power iteration on a Gaussian start (splitmix64 + Box-Muller), then the Frobenius
+    // norm of the operator on the final orthonormal block
+    auto estimate = [&](int which) {
+      std::vector<double> X((size_t)n * size), Y;
+      for (size_t k = 0; k < X.size(); k++) {
+        auto mix = [](uint64_t z) {
+          z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+          z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+          return z ^ (z >> 31);
+        };
+        const double u1 = ((mix(seed + (2 * k + 1) * 0x9E3779B97F4A7C15ull) >> 11) + 1) * 0x1.0p-53;
+        const double u2 = (mix(seed + (2 * k + 2) * 0x9E3779B97F4A7C15ull) >> 11) * 0x1.0p-53;
+        X[k] = std::sqrt(-2.0 * std::log(u1)) * std::cos(6.283185307179586 * u2);
+      }
+      if (!orthonormalise(X, n, size)) return 0.0;
+      for (int it = 0; it < iters; it++) {
+        apply(which, X, Y);
+        if (!orthonormalise(Y, n, size)) return 0.0;
+        X.swap(Y);
+      }
+      apply(which, X, Y);
+      double f = 0.0;
+      for (double v : Y) f += v * v;
+      return std::sqrt(f);
+    };
+    const double e = estimate(0), c = estimate(1);
+    *rel_err = c > 0.0 ? e / c : e;
+  });
+}
+
 hmat_status hmat_permutation(const hmat_t h, int64_t *perm) {
   return guard([&] {
     if (!h || !perm) fail(HMAT_EINVAL, "NULL argument");

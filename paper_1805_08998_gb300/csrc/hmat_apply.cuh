@@ -641,5 +641,20 @@ __global__ void __launch_bounds__(AT) k_panel(PanelArgs a) {
   }
 }
 
+// ---------------------------------------------------------------------------------------
+// H-matrix times a panel (Alg. 2, all leaves at once): Y += H X for row-major P-column panels X,
+// Y of the whole index set (tree order). Warps take leaves; outputs are added atomically.
+// ---------------------------------------------------------------------------------------
+template <typename T, int P>
+__global__ void __launch_bounds__(AT) k_hmatvec(const LeafDev *leaves, int nleaf, const T *data, const T *X, T *Y,
+                                                int cw_rows) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int SP = panel_row_stride(P);
+  const int warp = threadIdx.x >> 5;
+  T *cw = (T *)smem_raw + warp * cw_rows * SP;
+  for (int l = blockIdx.x * NWARP + warp; l < nleaf; l += gridDim.x * NWARP)
+    warp_leaf<T, P, SP>(leaves[l], data, false, 0, 0, X, Y, cw);
+}
+
 }  // namespace apply_detail
 }  // namespace hm

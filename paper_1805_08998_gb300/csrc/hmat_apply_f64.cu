@@ -11,4 +11,9 @@ cudaError_t launch_panels_f64(const PanelArgs &a, bool leaf_kind, cudaStream_t s
   return apply_detail::launch_panels_t<double>(a, leaf_kind, s);
 }
 
+cudaError_t launch_hmatvec(const LeafDev *leaves, int nleaf, const double *data, const double *X, double *Y,
+                           int cw_rows, cudaStream_t s) {
+  return apply_detail::launch_hmatvec_t<double>(leaves, nleaf, data, X, Y, cw_rows, s);
+}
+
 }  // namespace hm

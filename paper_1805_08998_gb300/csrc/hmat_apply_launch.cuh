@@ -72,5 +72,17 @@ static cudaError_t launch_panels_t(const PanelArgs &a, bool leaf_kind, cudaStrea
   return cudaGetLastError();
 }
 
+template <typename T>
+static cudaError_t launch_hmatvec_t(const LeafDev *leaves, int nleaf, const T *data, const T *X, T *Y, int cw_rows,
+                                    cudaStream_t s) {
+  constexpr int P = PANEL_P;
+  const size_t smem = (size_t)NWARP * cw_rows * panel_row_stride(P) * sizeof(T);
+  cudaError_t e = raise_smem_limit(k_hmatvec<T, P>, smem);
+  if (e != cudaSuccess) return e;
+  const int grid = std::max(1, std::min((nleaf + NWARP - 1) / NWARP, 152 * 16));
+  k_hmatvec<T, P><<<grid, AT, smem, s>>>(leaves, nleaf, data, X, Y, cw_rows);
+  return cudaGetLastError();
+}
+
 }  // namespace apply_detail
 }  // namespace hm

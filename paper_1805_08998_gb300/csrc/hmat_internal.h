@@ -191,6 +191,10 @@ size_t apply_smem_bytes(int prec, int P, const ApplyArgs &a);
 int apply_rows_per_lane(int dmax);
 cudaError_t launch_panels(int prec, const PanelArgs &a, bool leaf_kind, cudaStream_t s);
 int panel_width();
+// Y += H X (FP64) for row-major panels of panel_width() columns and row stride
+// panel_row_stride(panel_width()) over the whole index set in tree order; cw_rows >= max rank
+cudaError_t launch_hmatvec(const LeafDev *leaves, int nleaf, const double *data, const double *X, double *Y,
+                           int cw_rows, cudaStream_t s);
 int apply_panel_width(int p);
 // Gaussian test matrices Omega (n x p per active target, into x_base; round 0: p0 columns)
 cudaError_t launch_gaussian(int prec, const TargetDev *tg, const TargetState *st, int ntg, int p, uint64_t seed,

@@ -28,7 +28,7 @@ EXPORTS = ["hmat_points", "hmat_build", "hmat_multiply", "hmat_multiply_batched"
            "hmat_leaf_get", "hmat_permutation", "hmat_stats", "hmat_sumexpr_counts", "hmat_destroy",
            "hmat_data_bytes", "hmat_data_get", "hmat_rank_features", "hmat_rankmodel_train",
            "hmat_rankmodel_predict", "hmat_rankmodel_get", "hmat_rankmodel_create", "hmat_rankmodel_grad",
-           "hmat_rankmodel_grad_noalloc", "hmat_rankmodel_destroy", "hmat_last_error", "hmat_set_allocator"]
+           "hmat_rankmodel_grad_noalloc", "hmat_rankmodel_destroy", "hmat_matvec", "hmat_product_error", "hmat_last_error", "hmat_set_allocator"]
 
 RANK_FEATURES = 12
 RANK_PARAMS = 5057
@@ -122,6 +122,8 @@ def lib():
     L.hmat_rankmodel_create.argtypes = [_PF, _PF, _PF, ctypes.POINTER(_P)]
     L.hmat_rankmodel_grad.argtypes = [_P, _PF, _PF, _I64, _PF, _PF]
     L.hmat_rankmodel_grad_noalloc.argtypes = [_P, _PF, _PF, _I64, _PF, _PF, _P]
+    L.hmat_matvec.argtypes = [_P, _PD, _PD, _I64, _P]
+    L.hmat_product_error.argtypes = [_P, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_uint64, _PD]
     L.hmat_rankmodel_destroy.argtypes = [_P]
     L.hmat_rankmodel_destroy.restype = None
     L.hmat_destroy.argtypes = [_P]
@@ -132,7 +134,7 @@ def lib():
                  "hmat_leaf_info", "hmat_leaf_get", "hmat_permutation", "hmat_stats", "hmat_sumexpr_counts",
                  "hmat_set_allocator", "hmat_data_bytes", "hmat_data_get", "hmat_rank_features",
                  "hmat_rankmodel_train", "hmat_rankmodel_predict", "hmat_rankmodel_get", "hmat_rankmodel_create",
-                 "hmat_rankmodel_grad", "hmat_rankmodel_grad_noalloc"]:
+                 "hmat_rankmodel_grad", "hmat_rankmodel_grad_noalloc", "hmat_matvec", "hmat_product_error"]:
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -281,6 +283,22 @@ def hmat_multiply_batched(As, Bs, eps: float, mode: int = MODE_F64, rank_proposa
         h.last_status = st
         out.append(h)
     return out
+
+
+def hmat_matvec(Hm: HMatrix, x, stream=None) -> np.ndarray:
+    """y = H x for x of shape (n,) or (n, ncols), original point order."""
+    x = np.asarray(x, np.float64)
+    vec = x.ndim == 1
+    X = np.asfortranarray(x.reshape(x.shape[0], -1))
+    Y = np.zeros_like(X, order="F")
+    _check(lib().hmat_matvec(Hm.handle, X.ctypes.data_as(_PD), Y.ctypes.data_as(_PD), X.shape[1], _stream_ptr(stream)))
+    return Y[:, 0].copy() if vec else np.ascontiguousarray(Y)
+
+
+def hmat_product_error(A: HMatrix, B: HMatrix, C: HMatrix, iters: int = 10, size: int = 100, seed: int = 0) -> float:
+    out = ctypes.c_double()
+    _check(lib().hmat_product_error(A.handle, B.handle, C.handle, iters, size, seed, ctypes.byref(out)))
+    return out.value
 
 
 def hmat_sumexpr_counts(A: HMatrix, B: HMatrix):

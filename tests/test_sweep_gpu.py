@@ -60,3 +60,7 @@ def test_sweep_n524288(H, oracle, sweep, eps, mode, near_rtol):
         e = np.linalg.norm(D - blocks[l]) / np.linalg.norm(blocks[l])
         assert e <= near_rtol, (l, e)
     print(f"eps {eps} {mode}: {len(far)} far blocks, worst relative error {worst:.3g}")
+    if eps == 1e-6:  # the paper's global check (Sec. 6): subspace iterations on C v - A (A v)
+        est = H.hmat_product_error(A, A, C, iters=10, size=100, seed=3)
+        print(f"eps {eps}: estimated global relative error {est:.3g}")
+        assert est <= 1.5 * eps

@@ -73,6 +73,16 @@ typedef enum {
                           orthogonalisation (Gram, Cholesky) and the core eigen-solve in FP64 */
 } hmat_mode;
 
+/* Compressor of the far blocks' sum-expressions (Sec. 4). Both end with the same truncation of
+ * the compressed block to its eps-rank (Algorithm 5); they differ in how the low-rank factors are
+ * found from products of the sum-expression with vectors. */
+typedef enum {
+  HMAT_COMP_RANDOMIZED = 0,  /* blocked adaptive randomized range finder (Algorithm 8) */
+  HMAT_COMP_ACA = 1          /* adaptive cross approximation (Algorithm 6): one row e_i^T S and
+                                one column S e_j per step, partial pivoting, stopped when
+                                two consecutive crosses meet eq. (truncaca) at eps/4 */
+} hmat_compressor;
+
 typedef struct {
   int leaf_size;       /* n_min: leaf clusters hold at most this many points (>= 1) */
   double eta;          /* admissibility: max(diam tau, diam sigma) <= eta * dist(tau, sigma) */
@@ -100,6 +110,8 @@ typedef struct {
                           subspace iterations, no eps test; eps then only sets the threshold
                           below which sample directions are dropped as zero) */
   int power_iters;     /* subspace iterations q of the fixed-rank mode (0..4; -1 = default 1) */
+  int compressor;      /* hmat_compressor (HMAT_COMP_ACA needs fixed_rank = 0 and rank_proposal = 0;
+                          its rank is capped at max_rank - 1 per block, HMAT_ENOTCONV beyond) */
 } hmat_mult_opts;
 
 typedef struct {
@@ -174,7 +186,10 @@ hmat_status hmat_build(const double *xyz, int64_t n, int dim, hmat_kernel kernel
  * block evaluated exactly. A and B must share one block tree (EMISMATCH otherwise) and one
  * factor precision. C lives on the same tree with A's factor precision. Synchronises
  * `stream` at the end of every adaptive round and at the end. Returns HMAT_ENOTCONV (with a
- * valid C) when some block hit the rank or round cap. */
+ * valid C) when some block hit the rank or round cap. With opts->compressor = HMAT_COMP_ACA the
+ * far blocks are compressed by adaptive cross approximation (Algorithm 6; a round is then one
+ * cross, a row and a column of every unfinished block) and the cross factors L U are truncated
+ * to the eps-rank by a QR of L and the same FP64 eigen-truncation. */
 hmat_status hmat_multiply(const hmat_t A, const hmat_t B, const hmat_mult_opts *opts,
                           void *stream, hmat_t *C);
 

@@ -1081,6 +1081,11 @@ void Product::run() {
   const int power_q = o->power_iters < 0 ? 1 : o->power_iters;
   if (power_q > 4) fail(HMAT_EINVAL, "power_iters must be -1 (default) or 0..4");
   if (o->rank_proposal == 1 && !o->rank_model) fail(HMAT_EINVAL, "rank_proposal 1 needs a rank_model");
+  if (o->compressor != HMAT_COMP_RANDOMIZED && o->compressor != HMAT_COMP_ACA)
+    fail(HMAT_EINVAL, "compressor must be 0 (randomized) or 1 (cross approximation)");
+  const bool aca = o->compressor == HMAT_COMP_ACA;
+  if (aca && (fixed_k != 0 || o->rank_proposal != 0))
+    fail(HMAT_EINVAL, "the cross approximation compressor takes neither fixed_rank nor rank_proposal");
 
   // factors in compute precision
   DevBuf convA, convB;
@@ -1831,7 +1836,36 @@ void Product::run() {
     launches += 2;
     ck(cudaStreamSynchronize(s), "fixed rank");
   }
-  for (int round = 0; round < max_rounds && nf > 0 && fixed_k == 0; round++) {
+  if (aca && nf > 0) {
+    // Algorithm 6 on every far target at once: each step is one S^T pass (the pivot rows
+    // e_i^T S) and one S pass (the pivot columns S e_j), single columns, with the pivoting, the
+    // residual updates and eq. (truncaca) on the device between them. A step adds one cross or
+    // marks one zero row used, so the steps are bounded by the basis capacity plus the rows.
+    aa.p = 1;
+    aa.round = 1;  // every target takes aa.p columns
+    ck(launch_aca_start(cprec, aa.tg, aa.state, nf, d_qw.as<double>(), d_x.p, s), "cross approximation");
+    launches++;
+    int max_steps = 0;
+    for (const TargetDev &d : ftg) max_steps = std::max(max_steps, d.rmax + d.m);
+    for (int step = 0; step < max_steps; step++) {
+      rounds++;
+      timed_apply(true);
+      ck(launch_aca_row(cprec, aa.tg, aa.state, nf, d_y.p, d_qw.as<double>(), d_x.p, s), "cross approximation row");
+      timed_apply(false);
+      ck(cudaMemsetAsync(d_cnt.p, 0, sizeof(int32_t), s), "memset");
+      ck(launch_aca_col(cprec, aa.tg, aa.state, nf, d_y.p, d_qw.as<double>(), d_x.p, 0.25 * eps,
+                        d_cnt.as<int32_t>(), s),
+         "cross approximation column");
+      launches += 2;
+      int32_t act = 0;
+      ck(cudaMemcpyAsync(&act, d_cnt.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s), "count");
+      ck(cudaStreamSynchronize(s), "cross approximation step");
+      if (act == 0) break;
+    }
+    ck(launch_aca_qr(aa.tg, aa.state, nf, d_qw.as<double>(), s), "cross approximation QR");
+    launches++;
+  }
+  for (int round = 0; round < max_rounds && nf > 0 && fixed_k == 0 && !aca; round++) {
     rounds++;
     const int pr = round == 0 ? pmax : p;  // widest panel this round (round 0: each target's p0)
     aa.p = pr;
@@ -1991,9 +2025,9 @@ void Product::run() {
     const double e = elems_b[ftg[i].leaf];
     const int cols = st[i].r;  // columns that went through both passes
     fa += 2.0 * e * 2.0 * cols;
-    ba += e * 2.0 * ((cols + p - 1) / p) * es;
+    ba += e * 2.0 * (aca ? cols : (cols + p - 1) / p) * es;
     const double launches_b = 2.0 * std::max(1, st[i].nfwd);
-    bu += launches_b * (e + (double)(ftg[i].m + ftg[i].n) * p) * es;
+    bu += launches_b * (e + (double)(ftg[i].m + ftg[i].n) * (aca ? 1 : p)) * es;
   }
   for (const TargetDev &d : ntg) {
     const double kk = (double)plan.rank_cum[d.blk];

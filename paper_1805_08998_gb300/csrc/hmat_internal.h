@@ -134,6 +134,8 @@ struct TargetState {
   int32_t rank;         // final rank
   int32_t nfwd;         // rounds in which the target was sampled
   int32_t sweeps;       // Jacobi sweeps of the core truncation
+  int32_t piv_i, piv_j; // cross approximation: pivot row and column of the current step
+  int32_t hits, pad;    // cross approximation: consecutive crosses that met eq. (truncaca)
   double nrm2;          // ||W||_F^2 over all columns so far (= ||Q Q^T S||_F^2)
   double est2;          // ||Y||_F^2 / p of the first round (scale for dropping)
   double tail2;         // discarded energy in the final truncation
@@ -207,6 +209,23 @@ cudaError_t launch_orth(int prec, const TargetDev *tg, const int32_t *ids_warp, 
 cudaError_t launch_absorb_w(int prec, const TargetDev *tg, TargetState *st, int ntg, int p,
                             double eps_stop, void *y_base, double *qw, int round, int max_rounds,
                             int32_t *active_count, cudaStream_t s, int fixed = 0);
+// Adaptive cross approximation of the sum-expressions (Algorithm 6), one step per call pair.
+// L_k (m x k) lives in the Q buffer, U_k^T (n x k, the rows u_r as columns) in the W buffer;
+// column rmax - 1 of the Q buffer holds the used-row flags. launch_aca_start sets the first
+// pivot row's unit vector e_i as the input of the S^T pass; launch_aca_row takes e_i^T S from
+// y_base, forms u_r, picks the column pivot and sets e_j as the input of the S pass;
+// launch_aca_col takes S e_j, forms l_r, applies eq. (truncaca) at eps_stop (the target stops
+// after two consecutive crosses meet it), picks the next row pivot and counts the targets still
+// active into *active_count.
+cudaError_t launch_aca_start(int prec, const TargetDev *tg, TargetState *st, int ntg, double *qw, void *x_base,
+                             cudaStream_t s);
+cudaError_t launch_aca_row(int prec, const TargetDev *tg, TargetState *st, int ntg, const void *y_base, double *qw,
+                           void *x_base, cudaStream_t s);
+cudaError_t launch_aca_col(int prec, const TargetDev *tg, TargetState *st, int ntg, const void *y_base, double *qw,
+                           void *x_base, double eps_stop, int32_t *active_count, cudaStream_t s);
+// L = Q R (classical Gram-Schmidt twice, FP64) in place in the Q buffer and W <- U R^T in place,
+// so that L U^T = Q W^T with orthonormal Q: the input of the core truncation
+cudaError_t launch_aca_qr(const TargetDev *tg, const TargetState *st, int ntg, double *qw, cudaStream_t s);
 // core truncation of the targets listed in ids: one warp per target (bases of at most 32
 // columns) or one block per target (up to 96 columns)
 cudaError_t launch_final(const TargetDev *tg, TargetState *st, const int32_t *ids, int nids, bool warp_kernel,

@@ -1160,6 +1160,253 @@ __global__ void __launch_bounds__(WF_WARPS * 32) k_final_warp(const TargetDev *t
   }
 }
 
+// ---------------------------------------------------------------------------------------
+// a3-a5 by cross approximation: Algorithm 6 on the sum-expression, one row and one column per
+// step, every unfinished far target of the product in the same launches
+// ---------------------------------------------------------------------------------------
+
+// used-row flags of target t (m doubles, 0 or 1) in the last column of its Q buffer
+__device__ __forceinline__ double *aca_used(double *qw, const TargetDev &t) {
+  return qw + t.q_off + (int64_t)(t.rmax - 1) * t.m;
+}
+
+// first pivot row i_1 = 0: clear the flags and set e_0 (m entries) as the S^T pass input
+template <typename T>
+__global__ void __launch_bounds__(NT) k_aca_start(const TargetDev *tg, TargetState *st, double *qw, T *x_base) {
+  const int b = blockIdx.x;
+  const TargetDev t = tg[b];
+  double *used = aca_used(qw, t);
+  T *X = x_base + t.x_off;
+  for (int64_t i = threadIdx.x; i < t.m; i += NT) {
+    used[i] = 0.0;
+    X[i] = T(i == 0 ? 1 : 0);
+  }
+  if (threadIdx.x == 0) {
+    st[b].piv_i = 0;
+    st[b].piv_j = -1;
+    st[b].p_new = 0;
+    st[b].hits = 0;
+  }
+}
+
+// Row step: u_hat = e_i^T S - sum_{s<r} [l_s]_i u_s (Algorithm 6), column pivot j_r = argmax
+// |u_hat| (first on ties), u_r = u_hat / [u_hat]_{j_r}, stored as column r of the W buffer; the
+// S pass then gets e_{j_r}. A residual row that is exactly zero is marked used and the first
+// unused row becomes the pivot row of the next step (no column this step: p_new = 0); a target
+// with every row used stops.
+template <typename T>
+__global__ void __launch_bounds__(NT) k_aca_row(const TargetDev *tg, TargetState *st, const T *y_base, double *qw,
+                                                T *x_base) {
+  __shared__ double li[JMAX];
+  __shared__ double redv[NT / 32];
+  __shared__ int64_t redi[NT / 32];
+  const int b = blockIdx.x;
+  if (st[b].active == 0) return;
+  const TargetDev t = tg[b];
+  const int r = st[b].r;
+  const int64_t m = t.m, n = t.n, i = st[b].piv_i;
+  const double *L = qw + t.q_off;
+  double *U = qw + t.w_off;
+  double *u = U + (int64_t)r * n;
+  const T *row = y_base + t.y_off;
+  for (int s = threadIdx.x; s < r; s += NT) li[s] = L[i + (int64_t)s * m];
+  __syncthreads();
+  double bv = -1.0;
+  int64_t bj = -1;
+  for (int64_t j = threadIdx.x; j < n; j += NT) {
+    double v = (double)row[j];
+    for (int s = 0; s < r; s++) v -= li[s] * U[j + (int64_t)s * n];
+    u[j] = v;
+    const double a = fabs(v);
+    if (a > bv) { bv = a; bj = j; }
+  }
+  const int64_t jr = block_argmax(bv, bj, redv, redi);  // ends with a barrier: u is complete
+  const double piv = jr >= 0 ? u[jr] : 0.0;
+  __syncthreads();  // every thread holds piv before u[jr] is overwritten
+  T *X = x_base + t.x_off;
+  if (piv != 0.0) {
+    const double inv = 1.0 / piv;
+    for (int64_t j = threadIdx.x; j < n; j += NT) {
+      u[j] = (j == jr) ? 1.0 : u[j] * inv;
+      X[j] = T(j == jr ? 1 : 0);
+    }
+    if (threadIdx.x == 0) {
+      st[b].piv_j = (int)jr;
+      st[b].p_new = 1;
+    }
+    return;
+  }
+  // zero residual row
+  double *used = aca_used(qw, t);
+  if (threadIdx.x == 0) used[i] = 1.0;
+  __syncthreads();
+  int64_t cand = m;  // this thread's first unused row (m: none); the block takes the smallest
+  for (int64_t k = threadIdx.x; k < m; k += NT)
+    if (used[k] == 0.0) { cand = k; break; }
+  const int64_t next = block_argmax(-(double)cand, cand < m ? cand : -1, redv, redi);
+  if (threadIdx.x == 0) {
+    st[b].p_new = 0;
+    if (next < 0) st[b].active = 0;
+    else st[b].piv_i = (int)next;
+  }
+}
+
+// Column step: l_r = S e_{j_r} - sum_{s<r} [u_s]_{j_r} l_s (Algorithm 6), stored as column r of
+// the Q buffer; ||L_{r+1} U_{r+1}||_F^2 updated from the cross terms; stop once two consecutive
+// crosses have met eq. (truncaca), ||l_r|| ||u_r|| <= eps_stop ||L_r U_r||_F (keeping the new
+// crosses), or when r + 1 reaches min(m, n) (exact) or the basis capacity (cap: rank marked -2);
+// otherwise the next pivot row is argmax |l_r| over the unused rows and its unit vector the next
+// S^T input.
+template <typename T>
+__global__ void __launch_bounds__(NT) k_aca_col(const TargetDev *tg, TargetState *st, const T *y_base, double *qw,
+                                                T *x_base, double eps_stop, int32_t *active_count) {
+  __shared__ double uj[JMAX], dl[JMAX], du[JMAX];
+  __shared__ double red[NT / 32];
+  __shared__ double redv[NT / 32];
+  __shared__ int64_t redi[NT / 32];
+  const int b = blockIdx.x;
+  if (st[b].active == 0) return;
+  const TargetDev t = tg[b];
+  const int64_t m = t.m, n = t.n;
+  T *X = x_base + t.x_off;
+  if (st[b].p_new == 0) {  // the row step found a zero row: next row step at the new pivot
+    const int64_t i = st[b].piv_i;
+    for (int64_t k = threadIdx.x; k < m; k += NT) X[k] = T(k == i ? 1 : 0);
+    if (threadIdx.x == 0) atomicAdd(active_count, 1);
+    return;
+  }
+  const int r = st[b].r;
+  const int64_t i = st[b].piv_i, j = st[b].piv_j;
+  double *L = qw + t.q_off;
+  const double *U = qw + t.w_off;
+  double *l = L + (int64_t)r * m;
+  const double *u = U + (int64_t)r * n;
+  const T *col = y_base + t.y_off;
+  for (int s = threadIdx.x; s < r; s += NT) uj[s] = U[j + (int64_t)s * n];
+  __syncthreads();
+  double pl = 0.0;
+  for (int64_t k = threadIdx.x; k < m; k += NT) {
+    double v = (double)col[k];
+    for (int s = 0; s < r; s++) v -= uj[s] * L[k + (int64_t)s * m];
+    l[k] = v;
+    pl += v * v;
+  }
+  double pu = 0.0;
+  for (int64_t k = threadIdx.x; k < n; k += NT) pu += u[k] * u[k];
+  const double nl2 = block_sum(pl, red), nu2 = block_sum(pu, red);  // barriers: l is complete
+  // cross terms (l_s . l_r)(u_s . u_r), s < r: one warp per s
+  {
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int s = w; s < r; s += NT / 32) {
+      const double *ls = L + (int64_t)s * m, *us = U + (int64_t)s * n;
+      double a = 0.0, c = 0.0;
+      for (int64_t k = lane; k < m; k += 32) a += ls[k] * l[k];
+      for (int64_t k = lane; k < n; k += 32) c += us[k] * u[k];
+      a = warp_sum(a);
+      c = warp_sum(c);
+      if (lane == 0) { dl[s] = a; du[s] = c; }
+    }
+  }
+  double *used = aca_used(qw, t);
+  if (threadIdx.x == 0) used[i] = 1.0;
+  __syncthreads();
+  __shared__ int act_s;
+  if (threadIdx.x == 0) {
+    double cross = 0.0;
+    for (int s = 0; s < r; s++) cross += dl[s] * du[s];
+    const double prev = st[b].nrm2;
+    st[b].nrm2 = prev + 2.0 * cross + nl2 * nu2;
+    const int rn = r + 1;
+    st[b].r = rn;
+    st[b].nfwd += 1;
+    int act = 1;
+    const int hits = nl2 * nu2 <= eps_stop * eps_stop * prev ? st[b].hits + 1 : 0;  // eq. (truncaca)
+    st[b].hits = hits;
+    if (hits >= 2) act = 0;
+    if (rn >= min(t.m, t.n)) act = 0;                        // exact
+    if (act && rn >= t.rmax - 1) {                           // capacity (last column: flags)
+      st[b].rank = -2;
+      act = 0;
+    }
+    act_s = act;
+  }
+  __syncthreads();
+  if (!act_s) {
+    if (threadIdx.x == 0) st[b].active = 0;
+    return;
+  }
+  double bv = -1.0;
+  int64_t bi = -1;
+  for (int64_t k = threadIdx.x; k < m; k += NT)
+    if (used[k] == 0.0) {
+      const double a = fabs(l[k]);
+      if (a > bv) { bv = a; bi = k; }
+    }
+  const int64_t next = block_argmax(bv, bi, redv, redi);
+  if (next < 0) {
+    if (threadIdx.x == 0) st[b].active = 0;
+    return;
+  }
+  for (int64_t k = threadIdx.x; k < m; k += NT) X[k] = T(k == next ? 1 : 0);
+  if (threadIdx.x == 0) {
+    st[b].piv_i = (int)next;
+    atomicAdd(active_count, 1);
+  }
+}
+
+// L = Q R by classical Gram-Schmidt applied twice (FP64, in place in the Q buffer, R in shared
+// memory), then W <- U R^T in place: row i of W, column c, is sum_{s >= c} U[i][s] R[c][s], so
+// ascending c only overwrites entries no later column reads. A column with an exactly zero
+// remainder gets q = 0 and a zero row of R (it adds nothing to L U^T).
+__global__ void __launch_bounds__(NT) k_aca_qr(const TargetDev *tg, const TargetState *st, double *qw) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double *R = (double *)smem_raw;  // r x r, R[c][s] at c + s * r
+  __shared__ double g[JMAX];
+  __shared__ double red[NT / 32];
+  const int b = blockIdx.x;
+  const int r = st[b].r;
+  if (r == 0) return;
+  const TargetDev t = tg[b];
+  const int64_t m = t.m, n = t.n;
+  double *L = qw + t.q_off, *W = qw + t.w_off;
+  for (int o = threadIdx.x; o < r * r; o += NT) R[o] = 0.0;
+  __syncthreads();
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int c = 0; c < r; c++) {
+    double *v = L + (int64_t)c * m;
+    for (int pass = 0; pass < 2 && c > 0; pass++) {
+      for (int s = w; s < c; s += NT / 32) {
+        const double *q = L + (int64_t)s * m;
+        double a = 0.0;
+        for (int64_t k = lane; k < m; k += 32) a += q[k] * v[k];
+        a = warp_sum(a);
+        if (lane == 0) g[s] = a;
+      }
+      __syncthreads();
+      for (int64_t k = threadIdx.x; k < m; k += NT) {
+        double a = 0.0;
+        for (int s = 0; s < c; s++) a += L[k + (int64_t)s * m] * g[s];
+        v[k] -= a;
+      }
+      for (int s = threadIdx.x; s < c; s += NT) R[s + c * r] += g[s];
+      __syncthreads();
+    }
+    double part = 0.0;
+    for (int64_t k = threadIdx.x; k < m; k += NT) part += v[k] * v[k];
+    const double nrm = sqrt(block_sum(part, red));
+    const double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
+    for (int64_t k = threadIdx.x; k < m; k += NT) v[k] *= inv;
+    if (threadIdx.x == 0) R[c + c * r] = nrm;
+    __syncthreads();
+  }
+  for (int64_t k = threadIdx.x; k < n; k += NT)
+    for (int c = 0; c < r; c++) {
+      double a = 0.0;
+      for (int s = c; s < r; s++) a += W[k + (int64_t)s * n] * R[c + s * r];
+      W[k + (int64_t)c * n] = a;
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(NT) k_write_far(const TargetDev *tg, const TargetState *st, const double *qw,
                                                   const LeafDev *leafC, T *dataC) {
@@ -1470,6 +1717,42 @@ cudaError_t launch_absorb_w(int prec, const TargetDev *tg, TargetState *st, int 
   else
     k_absorb_w<float><<<ntg, NT, 0, s>>>(tg, st, p, eps_stop, (const float *)y_base, qw, round, max_rounds,
                                          active_count, fixed);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_aca_start(int prec, const TargetDev *tg, TargetState *st, int ntg, double *qw, void *x_base,
+                             cudaStream_t s) {
+  if (ntg == 0) return cudaSuccess;
+  if (prec == 64) k_aca_start<double><<<ntg, NT, 0, s>>>(tg, st, qw, (double *)x_base);
+  else k_aca_start<float><<<ntg, NT, 0, s>>>(tg, st, qw, (float *)x_base);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_aca_row(int prec, const TargetDev *tg, TargetState *st, int ntg, const void *y_base, double *qw,
+                           void *x_base, cudaStream_t s) {
+  if (ntg == 0) return cudaSuccess;
+  if (prec == 64) k_aca_row<double><<<ntg, NT, 0, s>>>(tg, st, (const double *)y_base, qw, (double *)x_base);
+  else k_aca_row<float><<<ntg, NT, 0, s>>>(tg, st, (const float *)y_base, qw, (float *)x_base);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_aca_col(int prec, const TargetDev *tg, TargetState *st, int ntg, const void *y_base, double *qw,
+                           void *x_base, double eps_stop, int32_t *active_count, cudaStream_t s) {
+  if (ntg == 0) return cudaSuccess;
+  if (prec == 64)
+    k_aca_col<double><<<ntg, NT, 0, s>>>(tg, st, (const double *)y_base, qw, (double *)x_base, eps_stop,
+                                         active_count);
+  else
+    k_aca_col<float><<<ntg, NT, 0, s>>>(tg, st, (const float *)y_base, qw, (float *)x_base, eps_stop, active_count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_aca_qr(const TargetDev *tg, const TargetState *st, int ntg, double *qw, cudaStream_t s) {
+  if (ntg == 0) return cudaSuccess;
+  const size_t sm = sizeof(double) * (JMAX - 1) * (JMAX - 1);
+  cudaError_t e;
+  if ((e = set_smem(k_aca_qr, sm)) != cudaSuccess) return e;
+  k_aca_qr<<<ntg, NT, sm, s>>>(tg, st, qw);
   return cudaGetLastError();
 }
 

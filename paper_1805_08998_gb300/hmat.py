@@ -22,6 +22,7 @@ STATUS_NAMES = {0: "HMAT_OK", 1: "HMAT_EINVAL", 2: "HMAT_ENOMEM", 3: "HMAT_ECUDA
 K_EXP, K_INVQ, K_POLY2 = 0, 1, 2
 PTS_CUBE, PTS_SPHERE = 0, 1
 MODE_F64, MODE_MIXED = 0, 1
+COMP_RANDOMIZED, COMP_ACA = 0, 1  # compressor of the sum-expressions: Algorithm 8 / Algorithm 6
 
 # every symbol include/hmat.h declares
 EXPORTS = ["hmat_points", "hmat_build", "hmat_multiply", "hmat_multiply_batched", "hmat_to_dense", "hmat_leaf_count", "hmat_leaf_info",
@@ -51,7 +52,7 @@ class MultOpts(ctypes.Structure):
     _fields_ = [("eps", ctypes.c_double), ("mode", ctypes.c_int), ("rank_proposal", ctypes.c_int),
                 ("max_rank", ctypes.c_int), ("max_rounds", ctypes.c_int), ("block_width", ctypes.c_int),
                 ("seed", ctypes.c_uint64), ("rank_model", ctypes.c_void_p), ("fixed_rank", ctypes.c_int),
-                ("power_iters", ctypes.c_int)]
+                ("power_iters", ctypes.c_int), ("compressor", ctypes.c_int)]
 
 
 class TrainOpts(ctypes.Structure):
@@ -253,9 +254,9 @@ def hmat_build(xyz: np.ndarray, kernel: int, leaf_size: int = 32, eta: float = 1
 def hmat_multiply(A: HMatrix, B: HMatrix, eps: float, mode: int = MODE_F64, rank_proposal: int = 0,
                   max_rank: int = 0, max_rounds: int = 0, block_width: int = 0, seed: int = 0,
                   stream=None, allow_notconv: bool = True, rank_model: "RankModel | None" = None,
-                  fixed_rank: int = 0, power_iters: int = -1) -> HMatrix:
+                  fixed_rank: int = 0, power_iters: int = -1, compressor: int = COMP_RANDOMIZED) -> HMatrix:
     opts = MultOpts(eps, mode, rank_proposal, max_rank, max_rounds, block_width, seed,
-                    rank_model.handle if rank_model is not None else None, fixed_rank, power_iters)
+                    rank_model.handle if rank_model is not None else None, fixed_rank, power_iters, compressor)
     h = _P()
     st = lib().hmat_multiply(A.handle, B.handle, ctypes.byref(opts), _stream_ptr(stream), ctypes.byref(h))
     _check(st, allow=(HMAT_ENOTCONV,) if allow_notconv else ())
@@ -266,12 +267,13 @@ def hmat_multiply(A: HMatrix, B: HMatrix, eps: float, mode: int = MODE_F64, rank
 
 def hmat_multiply_batched(As, Bs, eps: float, mode: int = MODE_F64, rank_proposal: int = 0, max_rank: int = 0,
                           max_rounds: int = 0, block_width: int = 0, seed: int = 0, stream=None,
-                          allow_notconv: bool = True, rank_model: "RankModel | None" = None):
+                          allow_notconv: bool = True, rank_model: "RankModel | None" = None,
+                          compressor: int = COMP_RANDOMIZED):
     """Products As[i] Bs[i] in one call; returns the list of outputs."""
     n = len(As)
     assert len(Bs) == n
     opts = MultOpts(eps, mode, rank_proposal, max_rank, max_rounds, block_width, seed,
-                    rank_model.handle if rank_model is not None else None, 0, -1)
+                    rank_model.handle if rank_model is not None else None, 0, -1, compressor)
     a = (_P * max(n, 1))(*[x.handle for x in As])
     b = (_P * max(n, 1))(*[x.handle for x in Bs])
     c = (_P * max(n, 1))()

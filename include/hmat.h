@@ -78,9 +78,14 @@ typedef enum {
  * found from products of the sum-expression with vectors. */
 typedef enum {
   HMAT_COMP_RANDOMIZED = 0,  /* blocked adaptive randomized range finder (Algorithm 8) */
-  HMAT_COMP_ACA = 1          /* adaptive cross approximation (Algorithm 6): one row e_i^T S and
+  HMAT_COMP_ACA = 1,         /* adaptive cross approximation (Algorithm 6): one row e_i^T S and
                                 one column S e_j per step, partial pivoting, stopped when
                                 two consecutive crosses meet eq. (truncaca) at eps/4 */
+  HMAT_COMP_LANCZOS = 2      /* Golub-Kahan-Lanczos bidiagonalization (Algorithm 7) from a
+                                Gaussian start vector (opts->seed), full reorthogonalization,
+                                one S w and one S^T q per step, stopped when two consecutive
+                                steps meet eq. (truncaca) at eps/4; the coefficient factor is
+                                then S^T Q (the bidiagonal B_k with one step of lookahead) */
 } hmat_compressor;
 
 typedef struct {
@@ -110,8 +115,9 @@ typedef struct {
                           subspace iterations, no eps test; eps then only sets the threshold
                           below which sample directions are dropped as zero) */
   int power_iters;     /* subspace iterations q of the fixed-rank mode (0..4; -1 = default 1) */
-  int compressor;      /* hmat_compressor (HMAT_COMP_ACA needs fixed_rank = 0 and rank_proposal = 0;
-                          its rank is capped at max_rank - 1 per block, HMAT_ENOTCONV beyond) */
+  int compressor;      /* hmat_compressor (HMAT_COMP_ACA and HMAT_COMP_LANCZOS need fixed_rank = 0
+                          and rank_proposal = 0; their rank is capped at max_rank - 1 per block,
+                          HMAT_ENOTCONV beyond) */
 } hmat_mult_opts;
 
 typedef struct {
@@ -189,7 +195,8 @@ hmat_status hmat_build(const double *xyz, int64_t n, int dim, hmat_kernel kernel
  * valid C) when some block hit the rank or round cap. With opts->compressor = HMAT_COMP_ACA the
  * far blocks are compressed by adaptive cross approximation (Algorithm 6; a round is then one
  * cross, a row and a column of every unfinished block) and the cross factors L U are truncated
- * to the eps-rank by a QR of L and the same FP64 eigen-truncation. */
+ * to the eps-rank by a QR of L and the same FP64 eigen-truncation; with HMAT_COMP_LANCZOS by
+ * Lanczos bidiagonalization (Algorithm 7), then the same truncation of Q (S^T Q)^T. */
 hmat_status hmat_multiply(const hmat_t A, const hmat_t B, const hmat_mult_opts *opts,
                           void *stream, hmat_t *C);
 

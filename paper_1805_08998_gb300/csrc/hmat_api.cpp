@@ -1081,11 +1081,12 @@ void Product::run() {
   const int power_q = o->power_iters < 0 ? 1 : o->power_iters;
   if (power_q > 4) fail(HMAT_EINVAL, "power_iters must be -1 (default) or 0..4");
   if (o->rank_proposal == 1 && !o->rank_model) fail(HMAT_EINVAL, "rank_proposal 1 needs a rank_model");
-  if (o->compressor != HMAT_COMP_RANDOMIZED && o->compressor != HMAT_COMP_ACA)
-    fail(HMAT_EINVAL, "compressor must be 0 (randomized) or 1 (cross approximation)");
-  const bool aca = o->compressor == HMAT_COMP_ACA;
-  if (aca && (fixed_k != 0 || o->rank_proposal != 0))
-    fail(HMAT_EINVAL, "the cross approximation compressor takes neither fixed_rank nor rank_proposal");
+  if (o->compressor != HMAT_COMP_RANDOMIZED && o->compressor != HMAT_COMP_ACA && o->compressor != HMAT_COMP_LANCZOS)
+    fail(HMAT_EINVAL, "compressor must be 0 (randomized), 1 (cross approximation) or 2 (Lanczos)");
+  const bool aca = o->compressor == HMAT_COMP_ACA, lanczos = o->compressor == HMAT_COMP_LANCZOS;
+  const bool single = aca || lanczos;  // one matrix-vector product per pass
+  if (single && (fixed_k != 0 || o->rank_proposal != 0))
+    fail(HMAT_EINVAL, "the cross approximation and Lanczos compressors take neither fixed_rank nor rank_proposal");
 
   // factors in compute precision
   DevBuf convA, convB;
@@ -1865,7 +1866,46 @@ void Product::run() {
     ck(launch_aca_qr(aa.tg, aa.state, nf, d_qw.as<double>(), s), "cross approximation QR");
     launches++;
   }
-  for (int round = 0; round < max_rounds && nf > 0 && fixed_k == 0 && !aca; round++) {
+  if (lanczos && nf > 0) {
+    // Algorithm 7 on every far target at once: each step is one S pass (q_r from w_r) and one
+    // S^T pass (w_{r+1} from q_r), single columns, with the recurrence, the reorthogonalization
+    // and eq. (truncaca) on the device between them; at most r_max - 1 steps. Then
+    // W = S^T Q in p-column passes, the input of the core truncation.
+    aa.p = 1;
+    aa.round = 1;
+    ck(launch_lz_start(cprec, aa.tg, aa.state, nf, d_qw.as<double>(), d_x.p, o->seed, s), "Lanczos start");
+    launches++;
+    int max_steps = 0;
+    for (const TargetDev &d : ftg) max_steps = std::max(max_steps, d.rmax);
+    for (int step = 0; step < max_steps; step++) {
+      rounds++;
+      timed_apply(false);
+      ck(launch_lz_q(cprec, aa.tg, aa.state, nf, d_y.p, d_qw.as<double>(), d_x.p, s), "Lanczos q");
+      timed_apply(true);
+      ck(cudaMemsetAsync(d_cnt.p, 0, sizeof(int32_t), s), "memset");
+      ck(launch_lz_w(cprec, aa.tg, aa.state, nf, d_y.p, d_qw.as<double>(), d_x.p, 0.25 * eps, d_cnt.as<int32_t>(),
+                     s),
+         "Lanczos w");
+      launches += 2;
+      int32_t act = 0;
+      ck(cudaMemcpyAsync(&act, d_cnt.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s), "count");
+      ck(cudaStreamSynchronize(s), "Lanczos step");
+      if (act == 0) break;
+    }
+    std::vector<TargetState> sl(nf);
+    ck(cudaMemcpyAsync(sl.data(), d_st.p, sizeof(TargetState) * nf, cudaMemcpyDeviceToHost, s), "states");
+    ck(cudaStreamSynchronize(s), "states");
+    int rtop = 0;
+    for (const TargetState &x : sl) rtop = std::max(rtop, x.r);
+    aa.p = p;
+    for (int c0 = 0; c0 < rtop; c0 += p) {
+      ck(launch_lz_load(cprec, aa.tg, aa.state, nf, d_qw.as<double>(), d_x.p, c0, p, s), "projection input");
+      timed_apply(true);
+      ck(launch_lz_store(cprec, aa.tg, aa.state, nf, d_y.p, d_qw.as<double>(), c0, p, s), "projection");
+      launches += 2;
+    }
+  }
+  for (int round = 0; round < max_rounds && nf > 0 && fixed_k == 0 && !single; round++) {
     rounds++;
     const int pr = round == 0 ? pmax : p;  // widest panel this round (round 0: each target's p0)
     aa.p = pr;
@@ -2025,9 +2065,9 @@ void Product::run() {
     const double e = elems_b[ftg[i].leaf];
     const int cols = st[i].r;  // columns that went through both passes
     fa += 2.0 * e * 2.0 * cols;
-    ba += e * 2.0 * (aca ? cols : (cols + p - 1) / p) * es;
+    ba += e * (single ? 2.0 * cols + (lanczos ? (cols + p - 1) / p : 0) : 2.0 * ((cols + p - 1) / p)) * es;
     const double launches_b = 2.0 * std::max(1, st[i].nfwd);
-    bu += launches_b * (e + (double)(ftg[i].m + ftg[i].n) * (aca ? 1 : p)) * es;
+    bu += launches_b * (e + (double)(ftg[i].m + ftg[i].n) * (single ? 1 : p)) * es;
   }
   for (const TargetDev &d : ntg) {
     const double kk = (double)plan.rank_cum[d.blk];

@@ -139,6 +139,7 @@ struct TargetState {
   double nrm2;          // ||W||_F^2 over all columns so far (= ||Q Q^T S||_F^2)
   double est2;          // ||Y||_F^2 / p of the first round (scale for dropping)
   double tail2;         // discarded energy in the final truncation
+  double alpha, beta;   // Lanczos bidiagonalization: the latest alpha_r and beta_r
 };
 
 struct ApplyArgs {
@@ -223,6 +224,25 @@ cudaError_t launch_aca_row(int prec, const TargetDev *tg, TargetState *st, int n
                            void *x_base, cudaStream_t s);
 cudaError_t launch_aca_col(int prec, const TargetDev *tg, TargetState *st, int ntg, const void *y_base, double *qw,
                            void *x_base, double eps_stop, int32_t *active_count, cudaStream_t s);
+// Golub-Kahan-Lanczos bidiagonalization of the sum-expressions (Algorithm 7) with full
+// reorthogonalization, one step per call pair: q_r (column r of the Q buffer) from S w_r and
+// w_{r+1} (column r + 1 of the W buffer) from S^T q_r. launch_lz_start draws w_1 (Gaussian,
+// normalised; the S pass input); launch_lz_q forms q_r = S w_r - beta_{r-1} q_{r-1}, projects it
+// twice against q_1..q_{r-1}, normalises (alpha_r) and sets it as the S^T input; launch_lz_w
+// forms S^T q_r - alpha_r w_r, projects it twice against w_1..w_r, normalises (beta_r), applies
+// eq. (truncaca) to alpha_r^2 + beta_r^2 at eps_stop (two consecutive steps) and counts the
+// targets still active. launch_lz_load / launch_lz_store move columns c0 .. c0+p-1 of Q into the
+// S^T pass input and its output into W (the projection W = S^T Q that ends the compression).
+cudaError_t launch_lz_start(int prec, const TargetDev *tg, TargetState *st, int ntg, double *qw, void *x_base,
+                            uint64_t seed, cudaStream_t s);
+cudaError_t launch_lz_q(int prec, const TargetDev *tg, TargetState *st, int ntg, const void *y_base, double *qw,
+                        void *x_base, cudaStream_t s);
+cudaError_t launch_lz_w(int prec, const TargetDev *tg, TargetState *st, int ntg, const void *y_base, double *qw,
+                        void *x_base, double eps_stop, int32_t *active_count, cudaStream_t s);
+cudaError_t launch_lz_load(int prec, const TargetDev *tg, TargetState *st, int ntg, const double *qw, void *x_base,
+                           int c0, int p, cudaStream_t s);
+cudaError_t launch_lz_store(int prec, const TargetDev *tg, const TargetState *st, int ntg, const void *y_base,
+                            double *qw, int c0, int p, cudaStream_t s);
 // L = Q R (classical Gram-Schmidt twice, FP64) in place in the Q buffer and W <- U R^T in place,
 // so that L U^T = Q W^T with orthonormal Q: the input of the core truncation
 cudaError_t launch_aca_qr(const TargetDev *tg, const TargetState *st, int ntg, double *qw, cudaStream_t s);

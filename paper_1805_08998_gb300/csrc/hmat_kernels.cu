@@ -1407,6 +1407,192 @@ __global__ void __launch_bounds__(NT) k_aca_qr(const TargetDev *tg, const Target
     }
 }
 
+// ---------------------------------------------------------------------------------------
+// a3-a5 by Lanczos bidiagonalization: Algorithm 7 on the sum-expression with full
+// reorthogonalization, one S and one S^T pass per step for every unfinished far target
+// ---------------------------------------------------------------------------------------
+
+// v <- v - B (B^T v), twice, for the first nb columns of B (ld rows); g holds nb <= JMAX
+// coefficients. Every thread of the block must call; ends with a barrier.
+__device__ void block_project2(double *v, const double *B, int64_t rows, int nb, double *g) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int pass = 0; pass < 2 && nb > 0; pass++) {
+    for (int s = w; s < nb; s += NT / 32) {
+      const double *bs = B + (int64_t)s * rows;
+      double a = 0.0;
+      for (int64_t k = lane; k < rows; k += 32) a += bs[k] * v[k];
+      a = warp_sum(a);
+      if (lane == 0) g[s] = a;
+    }
+    __syncthreads();
+    for (int64_t k = threadIdx.x; k < rows; k += NT) {
+      double a = 0.0;
+      for (int s = 0; s < nb; s++) a += B[k + (int64_t)s * rows] * g[s];
+      v[k] -= a;
+    }
+    __syncthreads();
+  }
+}
+
+// w_1: Gaussian entries (the same counter-based generator as the test matrices, round 0,
+// column 0), normalised, into column 0 of the W buffer and as the S pass input
+template <typename T>
+__global__ void __launch_bounds__(NT) k_lz_start(const TargetDev *tg, TargetState *st, double *qw, T *x_base,
+                                                 uint64_t seed) {
+  __shared__ double red[NT / 32];
+  const int b = blockIdx.x;
+  const TargetDev t = tg[b];
+  double *w = qw + t.w_off;
+  T *X = x_base + t.x_off;
+  double part = 0.0;
+  for (int64_t i = threadIdx.x; i < t.n; i += NT) {
+    const double v = (double)omega(seed, t.leaf, 0, 0, (int)i);
+    w[i] = v;
+    part += v * v;
+  }
+  const double nrm = sqrt(block_sum(part, red));
+  const double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
+  for (int64_t i = threadIdx.x; i < t.n; i += NT) {
+    w[i] *= inv;
+    X[i] = T(w[i]);
+  }
+  if (threadIdx.x == 0) {
+    st[b].alpha = 0.0;
+    st[b].beta = 0.0;
+    st[b].hits = 0;
+    if (!(nrm > 0.0)) st[b].active = 0;
+  }
+}
+
+// q_r = S w_r - beta_{r-1} q_{r-1} (S w_r from the S pass in y_base), projected twice against
+// q_1..q_{r-1}, alpha_r = ||q_r||, q_r / alpha_r into column r of the Q buffer and as the S^T
+// pass input. alpha_r = 0 (the Krylov space is exhausted) ends the target.
+template <typename T>
+__global__ void __launch_bounds__(NT) k_lz_q(const TargetDev *tg, TargetState *st, const T *y_base, double *qw,
+                                             T *x_base) {
+  __shared__ double g[JMAX];
+  __shared__ double red[NT / 32];
+  const int b = blockIdx.x;
+  if (st[b].active == 0) return;
+  const TargetDev t = tg[b];
+  const int r = st[b].r;
+  const int64_t m = t.m;
+  double *Q = qw + t.q_off;
+  double *q = Q + (int64_t)r * m;
+  const T *y = y_base + t.y_off;
+  const double beta = st[b].beta;
+  for (int64_t k = threadIdx.x; k < m; k += NT) q[k] = (double)y[k] - (r > 0 ? beta * Q[k + (int64_t)(r - 1) * m] : 0.0);
+  __syncthreads();
+  block_project2(q, Q, m, r, g);
+  double part = 0.0;
+  for (int64_t k = threadIdx.x; k < m; k += NT) part += q[k] * q[k];
+  const double alpha = sqrt(block_sum(part, red));
+  if (!(alpha > 0.0) || !isfinite(alpha)) {
+    if (threadIdx.x == 0) st[b].active = 0;
+    return;
+  }
+  const double inv = 1.0 / alpha;
+  T *X = x_base + t.x_off;
+  for (int64_t k = threadIdx.x; k < m; k += NT) {
+    q[k] *= inv;
+    X[k] = T(q[k]);
+  }
+  if (threadIdx.x == 0) st[b].alpha = alpha;
+}
+
+// w = S^T q_r - alpha_r w_r (S^T q_r from the S^T pass), projected twice against w_1..w_r,
+// beta_r = ||w||. The step's increment q_r (alpha_r w_r + beta_r w_{r+1})^T has Frobenius norm
+// sqrt(alpha_r^2 + beta_r^2) and the approximation so far sum_{s<r} (alpha_s^2 + beta_s^2):
+// eq. (truncaca) at eps_stop, met by two consecutive steps, ends the target, as do r + 1 = min(m, n),
+// beta_r = 0 and the basis capacity (rank marked -2). Otherwise w_{r+1} = w / beta_r goes into
+// column r + 1 of the W buffer and becomes the next S pass input.
+template <typename T>
+__global__ void __launch_bounds__(NT) k_lz_w(const TargetDev *tg, TargetState *st, const T *y_base, double *qw,
+                                             T *x_base, double eps_stop, int32_t *active_count) {
+  __shared__ double g[JMAX];
+  __shared__ double red[NT / 32];
+  __shared__ int act_s;
+  const int b = blockIdx.x;
+  if (st[b].active == 0) return;
+  const TargetDev t = tg[b];
+  const int r = st[b].r;
+  const int64_t n = t.n;
+  double *W = qw + t.w_off;
+  const double *wr = W + (int64_t)r * n;
+  double *wn = W + (int64_t)(r + 1) * n;  // r + 1 <= rmax - 1: inside the buffer
+  const T *y = y_base + t.y_off;
+  const double alpha = st[b].alpha;
+  for (int64_t k = threadIdx.x; k < n; k += NT) wn[k] = (double)y[k] - alpha * wr[k];
+  __syncthreads();
+  block_project2(wn, W, n, r + 1, g);
+  double part = 0.0;
+  for (int64_t k = threadIdx.x; k < n; k += NT) part += wn[k] * wn[k];
+  const double beta = sqrt(block_sum(part, red));
+  if (threadIdx.x == 0) {
+    const double inc = alpha * alpha + beta * beta;
+    const double prev = st[b].nrm2;
+    st[b].nrm2 = prev + inc;
+    const int hits = inc <= eps_stop * eps_stop * prev ? st[b].hits + 1 : 0;  // eq. (truncaca)
+    st[b].hits = hits;
+    const int rn = r + 1;
+    st[b].r = rn;
+    st[b].nfwd += 1;
+    int act = hits < 2;
+    if (rn >= min(t.m, t.n)) act = 0;                 // exact
+    if (!(beta > 0.0) || !isfinite(beta)) act = 0;    // invariant subspace
+    if (act && rn >= t.rmax - 1) {                    // capacity
+      st[b].rank = -2;
+      act = 0;
+    }
+    act_s = act;
+  }
+  __syncthreads();
+  if (!act_s) {
+    if (threadIdx.x == 0) st[b].active = 0;
+    return;
+  }
+  const double inv = 1.0 / beta;
+  T *X = x_base + t.x_off;
+  for (int64_t k = threadIdx.x; k < n; k += NT) {
+    wn[k] *= inv;
+    X[k] = T(wn[k]);
+  }
+  if (threadIdx.x == 0) {
+    st[b].beta = beta;
+    atomicAdd(active_count, 1);
+  }
+}
+
+// columns c0 .. c0+p-1 of Q (those below r) as the S^T pass input, zero padded; targets with no
+// such column sit the pass out
+template <typename T>
+__global__ void __launch_bounds__(NT) k_lz_load(const TargetDev *tg, TargetState *st, const double *qw, T *x_base,
+                                                int c0, int p) {
+  const int b = blockIdx.x;
+  const TargetDev t = tg[b];
+  const int cnt = min(p, st[b].r - c0);
+  __syncthreads();  // every thread has read r before thread 0 may change the state
+  if (threadIdx.x == 0) st[b].active = cnt > 0 ? 1 : 0;
+  if (cnt <= 0) return;
+  const double *Q = qw + t.q_off + (int64_t)c0 * t.m;
+  T *X = x_base + t.x_off;
+  for (int64_t o = threadIdx.x; o < (int64_t)t.m * p; o += NT) X[o] = o < (int64_t)t.m * cnt ? T(Q[o]) : T(0);
+}
+
+// the S^T pass output (n x p) into columns c0 .. c0+p-1 of W, those below r
+template <typename T>
+__global__ void __launch_bounds__(NT) k_lz_store(const TargetDev *tg, const TargetState *st, const T *y_base,
+                                                 double *qw, int c0, int p) {
+  const int b = blockIdx.x;
+  if (st[b].active == 0) return;
+  const TargetDev t = tg[b];
+  const int cnt = min(p, st[b].r - c0);
+  if (cnt <= 0) return;
+  double *W = qw + t.w_off + (int64_t)c0 * t.n;
+  const T *y = y_base + t.y_off;
+  for (int64_t o = threadIdx.x; o < (int64_t)t.n * cnt; o += NT) W[o] = (double)y[o];
+}
+
 template <typename T>
 __global__ void __launch_bounds__(NT) k_write_far(const TargetDev *tg, const TargetState *st, const double *qw,
                                                   const LeafDev *leafC, T *dataC) {
@@ -1744,6 +1930,48 @@ cudaError_t launch_aca_col(int prec, const TargetDev *tg, TargetState *st, int n
                                          active_count);
   else
     k_aca_col<float><<<ntg, NT, 0, s>>>(tg, st, (const float *)y_base, qw, (float *)x_base, eps_stop, active_count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lz_start(int prec, const TargetDev *tg, TargetState *st, int ntg, double *qw, void *x_base,
+                            uint64_t seed, cudaStream_t s) {
+  if (ntg == 0) return cudaSuccess;
+  if (prec == 64) k_lz_start<double><<<ntg, NT, 0, s>>>(tg, st, qw, (double *)x_base, seed);
+  else k_lz_start<float><<<ntg, NT, 0, s>>>(tg, st, qw, (float *)x_base, seed);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lz_q(int prec, const TargetDev *tg, TargetState *st, int ntg, const void *y_base, double *qw,
+                        void *x_base, cudaStream_t s) {
+  if (ntg == 0) return cudaSuccess;
+  if (prec == 64) k_lz_q<double><<<ntg, NT, 0, s>>>(tg, st, (const double *)y_base, qw, (double *)x_base);
+  else k_lz_q<float><<<ntg, NT, 0, s>>>(tg, st, (const float *)y_base, qw, (float *)x_base);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lz_w(int prec, const TargetDev *tg, TargetState *st, int ntg, const void *y_base, double *qw,
+                        void *x_base, double eps_stop, int32_t *active_count, cudaStream_t s) {
+  if (ntg == 0) return cudaSuccess;
+  if (prec == 64)
+    k_lz_w<double><<<ntg, NT, 0, s>>>(tg, st, (const double *)y_base, qw, (double *)x_base, eps_stop, active_count);
+  else
+    k_lz_w<float><<<ntg, NT, 0, s>>>(tg, st, (const float *)y_base, qw, (float *)x_base, eps_stop, active_count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lz_load(int prec, const TargetDev *tg, TargetState *st, int ntg, const double *qw, void *x_base,
+                           int c0, int p, cudaStream_t s) {
+  if (ntg == 0) return cudaSuccess;
+  if (prec == 64) k_lz_load<double><<<ntg, NT, 0, s>>>(tg, st, qw, (double *)x_base, c0, p);
+  else k_lz_load<float><<<ntg, NT, 0, s>>>(tg, st, qw, (float *)x_base, c0, p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lz_store(int prec, const TargetDev *tg, const TargetState *st, int ntg, const void *y_base,
+                            double *qw, int c0, int p, cudaStream_t s) {
+  if (ntg == 0) return cudaSuccess;
+  if (prec == 64) k_lz_store<double><<<ntg, NT, 0, s>>>(tg, st, (const double *)y_base, qw, c0, p);
+  else k_lz_store<float><<<ntg, NT, 0, s>>>(tg, st, (const float *)y_base, qw, c0, p);
   return cudaGetLastError();
 }
 

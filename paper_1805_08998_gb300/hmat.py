@@ -22,7 +22,8 @@ STATUS_NAMES = {0: "HMAT_OK", 1: "HMAT_EINVAL", 2: "HMAT_ENOMEM", 3: "HMAT_ECUDA
 K_EXP, K_INVQ, K_POLY2 = 0, 1, 2
 PTS_CUBE, PTS_SPHERE = 0, 1
 MODE_F64, MODE_MIXED = 0, 1
-COMP_RANDOMIZED, COMP_ACA = 0, 1  # compressor of the sum-expressions: Algorithm 8 / Algorithm 6
+# compressor of the sum-expressions: Algorithm 8 / Algorithm 6 / Algorithm 7
+COMP_RANDOMIZED, COMP_ACA, COMP_LANCZOS = 0, 1, 2
 
 # every symbol include/hmat.h declares
 EXPORTS = ["hmat_points", "hmat_build", "hmat_multiply", "hmat_multiply_batched", "hmat_to_dense", "hmat_leaf_count", "hmat_leaf_info",

@@ -1,7 +1,9 @@
-"""The cross approximation compressor (Algorithm 6 on the sum-expressions, then the truncation of
-the cross factors to the eps-rank) against the dense oracle product: every far block within
-1.5 eps of the exact block with rank at most k_eps + 2, near blocks exact, in FP64 and in the
-FP32 mixed mode, on one grouped (memory-bounded) product and in a batch."""
+"""The compressors of sum-expressions that work one vector at a time -- cross approximation
+(Algorithm 6, then a QR of L and the eps truncation) and Lanczos bidiagonalization (Algorithm 7
+with full reorthogonalization, then the truncation of Q (S^T Q)^T) -- against the dense oracle
+product: every far block within 1.5 eps of the exact block with rank at most k_eps + 2, near
+blocks exact, in FP64 and in the FP32 mixed mode, on one grouped (memory-bounded) product and in
+a batch."""
 import numpy as np
 import pytest
 
@@ -20,18 +22,26 @@ def H():
     return hmat
 
 
-def test_aca_n2048_f64(H, oracle):
+COMPRESSORS = ["aca", "lanczos"]
+
+
+def _comp(H, name):
+    return {"aca": H.COMP_ACA, "lanczos": H.COMP_LANCZOS}[name]
+
+
+@pytest.mark.parametrize("comp", COMPRESSORS)
+def test_n2048_f64(H, oracle, comp):
     """U[0,1]^2 (seed 0), exp(-r), leaf 32, A = B by ACA to 1e-10, eps = 1e-6, FP64."""
     P = inputs.points(0, 2, 2048, 0)
     T, Ao, _ = _oracle_pair(oracle, P, 32, 1.0, 0, 0, 1e-10)
     A = H.hmat_build(P, 0, leaf_size=32, eta=1.0, aca_eps=1e-10)
-    C = H.hmat_multiply(A, A, 1e-6, mode=H.MODE_F64, compressor=H.COMP_ACA)
+    C = H.hmat_multiply(A, A, 1e-6, mode=H.MODE_F64, compressor=_comp(H, comp))
     assert C.last_status == H.HMAT_OK
     DC = oracle.matmul(Ao.dense(), Ao.dense())
     worst, _, nf = _check_product(oracle, T, C, DC, 1e-6, near_rtol=1e-11)
     assert nf == int((T.leaf_blocks[:, 2] == 1).sum())
     st = C.stats()
-    # one step per cross: at least two crosses per block (the stop needs two that pass the test)
+    # one step per cross or Lanczos step: at least two per block (the stop needs two that pass)
     assert st["sample_passes"] >= 2 * nf
     Cd = C.to_dense()
     perm = T.perm
@@ -40,37 +50,41 @@ def test_aca_n2048_f64(H, oracle):
     assert np.linalg.norm(Cd - DCo) <= 1.5e-6 * np.linalg.norm(DCo)
 
 
+@pytest.mark.parametrize("comp", COMPRESSORS)
 @pytest.mark.parametrize("eps", [1e-4, 1e-8])
-def test_aca_3d_two_kernels(H, oracle, eps):
+def test_3d_two_kernels(H, oracle, eps, comp):
     """U[0,1]^3 (seed 5), A = exp(-r), B = 1/(1+r^2): the 3-D blocks on which a single
     eq. (truncaca) test at eps/4 stops early on some blocks."""
     P = inputs.points(0, 3, 3000, 5)
     T, Ao, Bo = _oracle_pair(oracle, P, 32, 1.0, 0, 1, 1e-10)
     A, B = _gpu_pair(H, P, 32, 1.0, 0, 1, 1e-10)
-    C = H.hmat_multiply(A, B, eps, mode=H.MODE_F64, compressor=H.COMP_ACA)
+    C = H.hmat_multiply(A, B, eps, mode=H.MODE_F64, compressor=_comp(H, comp))
     DC = oracle.matmul(Ao.dense(), Bo.dense())
     _check_product(oracle, T, C, DC, eps, near_rtol=1e-11)
 
 
-def test_aca_mixed_fp32(H, oracle):
+@pytest.mark.parametrize("comp", COMPRESSORS)
+def test_mixed_fp32(H, oracle, comp):
     """FP32 factors and contractions (rows and columns of S in FP32), FP64 cross updates, QR and
     core truncation, against the oracle on the same FP32-rounded inputs."""
     P = inputs.points(1, 3, 1500, 0)
     T, Ao, Bo = _oracle_pair(oracle, P, 32, 1.0, 0, 1, 1e-8, prec32=True)
     A, B = _gpu_pair(H, P, 32, 1.0, 0, 1, 1e-8, prec=32)
-    C = H.hmat_multiply(A, B, 1e-6, mode=H.MODE_MIXED, compressor=H.COMP_ACA)
+    C = H.hmat_multiply(A, B, 1e-6, mode=H.MODE_MIXED, compressor=_comp(H, comp))
     assert C.last_status == H.HMAT_OK
     DC = oracle.matmul(Ao.dense(), Bo.dense())
     _check_product(oracle, T, C, DC, 1e-6, near_rtol=2e-6)
 
 
-def test_aca_closed_forms(H, oracle):
-    """(1 + x.y)^2 in 2-D: every product block has rank <= 6, so the crosses exhaust it and the
-    blocks come out at rank <= 6 (+2) to 1e-10; a coarse eps keeps tiny ranks within bound."""
+@pytest.mark.parametrize("comp", COMPRESSORS)
+def test_closed_forms(H, oracle, comp):
+    """(1 + x.y)^2 in 2-D: every product block has rank <= 6, so the crosses (or the Krylov
+    space) exhaust it and the blocks come out at rank <= 6 (+2) to 1e-10; a coarse eps keeps tiny
+    ranks within bound."""
     P = inputs.points(0, 2, 600, 2)
     T, Ao, _ = _oracle_pair(oracle, P, 16, 1.0, 2, 2, 1e-13)
     A = H.hmat_build(P, 2, leaf_size=16, eta=1.0, aca_eps=1e-13)
-    C = H.hmat_multiply(A, A, 1e-10, mode=H.MODE_F64, compressor=H.COMP_ACA)
+    C = H.hmat_multiply(A, A, 1e-10, mode=H.MODE_F64, compressor=_comp(H, comp))
     la = H.leaf_arrays(C)
     assert la.rank[la.far == 1].max() <= 8
     DC = oracle.matmul(Ao.dense(), Ao.dense())
@@ -78,41 +92,45 @@ def test_aca_closed_forms(H, oracle):
     P = inputs.points(0, 2, 800, 5)
     T, Ao, _ = _oracle_pair(oracle, P, 16, 1.0, 0, 0, 1e-10)
     A = H.hmat_build(P, 0, leaf_size=16, aca_eps=1e-10)
-    C = H.hmat_multiply(A, A, 0.3, compressor=H.COMP_ACA)
+    C = H.hmat_multiply(A, A, 0.3, compressor=_comp(H, comp))
     DC = oracle.matmul(Ao.dense(), Ao.dense())
     _check_product(oracle, T, C, DC, 0.3, near_rtol=1e-11)
 
 
-def test_aca_cap_and_invalid(H):
-    """A rank cap below the eps-rank ends with HMAT_ENOTCONV (ranks <= max_rank - 1, the last
-    basis column holds the used-row flags); ACA takes neither fixed_rank nor a rank proposal."""
+@pytest.mark.parametrize("comp", COMPRESSORS)
+def test_cap_and_invalid(H, comp):
+    """A rank cap below the eps-rank ends with HMAT_ENOTCONV (ranks <= max_rank - 1: the cross
+    approximation keeps the used-row flags in the last basis column, Lanczos the next w there);
+    neither compressor takes fixed_rank or a rank proposal."""
     P = inputs.points(0, 2, 1024, 0)
     A = H.hmat_build(P, 0, leaf_size=32, aca_eps=1e-12)
-    C = H.hmat_multiply(A, A, 1e-12, max_rank=8, compressor=H.COMP_ACA)
+    C = H.hmat_multiply(A, A, 1e-12, max_rank=8, compressor=_comp(H, comp))
     assert C.last_status == H.HMAT_ENOTCONV
     st = C.stats()
     assert st["not_converged"] > 0 and st["max_rank"] <= 7
-    for kw in ({"fixed_rank": 4}, {"rank_proposal": 2}, {"compressor": 2}, {"compressor": -1}):
-        args = {"compressor": H.COMP_ACA, **kw}
+    for kw in ({"fixed_rank": 4}, {"rank_proposal": 2}, {"compressor": 3}, {"compressor": -1}):
+        args = {"compressor": _comp(H, comp), **kw}
         with pytest.raises(H.HmatError) as e:
             H.hmat_multiply(A, A, 1e-6, **args)
         assert e.value.status == H.HMAT_EINVAL
 
 
-def test_aca_batched_matches_single(H):
-    """Three products in one batched call give the blocks of three single calls: no random
-    numbers are drawn, but sums accumulated by atomics may round differently and move a pivot,
-    so the blocks agree to the sum of the two results' bounds (3 eps), ranks mostly exactly."""
+@pytest.mark.parametrize("comp", COMPRESSORS)
+def test_batched_matches_single(H, comp):
+    """Three products in one batched call give the blocks of three single calls (the same seed
+    draws the same Lanczos start vectors), but sums accumulated by atomics may round differently
+    and move a pivot or a stop, so the blocks agree to the sum of the two results' bounds
+    (3 eps), ranks mostly exactly."""
     As, Bs = [], []
     for i, n in enumerate((900, 1300, 700)):
         P = inputs.points(0, 3, n, 40 + i)
         A, B = _gpu_pair(H, P, 32, 1.0, 0, 1, 1e-9)
         As.append(A)
         Bs.append(B)
-    Cb = H.hmat_multiply_batched(As, Bs, 1e-6, compressor=H.COMP_ACA)
+    Cb = H.hmat_multiply_batched(As, Bs, 1e-6, compressor=_comp(H, comp))
     same = total = 0
     for A, B, C in zip(As, Bs, Cb):
-        Cs = H.hmat_multiply(A, B, 1e-6, compressor=H.COMP_ACA)
+        Cs = H.hmat_multiply(A, B, 1e-6, compressor=_comp(H, comp))
         for l in range(Cs.leaf_count()):
             a, b = Cs.leaf_get(l), C.leaf_get(l)
             if isinstance(a, tuple):
@@ -125,14 +143,15 @@ def test_aca_batched_matches_single(H):
     assert same >= 0.95 * total
 
 
-def test_aca_grouped(H, oracle, monkeypatch):
-    """A memory budget that splits the product into groups: every group runs its own cross
-    approximation steps; the blocks still meet the bound."""
+@pytest.mark.parametrize("comp", COMPRESSORS)
+def test_grouped(H, oracle, monkeypatch, comp):
+    """A memory budget that splits the product into groups: every group runs its own steps; the
+    blocks still meet the bound."""
     P = inputs.points(0, 3, 3000, 1)
     T, Ao, Bo = _oracle_pair(oracle, P, 32, 1.0, 0, 1, 1e-10)
     A, B = _gpu_pair(H, P, 32, 1.0, 0, 1, 1e-10)
     monkeypatch.setenv("HMAT_MEMORY_BUDGET_GB", "0.05")
-    C = H.hmat_multiply(A, B, 1e-6, compressor=H.COMP_ACA)
+    C = H.hmat_multiply(A, B, 1e-6, compressor=_comp(H, comp))
     monkeypatch.delenv("HMAT_MEMORY_BUDGET_GB")
     assert C.stats()["groups"] > 1
     DC = oracle.matmul(Ao.dense(), Bo.dense())

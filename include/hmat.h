@@ -80,12 +80,13 @@ typedef enum {
   HMAT_COMP_RANDOMIZED = 0,  /* blocked adaptive randomized range finder (Algorithm 8) */
   HMAT_COMP_ACA = 1,         /* adaptive cross approximation (Algorithm 6): one row e_i^T S and
                                 one column S e_j per step, partial pivoting, stopped when
-                                two consecutive crosses meet eq. (truncaca) at eps/4 */
+                                two consecutive crosses meet eq. (truncaca) at
+                                max(eps/8, 4 u), u the unit roundoff of the passes */
   HMAT_COMP_LANCZOS = 2      /* Golub-Kahan-Lanczos bidiagonalization (Algorithm 7) from a
                                 Gaussian start vector (opts->seed), full reorthogonalization,
-                                one S w and one S^T q per step, stopped when two consecutive
-                                steps meet eq. (truncaca) at eps/4; the coefficient factor is
-                                then S^T Q (the bidiagonal B_k with one step of lookahead) */
+                                one S w and one S^T q per step, stopped like ACA; the
+                                coefficient factor is then S^T Q (the bidiagonal B_k with one
+                                step of lookahead) */
 } hmat_compressor;
 
 typedef struct {

@@ -1,0 +1,147 @@
+"""FP64 reference of the one-vector compressors of a block -- test infrastructure only.
+
+Only the tests and the trials script beside this file use this module; the library never calls
+it, and the two share no code. Each routine takes an explicit dense block D (m x n) and sees it
+only through the products the paper allows a compressor: a row e_i^T D, a column D e_j, or D w
+and D^T q.
+
+  aca(D, eps_stop, kcap, need)
+      Algorithm 6 (Sec. 4.1) with partial pivoting: first pivot row 0; the column pivot is the
+      entry of largest modulus of the residual row (first on ties); the next pivot row is the
+      entry of largest modulus of the new residual column among the rows not used yet; an
+      exactly zero residual row is marked used and the first unused row is tried. Stop once
+      `need` consecutive crosses meet eq. (truncaca), ||l_r|| ||u_r|| <= eps_stop ||L_{r-1} U_{r-1}||_F
+      (the norm of the approximation before the cross, updated from the cross terms), keeping
+      every cross; or at min(m, n) or kcap crosses.
+  lanczos(D, w1, eps_stop, kcap, need)
+      Algorithm 7 (Sec. 4.2), Golub-Kahan-Lanczos bidiagonalization from the unit vector w1, with
+      every new q and w orthogonalized twice against all earlier ones. Step r adds
+      q_r (alpha_r w_r + beta_r w_{r+1})^T (one step of lookahead), of norm
+      sqrt(alpha_r^2 + beta_r^2); stop once `need` consecutive steps meet eq. (truncaca) against
+      sum_{s<r} (alpha_s^2 + beta_s^2), or at alpha_r = 0, beta_r = 0, min(m, n) or kcap steps.
+  truncate(L, U, eps)
+      Algorithm 5 (Sec. 4): QR of both factors, SVD of the small core, and the eps-rank of the
+      core (smallest k with relative Frobenius tail <= eps), giving the best approximation of
+      L U^T at relative error eps.
+
+Pins (tests/test_oracle.py): ACA reproduces the pivot rows and columns exactly (its
+interpolation property) and a matrix of rank r after r crosses; it skips a zero first row;
+Lanczos gives orthonormal Q and W with Q^T D W upper bidiagonal (alpha on the diagonal, beta
+above it), and run to full length the singular values of that bidiagonal are those of D (numpy's
+SVD); truncate's error equals the tail of numpy's singular values of L U^T.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def aca(D: np.ndarray, eps_stop: float, kcap: int, need: int = 2):
+    """Cross approximation of D: returns (L (m x k), U (n x k), k) with D ~ L U^T."""
+    D = np.asarray(D, np.float64)
+    m, n = D.shape
+    used = np.zeros(m, bool)
+    Ls, Us = [], []
+    norm2 = 0.0
+    hits = 0
+    i = 0
+    cap = min(m, n, kcap)
+    while len(Ls) < cap:
+        # residual row i of D - L U^T
+        u = D[i, :].copy()
+        for l, uu in zip(Ls, Us):
+            u -= l[i] * uu
+        j = int(np.argmax(np.abs(u)))
+        if u[j] == 0.0:
+            used[i] = True
+            free = np.flatnonzero(~used)
+            if free.size == 0:
+                break
+            i = int(free[0])
+            continue
+        u = u / u[j]
+        # residual column j
+        l = D[:, j].copy()
+        for ll, uu in zip(Ls, Us):
+            l -= uu[j] * ll
+        used[i] = True
+        cross = sum(float(ll @ l) * float(uu @ u) for ll, uu in zip(Ls, Us))
+        prev = norm2
+        norm2 = prev + 2.0 * cross + float(l @ l) * float(u @ u)
+        Ls.append(l)
+        Us.append(u)
+        hits = hits + 1 if float(l @ l) * float(u @ u) <= eps_stop * eps_stop * prev else 0
+        if hits >= need:
+            break
+        a = np.abs(l)
+        a[used] = -1.0
+        if np.all(used):
+            break
+        i = int(np.argmax(a))
+    L = np.array(Ls).T if Ls else np.zeros((m, 0))
+    U = np.array(Us).T if Us else np.zeros((n, 0))
+    return L, U, len(Ls)
+
+
+def _orth2(v: np.ndarray, basis) -> np.ndarray:
+    """v minus its projection onto the orthonormal vectors in basis, done twice."""
+    for _ in range(2):
+        for b in basis:
+            v = v - float(b @ v) * b
+    return v
+
+
+def lanczos(D: np.ndarray, w1: np.ndarray, eps_stop: float, kcap: int, need: int = 2):
+    """Bidiagonalization of D from w1: returns (Q (m x k), W (n x k'), alpha (k), beta (k), k),
+    k' = k + 1 when w_{k+1} exists, else k."""
+    D = np.asarray(D, np.float64)
+    m, n = D.shape
+    w = np.asarray(w1, np.float64)
+    w = w / np.linalg.norm(w)
+    Qs, Ws = [], [w]
+    alphas, betas = [], []
+    norm2 = 0.0
+    hits = 0
+    beta = 0.0
+    cap = min(m, n, kcap)
+    while len(Qs) < cap:
+        q = D @ Ws[-1]
+        if Qs:
+            q = q - beta * Qs[-1]
+        q = _orth2(q, Qs)
+        alpha = float(np.linalg.norm(q))
+        if alpha == 0.0:
+            break
+        q = q / alpha
+        Qs.append(q)
+        wn = D.T @ q - alpha * Ws[-1]
+        wn = _orth2(wn, Ws)
+        beta = float(np.linalg.norm(wn))
+        alphas.append(alpha)
+        betas.append(beta)
+        inc = alpha * alpha + beta * beta
+        prev = norm2
+        norm2 = prev + inc
+        hits = hits + 1 if inc <= eps_stop * eps_stop * prev else 0
+        if hits >= need or beta == 0.0 or len(Qs) >= cap:
+            break
+        Ws.append(wn / beta)
+    Q = np.array(Qs).T if Qs else np.zeros((m, 0))
+    W = np.array(Ws).T
+    return Q, W, np.array(alphas), np.array(betas), len(Qs)
+
+
+def truncate(L: np.ndarray, U: np.ndarray, eps: float):
+    """Best approximation of L U^T at relative Frobenius error eps: (U_k S_k, V_k)."""
+    L = np.asarray(L, np.float64)
+    U = np.asarray(U, np.float64)
+    if L.shape[1] == 0:
+        return L.copy(), U.copy()
+    QL, RL = np.linalg.qr(L)
+    QU, RU = np.linalg.qr(U)
+    X, s, Yt = np.linalg.svd(RL @ RU.T)
+    tail = np.sqrt(np.cumsum((s * s)[::-1])[::-1])  # tail[k] = ||s[k:]||
+    total = tail[0]
+    k = 0
+    while k < len(s) and tail[k] > eps * total:
+        k += 1
+    return QL @ (X[:, :k] * s[:k]), QU @ Yt[:k, :].T

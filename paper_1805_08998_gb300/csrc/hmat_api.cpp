@@ -1745,6 +1745,9 @@ void Product::run() {
   aa.p = p;
   const double eps = o->eps;
   const double eps_stop = 0.5 * eps;
+  // stop tolerance of the one-vector compressors: eps / 8, but not below four rounding units of
+  // the precision the passes run in (their increments cannot be resolved below it)
+  const double eps_stop_1v = std::max(0.125 * eps, 4.0 * (cprec == 64 ? 0x1.0p-53 : 0x1.0p-24));
   const double eps_trunc = fixed_k > 0 ? 0.0 : eps;  // fixed rank: keep every sampled direction
   int rounds = 0;
   // events around every application pass (S and S^T), read after the stream synchronises
@@ -1854,7 +1857,7 @@ void Product::run() {
       ck(launch_aca_row(cprec, aa.tg, aa.state, nf, d_y.p, d_qw.as<double>(), d_x.p, s), "cross approximation row");
       timed_apply(false);
       ck(cudaMemsetAsync(d_cnt.p, 0, sizeof(int32_t), s), "memset");
-      ck(launch_aca_col(cprec, aa.tg, aa.state, nf, d_y.p, d_qw.as<double>(), d_x.p, 0.25 * eps,
+      ck(launch_aca_col(cprec, aa.tg, aa.state, nf, d_y.p, d_qw.as<double>(), d_x.p, eps_stop_1v,
                         d_cnt.as<int32_t>(), s),
          "cross approximation column");
       launches += 2;
@@ -1883,7 +1886,7 @@ void Product::run() {
       ck(launch_lz_q(cprec, aa.tg, aa.state, nf, d_y.p, d_qw.as<double>(), d_x.p, s), "Lanczos q");
       timed_apply(true);
       ck(cudaMemsetAsync(d_cnt.p, 0, sizeof(int32_t), s), "memset");
-      ck(launch_lz_w(cprec, aa.tg, aa.state, nf, d_y.p, d_qw.as<double>(), d_x.p, 0.25 * eps, d_cnt.as<int32_t>(),
+      ck(launch_lz_w(cprec, aa.tg, aa.state, nf, d_y.p, d_qw.as<double>(), d_x.p, eps_stop_1v, d_cnt.as<int32_t>(),
                      s),
          "Lanczos w");
       launches += 2;

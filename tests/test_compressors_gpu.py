@@ -50,6 +50,26 @@ def test_n2048_f64(H, oracle, comp):
     assert np.linalg.norm(Cd - DCo) <= 1.5e-6 * np.linalg.norm(DCo)
 
 
+def test_aca_steps_match_oracle(H, oracle):
+    """The device cross approximation takes the oracle's steps: on the N = 2048 FP64 product the
+    crosses summed over all far blocks (the library's sample_passes) match those of the oracle's
+    Algorithm 6 run on the exact dense blocks with the same pivoting and stop rule (two
+    consecutive crosses at eps/8); a pivot can differ only where two entries tie to rounding."""
+    from oracle import compressors as X
+    P = inputs.points(0, 2, 2048, 0)
+    T, Ao, _ = _oracle_pair(oracle, P, 32, 1.0, 0, 0, 1e-10)
+    A = H.hmat_build(P, 0, leaf_size=32, eta=1.0, aca_eps=1e-10)
+    eps = 1e-6
+    C = H.hmat_multiply(A, A, eps, mode=H.MODE_F64, compressor=H.COMP_ACA)
+    DC = oracle.matmul(Ao.dense(), Ao.dense())
+    total = 0
+    for l in range(T.nleaf):
+        if T.leaf_blocks[l, 2] == 1:
+            r0, m, c0, n = T.leaf_ranges(l)
+            total += X.aca(DC[r0:r0 + m, c0:c0 + n], eps / 8, 95)[2]
+    assert abs(C.stats()["sample_passes"] - total) <= 0.01 * total, (C.stats()["sample_passes"], total)
+
+
 @pytest.mark.parametrize("comp", COMPRESSORS)
 @pytest.mark.parametrize("eps", [1e-4, 1e-8])
 def test_3d_two_kernels(H, oracle, eps, comp):

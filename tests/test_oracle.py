@@ -412,3 +412,114 @@ def test_mlp_target_round_trip():
     r = np.array([0, 1, 3, 7, 15, 96, -2], np.float64)
     np.testing.assert_allclose(R.predicted_rank(R.target(r)), np.maximum(r, 0), atol=1e-12)
     assert R.target(np.array([0.0]))[0] == 0.0 and R.target(np.array([3.0]))[0] == 2.0
+
+
+# ---------------------------------------------------------------- one-vector compressors (Sec. 4)
+
+def _lowrank(seed, m, n, r):
+    u = inputs.uniform01(seed, m * r).reshape(m, r) - 0.5
+    v = inputs.uniform01(seed + 1, n * r).reshape(n, r) - 0.5
+    return u @ v.T
+
+
+def test_aca_interpolates_pivots_and_recovers_low_rank():
+    """Algorithm 6: the cross approximation reproduces D exactly on every pivot row and column
+    (the Schur complement vanishes there), and a rank-5 matrix exactly after 5 crosses (the
+    next crosses are rounding noise). A dropped correction term or a transposed index breaks
+    both."""
+    from oracle import compressors as X
+    D = _lowrank(31, 40, 30, 5)
+    L, U, k = X.aca(D, 1e-14, 50)
+    assert 5 <= k <= 7
+    assert np.linalg.norm(D - L @ U.T) <= 1e-12 * np.linalg.norm(D)
+    # a full-rank matrix stopped early: exact on the pivot rows and columns only
+    G = inputs.uniform01(33, 24 * 20).reshape(24, 20)
+    L, U, k = X.aca(G, 0.2, 50, need=1)
+    assert 1 <= k < 20
+    R = G - L @ U.T
+    rows = [i for i in range(24) if np.abs(L[i, :]).max() > 0 and np.abs(R[i, :]).max() <= 1e-12]
+    cols = [j for j in range(20) if np.abs(R[:, j]).max() <= 1e-12]
+    assert len(rows) >= k and len(cols) >= k
+    # u_r is 1 at its pivot column and 0 at earlier pivot columns (unit triangular structure)
+    piv = [int(np.flatnonzero(np.isclose(U[:, r], 1.0))[0]) for r in range(k)]
+    for r in range(k):
+        assert abs(U[piv[r], r] - 1.0) <= 1e-14
+        for s in range(r):
+            assert abs(U[piv[s], r]) <= 1e-12
+
+
+def test_aca_skips_zero_row():
+    """An exactly zero first row is marked used and the next unused row starts the crosses."""
+    from oracle import compressors as X
+    D = _lowrank(35, 20, 16, 3)
+    D[0, :] = 0.0
+    L, U, k = X.aca(D, 1e-14, 30)
+    assert np.linalg.norm(D - L @ U.T) <= 1e-12 * np.linalg.norm(D)
+    Z = np.zeros((6, 5))
+    L, U, k = X.aca(Z, 1e-6, 10)
+    assert k == 0 and L.shape == (6, 0)
+
+
+def test_lanczos_bidiagonal_form():
+    """Algorithm 7: Q and W orthonormal and Q^T D W_k upper bidiagonal with alpha on the diagonal
+    and beta above it; run to full length, the singular values of that bidiagonal matrix are
+    D's (numpy's SVD)."""
+    from oracle import compressors as X
+    D = inputs.uniform01(41, 18 * 12).reshape(18, 12) - 0.3
+    w1 = inputs.uniform01(42, 12) - 0.5
+    Q, W, a, b, k = X.lanczos(D, w1, 0.0, 100)
+    assert k == 12
+    assert np.abs(Q.T @ Q - np.eye(k)).max() <= 1e-12
+    Wk = W[:, :k]
+    assert np.abs(Wk.T @ Wk - np.eye(k)).max() <= 1e-12
+    Bm = Q.T @ D @ Wk
+    ref = np.diag(a) + np.diag(b[:k - 1], 1)
+    assert np.abs(Bm - ref).max() <= 1e-12 * np.abs(D).max()
+    sv = np.linalg.svd(ref, compute_uv=False)
+    assert np.allclose(sv, np.linalg.svd(D, compute_uv=False), rtol=1e-12, atol=1e-12)
+    # a rank-4 matrix: the Krylov space is exhausted after 4 steps and Q Q^T D = D
+    R4 = _lowrank(43, 30, 25, 4)
+    Q, W, a, b, k = X.lanczos(R4, inputs.uniform01(44, 25) - 0.5, 1e-12, 100)
+    assert 4 <= k <= 6 and a[4] <= 1e-10 * a[0]
+    assert np.linalg.norm(R4 - Q @ (Q.T @ R4)) <= 1e-12 * np.linalg.norm(R4)
+
+
+def test_truncate_is_eckart_young():
+    """Algorithm 5: the truncated L U^T has the eps-rank of L U^T and its error is the tail of
+    the singular values (numpy's SVD of the product)."""
+    from oracle import compressors as X
+    L = inputs.uniform01(51, 40 * 9).reshape(40, 9) - 0.5
+    U = (inputs.uniform01(52, 30 * 9).reshape(30, 9) - 0.5) * (0.1 ** np.arange(9))
+    M = L @ U.T
+    s = np.linalg.svd(M, compute_uv=False)
+    for eps in (1e-1, 1e-3, 1e-6):
+        A, B = X.truncate(L, U, eps)
+        k = A.shape[1]
+        tail = np.sqrt(np.cumsum((s * s)[::-1])[::-1])
+        kref = int(np.argmax(tail <= eps * tail[0])) if np.any(tail <= eps * tail[0]) else len(s)
+        assert k == kref
+        assert abs(np.linalg.norm(M - A @ B.T) - np.sqrt(np.sum(s[k:] ** 2))) <= 1e-12 * np.linalg.norm(M)
+
+
+def test_compressors_meet_bound_on_product_blocks(oracle):
+    """The stop rule (two consecutive steps meeting eq. (truncaca) at eps/8) followed by the
+    truncation meets the blockwise bound 1.5 eps with rank <= k_eps + 2 on the exact far blocks
+    of a 3-D product (e^{-r} times 1/(1+r^2))."""
+    from oracle import compressors as X
+    from parity_util import _oracle_pair
+    P = inputs.points(0, 3, 2000, 5)
+    T, Ao, Bo = _oracle_pair(oracle, P, 32, 1.0, 0, 1, 1e-10)
+    DC = oracle.matmul(Ao.dense(), Bo.dense())
+    eps = 1e-6
+    far = [l for l in range(T.nleaf) if T.leaf_blocks[l, 2] == 1]
+    assert len(far) > 500
+    for l in far:
+        r0, m, c0, n = T.leaf_ranges(l)
+        blk = DC[r0:r0 + m, c0:c0 + n]
+        tr = oracle.truth_for_block(blk, eps, l)
+        L, U, _ = X.aca(blk, eps / 8, 95)
+        Q, _, _, _, _ = X.lanczos(blk, inputs.uniform01(l, n) - 0.5, eps / 8, 95)
+        for A, B in (X.truncate(L, U, eps), X.truncate(Q, blk.T @ Q, eps)):
+            err = np.linalg.norm(blk - A @ B.T) / tr.norm
+            assert err <= 1.5 * eps, (l, err)
+            assert A.shape[1] <= tr.k_eps + 2, (l, A.shape[1], tr.k_eps)

@@ -7,7 +7,8 @@
  * matrix product": the product L = HK is written as the sum-expression S(I,I) = HK
  * (Sec. 3.1), restricted block by block (Algorithm 3) and, at every leaf, either truncated
  * to low rank (far leaves, operator T of Algorithm 4, realised by the blocked adaptive
- * randomized range finder of Algorithm 8 with the stop test eq. (truncaca)) or evaluated
+ * randomized range finder of Algorithm 8 with the stop test eq. (truncaca), or on request by
+ * cross approximation, Algorithm 6, or Lanczos bidiagonalization, Algorithm 7) or evaluated
  * densely (near leaves, evaluate() of Algorithm 4).
  *
  * Conventions for every entry point:
@@ -147,7 +148,7 @@ typedef struct {
   int64_t n_terms;               /* low-rank products created by the restriction (a2) */
   int64_t n_lr_refs;             /* sum over leaves of their low-rank term counts */
   int64_t n_hpairs;              /* sum over leaves of their H-pair counts */
-  int rounds;                    /* adaptive rounds run */
+  int rounds;                    /* adaptive rounds run (cross approximation / Lanczos: steps) */
   int64_t not_converged;         /* far blocks that hit max_rank or max_rounds */
   double flops_apply;            /* algorithmic flops of the sum-expression applications */
   double flops_terms;            /* algorithmic flops of the low-rank products (a2) */
@@ -165,7 +166,8 @@ typedef struct {
   int64_t n_panels;              /* panels of products with one inadmissible factor */
   int64_t first_round_cols;      /* columns sampled in the first round, summed over far blocks */
   int64_t done_in_first_round;   /* far blocks whose stop test held in the first round */
-  int64_t sample_passes;         /* sum over far blocks of the rounds each one took part in */
+  int64_t sample_passes;         /* sum over far blocks of the rounds each one took part in
+                                    (cross approximation: crosses; Lanczos: steps) */
   int64_t groups;                /* subtree groups the product ran in (1: one pass) */
 } hmat_stats_t;
 

@@ -189,6 +189,25 @@ hmat_status hmat_build(const double *xyz, int64_t n, int dim, hmat_kernel kernel
                        const hmat_build_opts *opts, const hmat_t tree_from, void *stream,
                        hmat_t *out);
 
+/* The structure hmat_build and hmat_multiply would use on these points, computed on the host
+ * alone (no device memory, no stream, no GPU needed): the cluster tree by cardinality-balanced
+ * bisection (Def. 2.2), the block tree by Algorithm 1 with eta-admissibility (Def. 2.3), and
+ * the symbolic restriction of S(I,I) = HK down the whole block tree (Algorithm 3, as Algorithm 4
+ * recurses). xyz: n x dim, row-major, original order, host. Outputs, host, caller-owned, each
+ * may be NULL:
+ *   perm[n]            perm[i] = original index of permuted position i (as hmat_permutation);
+ *   *n_leaves          leaves of the block tree;
+ *   leaves[max_leaves] the first min(max_leaves, *n_leaves) leaves in depth-first order, as
+ *                      hmat_leaf_info gives them before factors exist (far: rank 0, near: -1);
+ *   n_lowrank[max_leaves], n_hpairs[max_leaves]  per leaf, the low-rank terms and H-pairs of
+ *                      its sum-expression (as hmat_sumexpr_counts);
+ *   *csp               C_sp, the largest number of blocks sharing one row cluster.
+ * EINVAL on NULL xyz, n < 1, dim outside 1..3, leaf_size outside 1..128, eta <= 0 or a
+ * non-finite coordinate. */
+hmat_status hmat_plan_host(const double *xyz, int64_t n, int dim, int leaf_size, double eta, int64_t *perm,
+                           int64_t *n_leaves, hmat_leaf *leaves, int64_t *n_lowrank, int64_t *n_hpairs,
+                           int64_t max_leaves, int *csp);
+
 /* C ~= A B with every far block of C the eps-approximation of its sum-expression
  * (Algorithm 4 with the truncation operator of Algorithm 8 + eq. (truncaca), then an FP64
  * eigen-truncation of the sampled core to relative Frobenius error eps) and every near

@@ -961,6 +961,49 @@ hmat_status hmat_rankmodel_grad_noalloc(const hmat_rankmodel_t m, const float *f
 
 void hmat_rankmodel_destroy(hmat_rankmodel_t m) { delete m; }
 
+hmat_status hmat_plan_host(const double *xyz, int64_t n, int dim, int leaf_size, double eta, int64_t *perm,
+                           int64_t *n_leaves, hmat_leaf *leaves, int64_t *n_lowrank, int64_t *n_hpairs,
+                           int64_t max_leaves, int *csp) {
+  return guard([&] {
+    if (!xyz) fail(HMAT_EINVAL, "NULL argument");
+    if (n < 1 || dim < 1 || dim > 3) fail(HMAT_EINVAL, "need n >= 1 and dim in 1..3");
+    if (leaf_size < 1 || leaf_size > 128) fail(HMAT_EINVAL, "leaf_size must be in 1..128");
+    if (!(eta > 0.0)) fail(HMAT_EINVAL, "eta must be > 0");
+    if (max_leaves < 0) fail(HMAT_EINVAL, "max_leaves must be >= 0");
+    for (int64_t i = 0; i < n * dim; i++)
+      if (!std::isfinite(xyz[i])) fail(HMAT_EINVAL, "non-finite point coordinate");
+    std::shared_ptr<Tree> tp = build_tree(xyz, n, dim, leaf_size, eta);
+    if (!tp) fail(HMAT_EINVAL, "tree construction failed");
+    const Tree &t = *tp;
+    const std::vector<LeafDev> lv = base_leaves(t);
+    const int64_t nl = (int64_t)lv.size();
+    if (perm) std::copy(t.perm.begin(), t.perm.end(), perm);
+    if (n_leaves) *n_leaves = nl;
+    if (csp) *csp = t.csp;
+    const int64_t k = std::min(max_leaves, nl);
+    if (leaves)
+      for (int64_t l = 0; l < k; l++) {
+        leaves[l].row_begin = lv[l].row;
+        leaves[l].row_size = lv[l].m;
+        leaves[l].col_begin = lv[l].col;
+        leaves[l].col_size = lv[l].n;
+        leaves[l].level = lv[l].level;
+        leaves[l].far = lv[l].rank >= 0 ? 1 : 0;
+        leaves[l].rank = lv[l].rank;
+      }
+    if ((n_lowrank || n_hpairs) && k > 0) {
+      std::vector<int32_t> rk(lv.size());
+      for (size_t l = 0; l < lv.size(); l++) rk[l] = lv[l].rank;  // the counts do not depend on ranks
+      Plan plan;
+      build_plan(t, rk, rk, plan);
+      for (int64_t l = 0; l < k; l++) {
+        if (n_lowrank) n_lowrank[l] = plan.nterm_cum[t.leaf_block[l]];
+        if (n_hpairs) n_hpairs[l] = plan.leaf_pair_off[l + 1] - plan.leaf_pair_off[l];
+      }
+    }
+  });
+}
+
 hmat_status hmat_sumexpr_counts(const hmat_t A, const hmat_t B, int64_t *n_lowrank, int64_t *n_hpairs) {
   return guard([&] {
     if (!A || !B || !n_lowrank || !n_hpairs) fail(HMAT_EINVAL, "NULL argument");

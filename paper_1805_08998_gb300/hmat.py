@@ -26,7 +26,8 @@ MODE_F64, MODE_MIXED = 0, 1
 COMP_RANDOMIZED, COMP_ACA, COMP_LANCZOS = 0, 1, 2
 
 # every symbol include/hmat.h declares
-EXPORTS = ["hmat_points", "hmat_build", "hmat_multiply", "hmat_multiply_batched", "hmat_to_dense", "hmat_leaf_count", "hmat_leaf_info",
+EXPORTS = ["hmat_points", "hmat_build", "hmat_plan_host", "hmat_multiply", "hmat_multiply_batched", "hmat_to_dense",
+           "hmat_leaf_count", "hmat_leaf_info",
            "hmat_leaf_get", "hmat_permutation", "hmat_stats", "hmat_sumexpr_counts", "hmat_destroy",
            "hmat_data_bytes", "hmat_data_get", "hmat_rank_features", "hmat_rankmodel_train",
            "hmat_rankmodel_predict", "hmat_rankmodel_get", "hmat_rankmodel_create", "hmat_rankmodel_grad",
@@ -115,6 +116,8 @@ def lib():
     L.hmat_permutation.argtypes = [_P, _PI64]
     L.hmat_stats.argtypes = [_P, ctypes.POINTER(Stats)]
     L.hmat_sumexpr_counts.argtypes = [_P, _P, _PI64, _PI64]
+    L.hmat_plan_host.argtypes = [_PD, _I64, ctypes.c_int, ctypes.c_int, ctypes.c_double, _PI64, _PI64,
+                                 ctypes.POINTER(Leaf), _PI64, _PI64, _I64, ctypes.POINTER(ctypes.c_int)]
     L.hmat_data_bytes.argtypes = [_P, _PI64]
     L.hmat_data_get.argtypes = [_P, _P, _I64]
     L.hmat_rank_features.argtypes = [_P, _P, ctypes.c_double, _P, _PF, _PF, _PI64]
@@ -131,7 +134,7 @@ def lib():
     L.hmat_destroy.argtypes = [_P]
     L.hmat_destroy.restype = None
     L.hmat_last_error.restype = ctypes.c_char_p
-    for name in ["hmat_points", "hmat_build", "hmat_multiply", "hmat_multiply_batched", "hmat_to_dense",
+    for name in ["hmat_points", "hmat_build", "hmat_plan_host", "hmat_multiply", "hmat_multiply_batched", "hmat_to_dense",
                  "hmat_leaf_count",
                  "hmat_leaf_info", "hmat_leaf_get", "hmat_permutation", "hmat_stats", "hmat_sumexpr_counts",
                  "hmat_set_allocator", "hmat_data_bytes", "hmat_data_get", "hmat_rank_features",
@@ -302,6 +305,39 @@ def hmat_product_error(A: HMatrix, B: HMatrix, C: HMatrix, iters: int = 10, size
     out = ctypes.c_double()
     _check(lib().hmat_product_error(A.handle, B.handle, C.handle, iters, size, seed, ctypes.byref(out)))
     return out.value
+
+
+@dataclass
+class PlanHost:
+    perm: np.ndarray
+    leaves: "LeafArrays"
+    n_lowrank: np.ndarray
+    n_hpairs: np.ndarray
+    csp: int
+
+
+def hmat_plan_host(points, leaf_size: int = 64, eta: float = 1.0) -> PlanHost:
+    """Cluster tree, block tree and per-leaf sum-expression counts on the host (no GPU)."""
+    P = np.ascontiguousarray(points, np.float64)
+    if P.ndim == 1:
+        P = P[:, None]
+    n, dim = P.shape
+    L = lib()
+    nl = ctypes.c_int64()
+    _check(L.hmat_plan_host(P.ctypes.data_as(_PD), n, dim, leaf_size, eta, None, ctypes.byref(nl), None, None,
+                            None, 0, None))
+    k = nl.value
+    perm = np.zeros(n, np.int64)
+    lv = (Leaf * max(k, 1))()
+    lr = np.zeros(k, np.int64)
+    hp = np.zeros(k, np.int64)
+    csp = ctypes.c_int()
+    _check(L.hmat_plan_host(P.ctypes.data_as(_PD), n, dim, leaf_size, eta, perm.ctypes.data_as(_PI64),
+                            ctypes.byref(nl), lv, lr.ctypes.data_as(_PI64), hp.ctypes.data_as(_PI64), k,
+                            ctypes.byref(csp)))
+    cols = {f: np.array([getattr(lv[i], f) for i in range(k)], np.int64)
+            for f in ("row_begin", "row_size", "col_begin", "col_size", "level", "far", "rank")}
+    return PlanHost(perm, LeafArrays(**cols), lr, hp, int(csp.value))
 
 
 def hmat_sumexpr_counts(A: HMatrix, B: HMatrix):

@@ -94,3 +94,48 @@ def test_last_error_is_thread_local(H):
     th.start()
     th.join()
     assert msg_main and seen["t"] == ""
+
+
+@pytest.mark.parametrize("kind,dim,n,leaf,eta", [(0, 2, 2048, 32, 1.0), (1, 3, 3000, 32, 1.0), (0, 3, 1531, 16, 1.0),
+                                                 (0, 1, 777, 8, 0.5), (0, 2, 300, 16, 2.0), (0, 3, 1, 4, 1.0)])
+def test_plan_host_matches_oracle(H, oracle, kind, dim, n, leaf, eta):
+    """a0/a1 host logic without a GPU: the library's cluster tree (Def. 2.2), block tree
+    (Algorithm 1, Def. 2.3) and restriction plan (Algorithm 3) give, bit for bit, the oracle's
+    permutation, leaf geometry, admissibility, levels, C_sp and per-leaf counts of low-rank terms
+    and H-pairs."""
+    P = inputs.points(kind, dim, n, 11)
+    T = oracle.Tree(P, leaf, eta)
+    ph = H.hmat_plan_host(P, leaf_size=leaf, eta=eta)
+    assert np.array_equal(ph.perm, T.perm)
+    la = ph.leaves
+    assert len(la.far) == T.nleaf
+    ref = np.array([T.leaf_ranges(l) for l in range(T.nleaf)])
+    assert np.array_equal(la.row_begin, ref[:, 0]) and np.array_equal(la.row_size, ref[:, 1])
+    assert np.array_equal(la.col_begin, ref[:, 2]) and np.array_equal(la.col_size, ref[:, 3])
+    assert np.array_equal(la.far, (T.leaf_blocks[:, 2] == 1).astype(np.int64))
+    assert np.array_equal(la.level, T.leaf_blocks[:, 3])
+    assert np.array_equal(la.rank, np.where(la.far == 1, 0, -1))
+    assert ph.csp == T.csp()
+    lr, hp, _ = T.sumexpr_counts()
+    assert np.array_equal(ph.n_lowrank, lr) and np.array_equal(ph.n_hpairs, hp)
+
+
+def test_plan_host_arguments(H):
+    P = inputs.points(0, 2, 100, 0)
+    L = H.lib()
+    for args in [(None, 100, 2, 16, 1.0), (P, 0, 2, 16, 1.0), (P, 100, 4, 16, 1.0), (P, 100, 2, 0, 1.0),
+                 (P, 100, 2, 16, 0.0), (P, 100, 2, 16, float("nan"))]:
+        pts, n, dim, leaf, eta = args
+        ptr = pts.ctypes.data_as(H._PD) if pts is not None else None
+        assert L.hmat_plan_host(ptr, n, dim, leaf, eta, None, None, None, None, None, 0, None) == H.HMAT_EINVAL
+    bad = P.copy()
+    bad[7, 0] = np.inf
+    assert L.hmat_plan_host(bad.ctypes.data_as(H._PD), 100, 2, 16, 1.0, None, None, None, None, None, 0,
+                            None) == H.HMAT_EINVAL
+    # a partial leaf buffer: only the first max_leaves entries are written
+    full = H.hmat_plan_host(P, leaf_size=8)
+    lr = np.full(5, -7, np.int64)
+    nl = ctypes.c_int64()
+    assert L.hmat_plan_host(P.ctypes.data_as(H._PD), 100, 2, 8, 1.0, None, ctypes.byref(nl), None,
+                            lr[:3].ctypes.data_as(H._PI64), None, 3, None) == H.HMAT_OK
+    assert nl.value == len(full.n_lowrank) and np.array_equal(lr[:3], full.n_lowrank[:3]) and np.all(lr[3:] == -7)

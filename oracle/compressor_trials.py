@@ -8,7 +8,9 @@ to each far leaf), runs the cross approximation (Algorithm 6) and the Lanczos bi
 truncates the result to the eps-rank (Algorithm 5), and prints per reading how many blocks miss
 the blockwise bound (error > 1.5 eps or rank > k_eps + 2), the worst error / eps and the mean
 number of steps. The readings: one step meeting the test at eps/4, eps/10 or eps/32, or two
-consecutive steps at eps/4 or eps/8. Uses only the oracle and the seeded point generator.
+consecutive steps at eps/4 or eps/8. For comparison it also runs the blocked randomized range
+finder (Algorithm 8: 8 columns per round, stop at eps/2, dropping at 0.1 eps) and reports its
+rounds. Uses only the oracle, the seeded point generator and numpy's seeded Gaussians.
 """
 from __future__ import annotations
 
@@ -54,6 +56,19 @@ def main():
                 r0, m, c0, nn = T.leaf_ranges(l)
                 blk = DC[r0:r0 + m, c0:c0 + nn]
                 blocks.append((l, blk, O.truth_for_block(blk, eps, l)))
+        rng = np.random.default_rng(7)
+        fails, worst, rounds = 0, 0.0, []
+        for l, blk, tr in blocks:
+            om = rng.standard_normal((blk.shape[1], 96))
+            Q, W, rd = X.randomized(blk, om, eps, 8, 96)
+            Uc, Vc = X.truncate(Q, W, eps)
+            err = np.linalg.norm(blk - Uc @ Vc.T) / tr.norm
+            worst = max(worst, err / eps)
+            rounds.append(rd)
+            if err > 1.5 * eps or Uc.shape[1] > tr.k_eps + 2:
+                fails += 1
+        print(f"{label:22s} N={n:5d} eps={eps:.0e} {'random':8s} {'8 per round':14s}: {fails:2d} of {len(blocks)} "
+              f"blocks miss the bound, worst {worst:.2f} eps, mean rounds {np.mean(rounds):.1f}", flush=True)
         for comp in ("aca", "lanczos"):
             for name, fac, need in RULES:
                 fails, worst, steps = 0, 0.0, []

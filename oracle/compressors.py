@@ -1,9 +1,9 @@
-"""FP64 reference of the one-vector compressors of a block -- test infrastructure only.
+"""FP64 reference of the compressors of a block (Sec. 4) -- test infrastructure only.
 
 Only the tests and the trials script beside this file use this module; the library never calls
 it, and the two share no code. Each routine takes an explicit dense block D (m x n) and sees it
-only through the products the paper allows a compressor: a row e_i^T D, a column D e_j, or D w
-and D^T q.
+only through the products the paper allows a compressor: a row e_i^T D, a column D e_j, or
+products D X and D^T Y with vectors or blocks of vectors. Random numbers are inputs (omega, w1).
 
   aca(D, eps_stop, kcap, need)
       Algorithm 6 (Sec. 4.1) with partial pivoting: first pivot row 0; the column pivot is the
@@ -19,6 +19,17 @@ and D^T q.
       q_r (alpha_r w_r + beta_r w_{r+1})^T (one step of lookahead), of norm
       sqrt(alpha_r^2 + beta_r^2); stop once `need` consecutive steps meet eq. (truncaca) against
       sum_{s<r} (alpha_s^2 + beta_s^2), or at alpha_r = 0, beta_r = 0, min(m, n) or kcap steps.
+  randomized(D, omega, eps, p, rmax)
+      Algorithm 8 (Sec. 4.3) in its blocked form: each round samples Y = D Omega_round (the next
+      p columns of omega), projects Y twice against the basis Q, orthonormalizes the new columns
+      by Gram-Schmidt applied twice and drops a column whose remaining norm is at most
+      0.1 eps ||D||_est (||D||_est^2 = ||Y_0||_F^2 / p from the first round), and appends
+      W_new = D^T Q_new. It stops when ||W_new||_F <= (eps/2) ||W_old||_F (eq. (truncaca) with the
+      block's energy), when no column is kept, when Q has min(m, n) columns, or when the next round
+      would pass rmax columns. Returns (Q, W = D^T Q, rounds).
+  fixed_rank(D, omega, q)
+      Algorithm 9 (Sec. 4.4): L = orth(D Omega) with k = omega's columns, then q times
+      U = orth(D^T L), L = orth(D U); finally U = D^T L. Returns (L, U), so D ~ L U^T with rank <= k.
   truncate(L, U, eps)
       Algorithm 5 (Sec. 4): QR of both factors, SVD of the small core, and the eps-rank of the
       core (smallest k with relative Frobenius tail <= eps), giving the best approximation of
@@ -28,7 +39,11 @@ Pins (tests/test_oracle.py): ACA reproduces the pivot rows and columns exactly (
 interpolation property) and a matrix of rank r after r crosses; it skips a zero first row;
 Lanczos gives orthonormal Q and W with Q^T D W upper bidiagonal (alpha on the diagonal, beta
 above it), and run to full length the singular values of that bidiagonal are those of D (numpy's
-SVD); truncate's error equals the tail of numpy's singular values of L U^T.
+SVD); the randomized range finder captures a rank-r matrix exactly in r orthonormal columns,
+dropping the rest, and on geometrically decaying singular values its truncated result meets
+1.5 eps at rank <= k_eps + 2 (numpy's SVD); the fixed-rank scheme returns rank <= k and, with a
+spectral gap after k, comes within 1 % of the best rank-k error (numpy's SVD tail); truncate's
+error equals the tail of numpy's singular values of L U^T.
 """
 from __future__ import annotations
 
@@ -128,6 +143,65 @@ def lanczos(D: np.ndarray, w1: np.ndarray, eps_stop: float, kcap: int, need: int
     Q = np.array(Qs).T if Qs else np.zeros((m, 0))
     W = np.array(Ws).T
     return Q, W, np.array(alphas), np.array(betas), len(Qs)
+
+
+def _gs2_drop(Y: np.ndarray, drop: float) -> np.ndarray:
+    """Gram-Schmidt applied twice to the columns of Y in order; a column whose remaining norm is
+    at most `drop` is left out. Returns the kept orthonormal columns."""
+    kept = []
+    for j in range(Y.shape[1]):
+        v = _orth2(Y[:, j].copy(), kept)
+        nv = float(np.linalg.norm(v))
+        if nv > drop:
+            kept.append(v / nv)
+    return np.array(kept).T if kept else np.zeros((Y.shape[0], 0))
+
+
+def randomized(D: np.ndarray, omega: np.ndarray, eps: float, p: int, rmax: int):
+    """Blocked adaptive range finder of D with the Gaussian columns omega (n x >= rounds * p)."""
+    D = np.asarray(D, np.float64)
+    m, n = D.shape
+    Q = np.zeros((m, 0))
+    W = np.zeros((n, 0))
+    est = None
+    rounds = 0
+    while True:
+        Om = omega[:, rounds * p:(rounds + 1) * p]
+        if Om.shape[1] < p:
+            break
+        rounds += 1
+        Y = D @ Om
+        if est is None:
+            est = np.sqrt(float(np.sum(Y * Y)) / p)
+        for _ in range(2):
+            Y = Y - Q @ (Q.T @ Y)
+        Qn = _gs2_drop(Y, 0.1 * eps * est)
+        if Qn.shape[1] == 0:
+            break
+        Wn = D.T @ Qn
+        old2 = float(np.sum(W * W))
+        new2 = float(np.sum(Wn * Wn))
+        Q = np.hstack([Q, Qn])
+        W = np.hstack([W, Wn])
+        if new2 <= (0.5 * eps) ** 2 * old2:
+            break
+        if Q.shape[1] >= min(m, n) or Q.shape[1] + p > rmax:
+            break
+    return Q, W, rounds
+
+
+def _orthonormal(Y: np.ndarray) -> np.ndarray:
+    return _gs2_drop(Y, 0.0)
+
+
+def fixed_rank(D: np.ndarray, omega: np.ndarray, q: int):
+    """Rank-k approximation L U^T of D (k = omega's columns) with q subspace iterations."""
+    D = np.asarray(D, np.float64)
+    L = _orthonormal(D @ omega)
+    for _ in range(q):
+        U = _orthonormal(D.T @ L)
+        L = _orthonormal(D @ U)
+    return L, D.T @ L
 
 
 def truncate(L: np.ndarray, U: np.ndarray, eps: float):

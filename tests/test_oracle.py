@@ -523,3 +523,49 @@ def test_compressors_meet_bound_on_product_blocks(oracle):
             err = np.linalg.norm(blk - A @ B.T) / tr.norm
             assert err <= 1.5 * eps, (l, err)
             assert A.shape[1] <= tr.k_eps + 2, (l, A.shape[1], tr.k_eps)
+
+
+def _with_singular_values(seed, m, n, s):
+    """A matrix U diag(s) V^T with orthonormal U, V from seeded uniforms (numpy QR)."""
+    U, _ = np.linalg.qr(inputs.uniform01(seed, m * len(s)).reshape(m, len(s)) - 0.5)
+    V, _ = np.linalg.qr(inputs.uniform01(seed + 1, n * len(s)).reshape(n, len(s)) - 0.5)
+    return (U * s) @ V.T
+
+
+def test_randomized_range_finder():
+    """Algorithm 8, blocked: a rank-5 matrix is captured in one round by exactly 5 orthonormal
+    columns (the other 3 samples fall below the drop threshold), and the next round keeps none;
+    on singular values 2^-i the truncated result meets 1.5 eps at rank <= k_eps + 2."""
+    from oracle import compressors as X
+    D = _lowrank(61, 40, 30, 5)
+    om = np.random.default_rng(62).standard_normal((30, 24))
+    Q, W, rounds = X.randomized(D, om, 1e-10, 8, 64)
+    assert Q.shape[1] == 5 and rounds == 2
+    assert np.abs(Q.T @ Q - np.eye(5)).max() <= 1e-13
+    assert np.linalg.norm(D - Q @ W.T) <= 1e-12 * np.linalg.norm(D)
+    s = 2.0 ** -np.arange(30)
+    G = _with_singular_values(63, 50, 40, s)
+    om = np.random.default_rng(64).standard_normal((40, 80))
+    for eps in (1e-2, 1e-4, 1e-7):
+        Q, W, _ = X.randomized(G, om, eps, 8, 80)
+        A, B = X.truncate(Q, W, eps)
+        tail = np.sqrt(np.cumsum((s * s)[::-1])[::-1])
+        k_eps = int(np.argmax(tail <= eps * tail[0]))
+        err = np.linalg.norm(G - A @ B.T) / np.linalg.norm(G)
+        assert err <= 1.5 * eps and A.shape[1] <= k_eps + 2, (eps, err, A.shape[1], k_eps)
+
+
+def test_fixed_rank_subspace_iteration():
+    """Algorithm 9: rank <= k, and with a spectral gap after k (singular values 1..0.5, then
+    1e-4 and below) one subspace iteration comes within 1 % of the best rank-k error."""
+    from oracle import compressors as X
+    s = np.concatenate([np.linspace(1.0, 0.5, 6), 1e-4 * 0.5 ** np.arange(20)])
+    G = _with_singular_values(71, 60, 45, s)
+    om = np.random.default_rng(72).standard_normal((45, 6))
+    best = np.sqrt(np.sum(s[6:] ** 2))
+    for q in (1, 2):
+        L, U = X.fixed_rank(G, om, q)
+        assert L.shape[1] <= 6
+        assert np.abs(L.T @ L - np.eye(L.shape[1])).max() <= 1e-12
+        err = np.linalg.norm(G - L @ U.T)
+        assert best <= err * (1 + 1e-12) and err <= 1.01 * best, (q, err, best)

@@ -12,6 +12,10 @@
 //   k_orth          project the new samples against the basis twice and orthonormalise them by
 //                   Gram-Schmidt twice with dropping, all in FP64 (the projection step of Alg. 8)
 //   k_absorb_w      append W_new = S^T Q_new and apply the blocked stop test eq. (truncaca)
+//   k_aca_*         the cross approximation compressor (Alg. 6) on the sum-expressions: start,
+//                   row step (pivot column), column step (stop test, next pivot row), QR of L
+//   k_lz_*          the Lanczos bidiagonalization compressor (Alg. 7): start vector, q step,
+//                   w step (stop test), and the projection W = S^T Q in column blocks
 //   k_final         core truncation: eigen-decomposition of W^T W (Jacobi, FP64), eps-rank,
 //                   U = Q V_k, V = W V_k (the small SVD of Algorithm 5 on the sampled core)
 //   k_write_far     copy the truncated factors into the output H-matrix

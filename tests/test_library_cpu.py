@@ -139,3 +139,24 @@ def test_plan_host_arguments(H):
     assert L.hmat_plan_host(P.ctypes.data_as(H._PD), 100, 2, 8, 1.0, None, ctypes.byref(nl), None,
                             lr[:3].ctypes.data_as(H._PI64), None, 3, None) == H.HMAT_OK
     assert nl.value == len(full.n_lowrank) and np.array_equal(lr[:3], full.n_lowrank[:3]) and np.all(lr[3:] == -7)
+
+
+@pytest.mark.parametrize("kind,n", [(1, 32768), (0, 131072)])
+def test_plan_host_full_size(H, oracle, kind, n):
+    """Integer work at full size, bit-exact: the benchmark's sphere workload (N = 32768) and the
+    3-D workload of the learned proposal (N = 131072), leaf 64, eta 1: permutation, leaf
+    geometry and admissibility, C_sp and every leaf's term and H-pair counts."""
+    dim = 3
+    P = inputs.points(kind, dim, n, 0)
+    T = oracle.Tree(P, 64, 1.0)
+    ph = H.hmat_plan_host(P, leaf_size=64, eta=1.0)
+    assert np.array_equal(ph.perm, T.perm)
+    la = ph.leaves
+    assert len(la.far) == T.nleaf
+    assert np.array_equal(la.far, (T.leaf_blocks[:, 2] == 1).astype(np.int64))
+    assert np.array_equal(la.level, T.leaf_blocks[:, 3])
+    ref = np.array([T.leaf_ranges(l) for l in range(T.nleaf)])
+    assert np.array_equal(la.row_begin, ref[:, 0]) and np.array_equal(la.col_size, ref[:, 3])
+    assert ph.csp == T.csp()
+    lr, hp, _ = T.sumexpr_counts()
+    assert np.array_equal(ph.n_lowrank, lr) and np.array_equal(ph.n_hpairs, hp)

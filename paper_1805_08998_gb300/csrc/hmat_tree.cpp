@@ -8,6 +8,7 @@
 #include <atomic>
 #include <cmath>
 #include <thread>
+#include <utility>
 #include <cuda_runtime.h>
 
 namespace hm {
@@ -33,7 +34,12 @@ struct Builder {
   }
   // Every cluster above depth D splits in two (D = smallest d with ceil(n/2^d) <= leaf_size):
   // axis = longest bounding-box side (first on ties), points ordered by (coordinate, original
-  // index), first child = the first floor(size/2) of them.
+  // index), first child = the first floor(size/2) of them. Only the last split orders its
+  // points completely (that order is the one inside the leaves); a split above it only selects
+  // the floor(size/2) smallest keys, since each child orders its own points again by its own
+  // axis and its bounding box does not depend on their order. The keys are a strict total order,
+  // so the selected sets, and hence the permutation, equal those of a full sort at every level.
+  std::vector<std::pair<double, int64_t>> keys;
   int cluster(int64_t begin, int64_t size, int level) {
     const int id = (int)t.cl.size();
     t.cl.emplace_back();
@@ -52,13 +58,20 @@ struct Builder {
       }
       const double *P = t.orig.data();
       const int dim = t.dim;
-      std::sort(t.perm.begin() + begin, t.perm.begin() + begin + size, [&](int64_t a, int64_t b) {
-        const double xa = P[a * dim + axis], xb = P[b * dim + axis];
-        if (xa < xb) return true;
-        if (xa > xb) return false;
-        return a < b;
-      });
+      keys.resize(size);
+      for (int64_t i = 0; i < size; i++) {
+        const int64_t q = t.perm[begin + i];
+        keys[i] = {P[q * dim + axis], q};
+      }
+      auto less = [](const std::pair<double, int64_t> &a, const std::pair<double, int64_t> &b) {
+        if (a.first < b.first) return true;
+        if (a.first > b.first) return false;
+        return a.second < b.second;
+      };
       const int64_t h = size / 2;
+      if (level + 1 < t.depth) std::nth_element(keys.begin(), keys.begin() + h, keys.end(), less);
+      else std::sort(keys.begin(), keys.end(), less);
+      for (int64_t i = 0; i < size; i++) t.perm[begin + i] = keys[i].second;
       const int c0 = cluster(begin, h, level + 1);
       const int c1 = cluster(begin + h, size - h, level + 1);
       t.cl[id].child[0] = c0;

@@ -99,3 +99,22 @@ def check_sampled(oracle, T, Ao, Bo, C, eps, near_rtol, far, near, tol_factor=1.
         e = np.linalg.norm(D - blk) / max(np.linalg.norm(blk), 1e-300)
         assert e <= near_rtol, (l, e)
     return worst
+
+
+def read_tree_golden(path):
+    """Parse a hand-derived tree fixture of tests/golden/: the points' closed form is in its
+    header; returns (perm, counts dict, leaves dict keyed by (row_begin, row_size, col_begin,
+    col_size) -> (level, far, n_lowrank, n_hpairs, [low-rank terms created per level ...]))."""
+    perm, counts, leaves = None, {}, {}
+    for line in open(path):
+        f = line.split()
+        if not f or f[0].startswith("#"):
+            continue
+        if f[0] == "perm":
+            perm = np.array([int(x) for x in f[1:]], np.int64)
+        elif f[0] == "counts":
+            counts = {f[i]: int(f[i + 1]) for i in range(1, len(f), 2)}
+        elif f[0] == "leaf":
+            r0, m, c0, n, lev = (int(x) for x in f[1:6])
+            leaves[(r0, m, c0, n)] = (lev, f[6] == "F", int(f[7]), int(f[8]), [int(x) for x in f[9:]])
+    return perm, counts, leaves

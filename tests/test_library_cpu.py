@@ -141,6 +141,24 @@ def test_plan_host_arguments(H):
     assert nl.value == len(full.n_lowrank) and np.array_equal(lr[:3], full.n_lowrank[:3]) and np.all(lr[3:] == -7)
 
 
+def test_plan_host_matches_hand_derived_example(H):
+    """The library's trees and restriction plan against the worked example derived by hand in
+    tests/golden/tree_1d_n16_leaf2_eta1.txt (Def. 2.2, Def. 2.3, Algorithms 1 and 3)."""
+    from parity_util import read_tree_golden
+    perm, counts, leaves = read_tree_golden(os.path.join(ROOT, "tests", "golden", "tree_1d_n16_leaf2_eta1.txt"))
+    P = (((5 * np.arange(16) + 3) % 16) / 16.0).reshape(16, 1)
+    ph = H.hmat_plan_host(P, leaf_size=2, eta=1.0)
+    assert np.array_equal(ph.perm, perm)
+    assert ph.csp == counts["csp"]
+    la = ph.leaves
+    assert len(la.far) == counts["leaves"] and int(la.far.sum()) == counts["far"]
+    got = {}
+    for l in range(len(la.far)):
+        key = (int(la.row_begin[l]), int(la.row_size[l]), int(la.col_begin[l]), int(la.col_size[l]))
+        got[key] = (int(la.level[l]), bool(la.far[l]), int(ph.n_lowrank[l]), int(ph.n_hpairs[l]))
+    assert got == {k: v[:4] for k, v in leaves.items()}
+
+
 @pytest.mark.parametrize("kind,n", [(1, 32768), (0, 131072)])
 def test_plan_host_full_size(H, oracle, kind, n):
     """Integer work at full size, bit-exact: the benchmark's sphere workload (N = 32768) and the

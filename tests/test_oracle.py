@@ -5,6 +5,8 @@ index, a transposed operand, an off-by-one rank) and checks it against something
 than the oracle itself: brute force, closed forms, an independent library routine, or a
 theorem of the paper.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -92,6 +94,39 @@ def test_block_tree_partition_and_admissibility(oracle, kind, dim, n, leaf, eta)
             want = {(int(x), int(y)) for x in T.cl[tau, 3:5] for y in T.cl[sig, 3:5]}
             assert kids == want
     assert (cover == 1).all()
+
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def golden_points_1d_n16():
+    """The points of tests/golden/tree_1d_n16_leaf2_eta1.txt: x_i = ((5 i + 3) mod 16) / 16."""
+    return (((5 * np.arange(16) + 3) % 16) / 16.0).reshape(16, 1)
+
+
+def test_hand_derived_example_tree_and_counts(oracle):
+    """Def. 2.2, Def. 2.3, Algorithm 1 and Algorithm 3 against a worked example derived by hand
+    (16 points on a line, leaf 2, eta 1): permutation, block and leaf counts, C_sp, every leaf's
+    level and admissibility (including the equality case of the <= test), and its low-rank
+    terms, H-pairs and the level each low-rank term is created on. A wrong split, a strict
+    inequality, a dropped inherited term or an H-pair kept as low rank each change a line."""
+    from parity_util import read_tree_golden
+    perm, counts, leaves = read_tree_golden(os.path.join(GOLDEN, "tree_1d_n16_leaf2_eta1.txt"))
+    T = oracle.Tree(golden_points_1d_n16(), 2, 1.0)
+    assert np.array_equal(T.perm, perm)
+    assert (T.ncl, T.nbl, T.nleaf, T.depth, T.csp()) == (counts["clusters"], counts["blocks"], counts["leaves"],
+                                                         counts["depth"], counts["csp"])
+    assert len(T.far_leaves()) == counts["far"] and len(T.near_leaves()) == counts["near"]
+    lr, hp, at = T.sumexpr_counts()
+    seen = set()
+    for l in range(T.nleaf):
+        key = T.leaf_ranges(l)
+        lev, far, n_lr, n_hp, created = leaves[key]
+        seen.add(key)
+        assert int(T.leaf_blocks[l, 3]) == lev and (T.leaf_blocks[l, 2] == 1) == far, key
+        assert (int(lr[l]), int(hp[l])) == (n_lr, n_hp), key
+        assert [int(x) for x in at[l, 2:2 + len(created)]] == created and at[l, :2].sum() == 0, key
+    assert seen == set(leaves)
 
 
 def test_admissibility_symmetric(oracle):

@@ -167,11 +167,13 @@ def _traffic_from_profile():
 
 # ------------------------------------------------------------------------------------ CPU oracle
 
-def oracle_sample(n_blocks_per_level=2, seed=0, threads=None, budget_s=25.0, setup=None):
+def oracle_sample(n_blocks_per_level=2, seed=0, threads=None, budget_s=25.0, min_s=0.0, setup=None):
     """Time the oracle on a stratified sample of target blocks of the workload and extrapolate
     to the whole product: exact block C|b = A|tau x I * B|I x sigma (cost ~ m n N) plus the
     SVD truncation of far blocks (cost ~ m n min(m, n)). Returns (estimated seconds for the full
-    product, description, threads used, setup)."""
+    product, description, threads used, setup). Levels are visited in passes, n_blocks_per_level
+    new blocks of each per pass, until at least min_s seconds of oracle work are done (or the
+    candidates run out); no block starts after budget_s."""
     from oracle import oracle as O
     if threads:
         O.set_threads(threads)
@@ -192,27 +194,37 @@ def oracle_sample(n_blocks_per_level=2, seed=0, threads=None, budget_s=25.0, set
     c_prod, c_svd = [], []
     t_start = time.perf_counter()
     done = 0
+    pools = []
     for level in sorted(set(lv.tolist()), reverse=True):
         cand = np.nonzero((lv == level) & (mn <= 256 * 256))[0]
-        if len(cand) == 0:
-            continue
-        for l in rng.choice(cand, size=min(n_blocks_per_level, len(cand)), replace=False):
-            if time.perf_counter() - t_start > budget_s:
-                break
-            r0, m, c0, n = sizes[l]
-            t0 = time.perf_counter()
-            blk = O.block_product(A, B, r0, m, c0, n)
-            t1 = time.perf_counter()
-            c_prod.append((t1 - t0) / (m * n * N))
-            if far[l]:
-                O.truth_for_block(blk, W["eps"])
-                c_svd.append((time.perf_counter() - t1) / (m * n * min(m, n)))
-            done += 1
+        if len(cand):
+            pools.append(list(rng.permutation(cand)))
+    while True:
+        took = 0
+        for pool in pools:
+            for _ in range(n_blocks_per_level):
+                if not pool or time.perf_counter() - t_start > budget_s:
+                    break
+                l = pool.pop()
+                r0, m, c0, n = sizes[l]
+                t0 = time.perf_counter()
+                blk = O.block_product(A, B, r0, m, c0, n)
+                t1 = time.perf_counter()
+                c_prod.append((t1 - t0) / (m * n * N))
+                if far[l]:
+                    O.truth_for_block(blk, W["eps"])
+                    c_svd.append((time.perf_counter() - t1) / (m * n * min(m, n)))
+                done += 1
+                took += 1
+        elapsed = time.perf_counter() - t_start
+        if took == 0 or elapsed >= min_s or elapsed > budget_s:
+            break
     cp = float(np.mean(c_prod))
     cs = float(np.mean(c_svd)) if c_svd else 0.0
     svd_work = float(np.sum((mn * np.minimum(sizes[:, 1], sizes[:, 3]))[far]))
     t_est = cp * float(np.sum(mn)) * N + cs * svd_work
-    desc = (f"{done} blocks (stratified by level, m*n <= 256^2) of the N={N} product: exact block products "
+    desc = (f"{done} blocks (stratified by level, m*n <= 256^2; {time.perf_counter() - t_start:.1f} s of "
+            f"oracle work) of the N={N} product: exact block products "
             f"and SVD truncations timed, extrapolated to all {T.nleaf} leaves by cost ~ m*n*N (+ m*n*min(m,n) "
             f"for the far-block SVDs)")
     return t_est, desc, O.num_threads(), setup
@@ -226,19 +238,21 @@ def run_reference(args):
         return
     setup = None
     for w in range(args.warmup):
-        _, _, _, setup = oracle_sample(n_blocks_per_level=1, seed=100 + w, budget_s=10.0, setup=setup)
+        _, _, _, setup = oracle_sample(n_blocks_per_level=1, seed=100 + w, budget_s=5.0, setup=setup)
     vals = []
     t0 = time.perf_counter()
     desc, thr = "", 0
     for k in range(args.steps):
-        t_est, desc, thr, setup = oracle_sample(n_blocks_per_level=1, seed=k, budget_s=10.0, setup=setup)
+        t_est, desc, thr, setup = oracle_sample(n_blocks_per_level=1, seed=k, budget_s=15.0, min_s=10.0,
+                                                setup=setup)
         vals.append(WORKLOAD["n"] / t_est)
     wall = time.perf_counter() - t0
     v = float(np.median(vals))
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * WORKLOAD["n"] / v, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": WORKLOAD,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": dict(WORKLOAD, parallelism="replicas" if world > 1 else "single"),
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": thr, "kind": "oracle",
                          "sample": desc + "; one stratified sample per step"},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -366,7 +380,7 @@ def run_ours(args):
 
     if rank == 0:
         # CPU oracle baseline on the host cores (bounded sample)
-        t_est, desc, thr, _ = oracle_sample(n_blocks_per_level=2, budget_s=20.0)
+        t_est, desc, thr, _ = oracle_sample(n_blocks_per_level=2, budget_s=25.0, min_s=15.0)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",

@@ -17,7 +17,11 @@
  *     thread-local message describing the last failure on the calling thread.
  *   - Host buffers are owned by the caller. Device memory is owned by the library and is
  *     taken from the allocator set with hmat_set_allocator (default: the CUDA stream-ordered
- *     pool, cudaMallocAsync/cudaFreeAsync, on the given stream).
+ *     pool, cudaMallocAsync/cudaFreeAsync, on the given stream). Three small kinds of buffer
+ *     are taken with plain cudaMalloc instead, because they can outlive the stream they were
+ *     made on: a block tree's point and block tables (shared by every handle on that tree,
+ *     n * dim * 8 + 32 bytes per block), a rank model's weights (about 30 KB) and the
+ *     optimizer state of hmat_rankmodel_train (freed before it returns).
  *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream). Work is
  *     enqueued on it; calls that read results back to the host synchronise it (stated per call).
  *   - Index conventions: points are given in their ORIGINAL order; internally the library
@@ -355,7 +359,11 @@ const char *hmat_last_error(void);
 
 /* Route the library's device allocations through alloc/free (both non-NULL), or restore the
  * default stream-ordered CUDA pool (both NULL). alloc(bytes, stream, ctx) returns a device
- * pointer or NULL; free(ptr, ctx) releases it. Not thread-safe against concurrent calls. */
+ * pointer or NULL; free(ptr, ctx) releases it. Covers every buffer of builds, products,
+ * matrix-vector products and error estimates (factors, plan tables, sampling buffers); not the
+ * cudaMalloc buffers listed under the conventions above. A buffer is released through the
+ * free function set when it is released, so change the allocator only while no handle made
+ * under the previous one is alive. Not thread-safe against concurrent calls. */
 hmat_status hmat_set_allocator(void *(*alloc)(size_t bytes, void *stream, void *ctx),
                                void (*free_fn)(void *ptr, void *ctx), void *ctx);
 

@@ -133,20 +133,6 @@ DevBuf upload(const std::vector<T> &v, cudaStream_t s) {
   return b;
 }
 
-// run fn(0 .. count-1) on up to 16 host threads
-template <typename F>
-void parallel_for(size_t count, F &&fn) {
-  const unsigned hw = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
-  std::atomic<size_t> next{0};
-  auto worker = [&]() {
-    for (size_t i = next++; i < count; i = next++) fn(i);
-  };
-  std::vector<std::thread> th;
-  for (unsigned k = 1; k < std::min<size_t>(hw, count); k++) th.emplace_back(worker);
-  worker();
-  for (auto &x : th) x.join();
-}
-
 double now_ms() {
   return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }

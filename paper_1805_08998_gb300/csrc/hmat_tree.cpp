@@ -324,19 +324,8 @@ void build_plan(const Tree &t, const std::vector<int32_t> &rankA, const std::vec
   if (walks.size() < 1 + ntask) walks.resize(1 + ntask);
   for (size_t i = 0; i < ntask; i++) walks[1 + i].reset(&pt, &plan, -1, nullptr);
   const size_t nwalk = 1 + ntask;
-  const unsigned hw = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
-  auto parallel = [&](size_t count, auto &&fn) {
-    std::atomic<size_t> next{0};
-    auto worker = [&]() {
-      for (size_t i = next++; i < count; i = next++) fn(i);
-    };
-    std::vector<std::thread> th;
-    for (unsigned k = 1; k < std::min<size_t>(hw, count); k++) th.emplace_back(worker);
-    worker();
-    for (auto &x : th) x.join();
-  };
   if (ntask > 0)
-    parallel(ntask, [&](size_t i) {
+    parallel_for(ntask, [&](size_t i) {
       Planner &w = walks[1 + i];
       w.pool.assign(tasks[i].pairs.begin(), tasks[i].pairs.end());
       w.visit(tasks[i].block, 0, tasks[i].pairs.size());
@@ -362,7 +351,7 @@ void build_plan(const Tree &t, const std::vector<int32_t> &rankA, const std::vec
   plan.leaf_pair_off.assign(nleaf + 1, 0);
   for (size_t l = 0; l < nleaf; l++) plan.leaf_pair_off[l + 1] = plan.leaf_pair_off[l] + cnt[l];
   plan.leaf_pairs.resize(npairs);
-  parallel(nwalk, [&](size_t i) {
+  parallel_for(nwalk, [&](size_t i) {
     const Planner &w = walks[i];
     std::copy(w.terms.begin(), w.terms.end(), plan.terms.begin() + toff[i]);
     const int32_t off = (int32_t)toff[i];

@@ -1,12 +1,51 @@
 // hmat_tree.h -- host-side cluster tree, block-cluster tree and sum-expression plan.
 #pragma once
+#include <algorithm>
+#include <atomic>
 #include <cstdint>
+#include <exception>
 #include <memory>
+#include <mutex>
+#include <thread>
 #include <vector>
 
 #include "hmat_internal.h"
 
 namespace hm {
+
+// Runs fn(0 .. count-1) on up to 16 host threads, the calling thread included. If fn throws on
+// any thread, no thread takes a new index, and the first exception is rethrown on the calling
+// thread once all threads have joined: no exception leaves a worker thread (that would end the
+// process). If the system refuses a new thread, the threads already started do the work.
+template <typename F>
+void parallel_for(size_t count, F &&fn) {
+  const unsigned hw = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+  std::atomic<size_t> next{0};
+  std::exception_ptr err;
+  std::mutex mu;
+  auto worker = [&]() {
+    try {
+      for (size_t i = next++; i < count; i = next++) fn(i);
+    } catch (...) {
+      std::lock_guard<std::mutex> lk(mu);
+      if (!err) err = std::current_exception();
+      next = count;
+    }
+  };
+  const size_t nt = std::min<size_t>(hw, count);
+  std::vector<std::thread> th;
+  th.reserve(nt);
+  for (size_t k = 1; k < nt; k++) {
+    try {
+      th.emplace_back(worker);
+    } catch (...) {
+      break;
+    }
+  }
+  worker();
+  for (auto &x : th) x.join();
+  if (err) std::rethrow_exception(err);
+}
 
 struct Cluster {
   int level = 0;

@@ -96,6 +96,31 @@ def test_last_error_is_thread_local(H):
     assert msg_main and seen["t"] == ""
 
 
+@pytest.mark.skipif(any(os.path.exists(f"/dev/nvidia{i}") for i in range(16)),
+                    reason="checks the behaviour without a CUDA device")
+def test_no_device_returns_status(H):
+    """Without a usable CUDA device, the entry points that need one return HMAT_ECUDA with a
+    message and leave their output handle NULL; nothing aborts across the ABI, and the library
+    stays usable for host-only calls."""
+    F = H.RANK_FEATURES
+    P = inputs.points(0, 2, 300, 0)
+    calls = [lambda: H.hmat_build(P, 0, leaf_size=16),
+             lambda: H.hmat_rankmodel_create(np.zeros(H.RANK_PARAMS, np.float32), np.zeros(F), np.ones(F)),
+             lambda: H.hmat_rankmodel_train(np.zeros((10, F), np.float32), np.ones(10, np.float32))]
+    for call in calls:
+        with pytest.raises(H.HmatError) as e:
+            call()
+        assert e.value.status == H.HMAT_ECUDA and H.lib().hmat_last_error()
+    L = H.lib()
+    out = ctypes.c_void_p(1)
+    opts = H.BuildOpts(16, 1.0, 1e-8, 64, 0)
+    assert L.hmat_build(P.ctypes.data_as(H._PD), 300, 2, 0, ctypes.byref(opts), None, None,
+                        ctypes.byref(out)) == H.HMAT_ECUDA
+    assert out.value is None
+    ph = H.hmat_plan_host(P, leaf_size=16)
+    assert len(ph.perm) == 300 and H.lib().hmat_last_error() == b""
+
+
 @pytest.mark.parametrize("kind,dim,n,leaf,eta", [(0, 2, 2048, 32, 1.0), (1, 3, 3000, 32, 1.0), (0, 3, 1531, 16, 1.0),
                                                  (0, 1, 777, 8, 0.5), (0, 2, 300, 16, 2.0), (0, 3, 1, 4, 1.0)])
 def test_plan_host_matches_oracle(H, oracle, kind, dim, n, leaf, eta):

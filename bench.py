@@ -397,7 +397,14 @@ def run_ours(args):
                          "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "peak_source": peak_kind, "traffic": traffic,
                          "per_launch_ms": per_launch_ms, "launches_per_step": apply_launches,
-                         "algorithmic_bytes_per_launch": apply_bytes / max(apply_launches, 1)},
+                         "algorithmic_bytes_per_launch": apply_bytes / max(apply_launches, 1),
+                         "bytes_basis": "per use: every active target's sum-expression read once per pass, "
+                                        "plus its In/Out panels; terms shared by neighbouring targets count "
+                                        "once per target",
+                         # the DRAM rate of the same pass: measured DRAM bytes (ncu, one pass) over the
+                         # live pass time, i.e. the unique bytes after L2 reuse
+                         "dram_gbs": (traffic / (per_launch_ms * 1e-3) / 1e9) if traffic else None,
+                         "dram_frac": (traffic / (per_launch_ms * 1e-3) / 1e9 / peak) if traffic else None},
             "cpu_baseline": {"value": W["n"] / t_est, "unit": UNIT, "cores": thr, "kind": "oracle",
                              "sample": desc},
             "e2e": {"value": replica_value(W["n"], e2e_s * 1e3, world), "unit": UNIT, "h2d_bytes_per_step": h2d // e2e_steps,

@@ -95,7 +95,9 @@ typedef enum {
 } hmat_compressor;
 
 typedef struct {
-  int leaf_size;       /* n_min: leaf clusters hold at most this many points (>= 1) */
+  int leaf_size;       /* n_min: leaf clusters hold at most this many points (2..128; all leaves
+                          sit on one level, and n_min >= 2 keeps every cluster non-empty as
+                          Def. 2.2 requires) */
   double eta;          /* admissibility: max(diam tau, diam sigma) <= eta * dist(tau, sigma) */
   double aca_eps;      /* ACA stop tolerance for far leaves (Algorithm 6, eq. (truncaca)) */
   int factor_prec;     /* 64: store factors in FP64; 32: store factors in FP32 */
@@ -206,7 +208,7 @@ hmat_status hmat_build(const double *xyz, int64_t n, int dim, hmat_kernel kernel
  *   n_lowrank[max_leaves], n_hpairs[max_leaves]  per leaf, the low-rank terms and H-pairs of
  *                      its sum-expression (as hmat_sumexpr_counts);
  *   *csp               C_sp, the largest number of blocks sharing one row cluster.
- * EINVAL on NULL xyz, n < 1, dim outside 1..3, leaf_size outside 1..128, eta <= 0 or a
+ * EINVAL on NULL xyz, n < 1, dim outside 1..3, leaf_size outside 2..128, eta <= 0 or a
  * non-finite coordinate. */
 hmat_status hmat_plan_host(const double *xyz, int64_t n, int dim, int leaf_size, double eta, int64_t *perm,
                            int64_t *n_leaves, hmat_leaf *leaves, int64_t *n_lowrank, int64_t *n_hpairs,

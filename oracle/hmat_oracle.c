@@ -192,9 +192,13 @@ static int build_block(or_tree *t, int tau, int sigma) {
  * D = smallest d >= 0 with ceil(n / 2^d) <= leaf_size, so all leaves sit on level D and
  * hold at most leaf_size points. Split axis = longest bounding-box side (first on ties);
  * the points are ordered by (coordinate, original index) and the first floor(size/2) form
- * the first child. */
+ * the first child. leaf_size >= 2 is required: the clusters of level d hold floor(n / 2^d)
+ * or ceil(n / 2^d) points, so those of level D - 1 hold at least leaf_size and their halves
+ * at least floor(leaf_size / 2); with leaf_size = 1 a one-point cluster above level D would
+ * split into an empty and a one-point child, and Def. 2.2 (iii) wants every cluster
+ * non-empty. */
 void *or_tree_build(const double *pts, int64_t n, int dim, int leaf_size, double eta) {
-  if (n < 1 || dim < 1 || dim > OR_MAXDIM || leaf_size < 1 || !(eta > 0.0)) return NULL;
+  if (n < 1 || dim < 1 || dim > OR_MAXDIM || leaf_size < 2 || !(eta > 0.0)) return NULL;
   or_tree *t = (or_tree *)calloc(1, sizeof(or_tree));
   t->n = n; t->dim = dim; t->leaf_size = leaf_size; t->eta = eta;
   int depth = 0;

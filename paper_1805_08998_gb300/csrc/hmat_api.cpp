@@ -362,7 +362,7 @@ hmat_status hmat_build(const double *xyz, int64_t n, int dim, hmat_kernel kernel
     if (n < 1 || dim < 1 || dim > 3) fail(HMAT_EINVAL, "need n >= 1 and dim in 1..3");
     if (kernel < HMAT_K_EXP || kernel > HMAT_K_POLY2) fail(HMAT_EINVAL, "unknown kernel");
     if (opts->factor_prec != 32 && opts->factor_prec != 64) fail(HMAT_EINVAL, "factor_prec must be 32 or 64");
-    if (opts->leaf_size < 1 || opts->leaf_size > 128) fail(HMAT_EINVAL, "leaf_size must be in 1..128");
+    if (opts->leaf_size < 2 || opts->leaf_size > 128) fail(HMAT_EINVAL, "leaf_size must be in 2..128");
     if (!(opts->eta > 0.0) || !(opts->aca_eps > 0.0)) fail(HMAT_EINVAL, "eta and aca_eps must be > 0");
     const int kmax = opts->aca_kmax > 0 ? opts->aca_kmax : 128;
     if (kmax > 128) fail(HMAT_EINVAL, "aca_kmax must be <= 128");
@@ -953,7 +953,7 @@ hmat_status hmat_plan_host(const double *xyz, int64_t n, int dim, int leaf_size,
   return guard([&] {
     if (!xyz) fail(HMAT_EINVAL, "NULL argument");
     if (n < 1 || dim < 1 || dim > 3) fail(HMAT_EINVAL, "need n >= 1 and dim in 1..3");
-    if (leaf_size < 1 || leaf_size > 128) fail(HMAT_EINVAL, "leaf_size must be in 1..128");
+    if (leaf_size < 2 || leaf_size > 128) fail(HMAT_EINVAL, "leaf_size must be in 2..128");
     if (!(eta > 0.0)) fail(HMAT_EINVAL, "eta must be > 0");
     if (max_leaves < 0) fail(HMAT_EINVAL, "max_leaves must be >= 0");
     for (int64_t i = 0; i < n * dim; i++)

@@ -141,7 +141,9 @@ struct Builder {
 }  // namespace
 
 std::shared_ptr<Tree> build_tree(const double *xyz, int64_t n, int dim, int leaf_size, double eta) {
-  if (!xyz || n < 1 || dim < 1 || dim > 3 || leaf_size < 1 || !(eta > 0.0)) return nullptr;
+  // leaf_size >= 2 keeps every cluster non-empty (Def. 2.2): a cluster of level depth - 1 holds
+  // at least leaf_size points, so each half holds at least leaf_size / 2 >= 1
+  if (!xyz || n < 1 || dim < 1 || dim > 3 || leaf_size < 2 || !(eta > 0.0)) return nullptr;
   auto t = std::make_shared<Tree>();
   t->n = n;
   t->dim = dim;

@@ -53,6 +53,9 @@ def test_argument_validation(H):
     with pytest.raises(H.HmatError) as e:
         H.hmat_build(xyz, 0, leaf_size=0)
     assert e.value.status == H.HMAT_EINVAL
+    with pytest.raises(H.HmatError) as e:  # n_min = 1 would make empty clusters (Def. 2.2)
+        H.hmat_build(xyz, 0, leaf_size=1)
+    assert e.value.status == H.HMAT_EINVAL
     with pytest.raises(H.HmatError) as e:
         H.hmat_build(xyz, 0, leaf_size=16, eta=-1.0)
     assert e.value.status == H.HMAT_EINVAL
@@ -122,7 +125,8 @@ def test_no_device_returns_status(H):
 
 
 @pytest.mark.parametrize("kind,dim,n,leaf,eta", [(0, 2, 2048, 32, 1.0), (1, 3, 3000, 32, 1.0), (0, 3, 1531, 16, 1.0),
-                                                 (0, 1, 777, 8, 0.5), (0, 2, 300, 16, 2.0), (0, 3, 1, 4, 1.0)])
+                                                 (0, 1, 777, 8, 0.5), (0, 2, 300, 16, 2.0), (0, 3, 1, 4, 1.0),
+                                                 (0, 2, 101, 2, 1.0), (0, 3, 5, 2, 1.0)])
 def test_plan_host_matches_oracle(H, oracle, kind, dim, n, leaf, eta):
     """a0/a1 host logic without a GPU: the library's cluster tree (Def. 2.2), block tree
     (Algorithm 1, Def. 2.3) and restriction plan (Algorithm 3) give, bit for bit, the oracle's
@@ -145,11 +149,48 @@ def test_plan_host_matches_oracle(H, oracle, kind, dim, n, leaf, eta):
     assert np.array_equal(ph.n_lowrank, lr) and np.array_equal(ph.n_hpairs, hp)
 
 
+def _degenerate_points(case):
+    if case == "duplicates":   # 40 distinct points, each 25 times: ties everywhere
+        return np.repeat(inputs.points(0, 3, 40, 1), 25, axis=0)
+    if case == "identical":    # one point 500 times: zero boxes, nothing admissible
+        return np.zeros((500, 2))
+    if case == "collinear":    # a segment in 3-D: two box sides stay proportional
+        t = inputs.uniform01(6, 1000)
+        return np.stack([t, 2 * t, -t], 1)
+    if case == "two_clusters":  # two well separated squares
+        return np.concatenate([inputs.points(0, 2, 500, 2), inputs.points(0, 2, 500, 3) + 10.0])
+    g = np.arange(12.0)         # integer grid: equal box sides and tied coordinates
+    X, Y = np.meshgrid(g, g)
+    return np.stack([X.ravel(), Y.ravel()], 1)
+
+
+@pytest.mark.parametrize("case,leaf", [("duplicates", 16), ("identical", 8), ("collinear", 16),
+                                       ("two_clusters", 16), ("grid", 4)])
+def test_plan_host_degenerate_geometry(H, oracle, case, leaf):
+    """Ties, zero-size boxes and collinear points: the library's trees and plan still equal the
+    oracle's bit for bit (split ties by original index, first longest side, distance 0 never
+    admissible)."""
+    P = _degenerate_points(case)
+    T = oracle.Tree(P, leaf, 1.0)
+    ph = H.hmat_plan_host(P, leaf_size=leaf, eta=1.0)
+    assert np.array_equal(ph.perm, T.perm)
+    la = ph.leaves
+    ref = np.array([T.leaf_ranges(l) for l in range(T.nleaf)])
+    assert len(la.far) == T.nleaf
+    assert np.array_equal(la.row_begin, ref[:, 0]) and np.array_equal(la.col_begin, ref[:, 2])
+    assert np.array_equal(la.far, (T.leaf_blocks[:, 2] == 1).astype(np.int64))
+    assert ph.csp == T.csp()
+    lr, hp, _ = T.sumexpr_counts()
+    assert np.array_equal(ph.n_lowrank, lr) and np.array_equal(ph.n_hpairs, hp)
+    if case == "identical":
+        assert la.far.sum() == 0
+
+
 def test_plan_host_arguments(H):
     P = inputs.points(0, 2, 100, 0)
     L = H.lib()
     for args in [(None, 100, 2, 16, 1.0), (P, 0, 2, 16, 1.0), (P, 100, 4, 16, 1.0), (P, 100, 2, 0, 1.0),
-                 (P, 100, 2, 16, 0.0), (P, 100, 2, 16, float("nan"))]:
+                 (P, 100, 2, 1, 1.0), (P, 100, 2, 129, 1.0), (P, 100, 2, 16, 0.0), (P, 100, 2, 16, float("nan"))]:
         pts, n, dim, leaf, eta = args
         ptr = pts.ctypes.data_as(H._PD) if pts is not None else None
         assert L.hmat_plan_host(ptr, n, dim, leaf, eta, None, None, None, None, None, 0, None) == H.HMAT_EINVAL

@@ -30,7 +30,8 @@ def _bbox(P):
 
 # ---------------------------------------------------------------- trees (Def. 2.2, 2.3, Alg. 1)
 
-@pytest.mark.parametrize("kind,dim,n,leaf", [(0, 2, 300, 8), (1, 3, 517, 16), (0, 3, 64, 64), (0, 1, 1, 4)])
+@pytest.mark.parametrize("kind,dim,n,leaf", [(0, 2, 300, 8), (1, 3, 517, 16), (0, 3, 64, 64), (0, 1, 1, 4),
+                                             (0, 2, 101, 2), (0, 2, 5, 2)])
 def test_cluster_tree_definition(oracle, kind, dim, n, leaf):
     """Def. 2.2: root = I, children partition the parent, all non-empty; leaves <= n_min;
     depth = ceil(log2(n / leaf)); each split puts the smaller coordinates on the first child."""
@@ -57,6 +58,14 @@ def test_cluster_tree_definition(oracle, kind, dim, n, leaf):
         left, right = Pp[b:b + s // 2, ax], Pp[b + s // 2:b + s, ax]
         if len(left) and len(right):
             assert left.max() <= right.min()
+
+
+def test_cluster_tree_rejects_leaf_size_one(oracle):
+    """Def. 2.2 (iii): clusters are non-empty. With every leaf on one level, n_min = 1 would split
+    a one-point cluster above the leaf level into an empty and a one-point child (N = 5: level 2
+    holds clusters of 1 and 2 points), so the tree requires n_min >= 2."""
+    with pytest.raises(ValueError):
+        oracle.Tree(inputs.points(0, 2, 5, 4), 1, 1.0)
 
 
 def _adm(Pt, Ps, eta):

@@ -7,6 +7,8 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <limits>
+#include <stdexcept>
 #include <thread>
 #include <utility>
 #include <cuda_runtime.h>
@@ -339,6 +341,9 @@ void build_plan(const Tree &t, const std::vector<int32_t> &rankA, const std::vec
     toff[i + 1] = toff[i] + walks[i].terms.size();
     npairs += walks[i].leaf_pairs.size();
   }
+  // term indices are 32-bit in the plan and in the device tables
+  if (toff[nwalk] > (size_t)std::numeric_limits<int32_t>::max())
+    throw std::length_error("restriction plan: more than 2^31 - 1 low-rank terms");
   plan.terms.resize(toff[nwalk]);
   std::vector<const PairDev *> src(nleaf, nullptr);
   std::vector<int64_t> cnt(nleaf, 0);

@@ -54,3 +54,28 @@ def test_single_rank_and_reference_rule():
     assert bench.replica_value(1000, 2.0, 1) == pytest.approx(5e5)
     assert bench.reference_runs_here(0, 1) and bench.reference_runs_here(0, 4)
     assert not bench.reference_runs_here(1, 4)
+
+
+def test_reference_arm_json_line():
+    """`bench.py --impl reference` (the CPU oracle, timed on the host cores) prints one JSON line
+    with the keys of the GPU arm's line, the same workload config, and its own CPU-baseline
+    record; e2e moves no bytes between host and device."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "1"], capture_output=True, text=True, timeout=600, cwd=root)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+              "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
+    assert d["config"] == dict(bench.WORKLOAD, parallelism="single")
+    assert d["value"] > 0 and d["higher_is_better"] is True
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}

@@ -279,6 +279,8 @@ static double kernel_eval(int kernel, const double *x, const double *y, int dim)
 
 typedef struct {
   const or_tree *t;
+  int nleaf;                  /* t->nleaf, kept so that freeing never reads the tree, which a
+                                 garbage collector may have freed first */
   int kernel;
   int prec32;                 /* factors rounded to float after assembly */
   int *rank;                  /* per leaf; -1 for near leaves */
@@ -371,7 +373,7 @@ static int aca_block(const or_tree *t, int kernel, int64_t r0, int64_t m, int64_
 void *or_hmat_build(const void *tree, int kernel, double aca_eps, int aca_kmax, int prec32) {
   const or_tree *t = (const or_tree *)tree;
   or_hmat *h = (or_hmat *)calloc(1, sizeof(or_hmat));
-  h->t = t; h->kernel = kernel; h->prec32 = prec32;
+  h->t = t; h->nleaf = t->nleaf; h->kernel = kernel; h->prec32 = prec32;
   h->rank = (int *)malloc(sizeof(int) * t->nleaf);
   h->U = (double **)calloc(t->nleaf, sizeof(double *));
   h->V = (double **)calloc(t->nleaf, sizeof(double *));
@@ -403,7 +405,7 @@ void *or_hmat_build(const void *tree, int kernel, double aca_eps, int aca_kmax, 
 void or_hmat_free(void *hh) {
   or_hmat *h = (or_hmat *)hh;
   if (!h) return;
-  for (int l = 0; l < h->t->nleaf; l++) { free(h->U[l]); free(h->V[l]); free(h->D[l]); }
+  for (int l = 0; l < h->nleaf; l++) { free(h->U[l]); free(h->V[l]); free(h->D[l]); }
   free(h->U); free(h->V); free(h->D); free(h->rank); free(h);
 }
 

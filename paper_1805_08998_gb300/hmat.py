@@ -275,7 +275,8 @@ def hmat_multiply_batched(As, Bs, eps: float, mode: int = MODE_F64, rank_proposa
                           compressor: int = COMP_RANDOMIZED):
     """Products As[i] Bs[i] in one call; returns the list of outputs."""
     n = len(As)
-    assert len(Bs) == n
+    if len(Bs) != n:
+        raise _shape_error(f"{n} left factors but {len(Bs)} right factors")
     opts = MultOpts(eps, mode, rank_proposal, max_rank, max_rounds, block_width, seed,
                     rank_model.handle if rank_model is not None else None, 0, -1, compressor)
     a = (_P * max(n, 1))(*[x.handle for x in As])
@@ -295,6 +296,8 @@ def hmat_matvec(Hm: HMatrix, x, stream=None) -> np.ndarray:
     """y = H x for x of shape (n,) or (n, ncols), original point order."""
     x = np.asarray(x, np.float64)
     vec = x.ndim == 1
+    if x.ndim not in (1, 2) or x.shape[0] != Hm.stats()["n"]:
+        raise _shape_error(f"x must have shape (n,) or (n, ncols) with n = {Hm.stats()['n']}, got {x.shape}")
     X = np.asfortranarray(x.reshape(x.shape[0], -1))
     Y = np.zeros_like(X, order="F")
     _check(lib().hmat_matvec(Hm.handle, X.ctypes.data_as(_PD), Y.ctypes.data_as(_PD), X.shape[1], _stream_ptr(stream)))
@@ -370,6 +373,24 @@ def _f32(a) -> np.ndarray:
     return np.ascontiguousarray(a, dtype=np.float32)
 
 
+def _shape_error(msg: str) -> HmatError:
+    # the C side sees only pointers and counts, so array shapes are checked here
+    return HmatError(HMAT_EINVAL, msg)
+
+
+def _samples(features, ranks=None):
+    """features as a (count, RANK_FEATURES) float32 array; ranks, if given, as count float32."""
+    X = _f32(features)
+    if X.ndim != 2 or X.shape[1] != RANK_FEATURES:
+        raise _shape_error(f"features must have shape (count, {RANK_FEATURES}), got {X.shape}")
+    if ranks is None:
+        return X
+    y = _f32(ranks).reshape(-1)
+    if y.shape[0] != X.shape[0]:
+        raise _shape_error(f"{X.shape[0]} feature rows but {y.shape[0]} ranks")
+    return X, y
+
+
 class RankModel:
     """Owner of an hmat_rankmodel_t (the learned rank proposal); released with
     hmat_rankmodel_destroy."""
@@ -390,7 +411,7 @@ class RankModel:
         return self._h
 
     def predict(self, features) -> np.ndarray:
-        X = _f32(features)
+        X = _samples(features)
         out = np.zeros(X.shape[0], np.float32)
         _check(lib().hmat_rankmodel_predict(self._h, X.ctypes.data_as(_PF), X.shape[0], out.ctypes.data_as(_PF)))
         return out
@@ -407,7 +428,7 @@ class RankModel:
         return w, mu, dv, loss.value
 
     def grad(self, features, ranks):
-        X, y = _f32(features), _f32(ranks)
+        X, y = _samples(features, ranks)
         g = np.zeros(RANK_PARAMS, np.float32)
         loss = ctypes.c_float()
         _check(lib().hmat_rankmodel_grad(self._h, X.ctypes.data_as(_PF), y.ctypes.data_as(_PF), X.shape[0],
@@ -418,7 +439,7 @@ class RankModel:
 def hmat_rankmodel_grad_noalloc(model: RankModel, features, ranks, stream=None):
     """hmat_rankmodel_grad without device allocation (fixed scratch; at most
     RANKGRAD_NOALLOC_MAX samples; concurrent calls on one device race)."""
-    X, y = _f32(features), _f32(ranks)
+    X, y = _samples(features, ranks)
     g = np.zeros(RANK_PARAMS, np.float32)
     loss = ctypes.c_float()
     _check(lib().hmat_rankmodel_grad_noalloc(model.handle, X.ctypes.data_as(_PF), y.ctypes.data_as(_PF), X.shape[0],
@@ -439,7 +460,7 @@ def hmat_rank_features(A: HMatrix, B: HMatrix, eps: float, C: HMatrix | None = N
 
 def hmat_rankmodel_train(features, ranks, epochs: int = 0, lr: float = 0.0, seed: int = 0,
                          stream=None) -> RankModel:
-    X, y = _f32(features), _f32(ranks)
+    X, y = _samples(features, ranks)
     opts = TrainOpts(epochs, lr, seed)
     h = _P()
     _check(lib().hmat_rankmodel_train(X.ctypes.data_as(_PF), y.ctypes.data_as(_PF), X.shape[0], ctypes.byref(opts),
@@ -448,7 +469,10 @@ def hmat_rankmodel_train(features, ranks, epochs: int = 0, lr: float = 0.0, seed
 
 
 def hmat_rankmodel_create(weights, mean, dev) -> RankModel:
-    w, mu, dv = _f32(weights), _f32(mean), _f32(dev)
+    w, mu, dv = _f32(weights).reshape(-1), _f32(mean).reshape(-1), _f32(dev).reshape(-1)
+    if w.shape[0] != RANK_PARAMS or mu.shape[0] != RANK_FEATURES or dv.shape[0] != RANK_FEATURES:
+        raise _shape_error(f"need {RANK_PARAMS} weights and {RANK_FEATURES} means and deviations, got "
+                           f"{w.shape[0]}, {mu.shape[0]}, {dv.shape[0]}")
     h = _P()
     _check(lib().hmat_rankmodel_create(w.ctypes.data_as(_PF), mu.ctypes.data_as(_PF), dv.ctypes.data_as(_PF),
                                        ctypes.byref(h)))

@@ -83,6 +83,25 @@ def test_argument_validation(H):
         H.hmat_points(1, 2, 10, 0)
 
 
+def test_binding_checks_array_shapes(H):
+    """The C-ABI sees only pointers and counts, so the binding checks array shapes before a call:
+    a wrongly shaped array raises HMAT_EINVAL instead of letting the library read or write past
+    its end. (These checks run before any device is touched.)"""
+    F = H.RANK_FEATURES
+    bad = [lambda: H.hmat_rankmodel_create(np.zeros(10), np.zeros(F), np.ones(F)),
+           lambda: H.hmat_rankmodel_create(np.zeros(H.RANK_PARAMS), np.zeros(F - 1), np.ones(F)),
+           lambda: H.hmat_rankmodel_train(np.zeros((10, F - 5)), np.ones(10)),
+           lambda: H.hmat_rankmodel_train(np.zeros((10, F)), np.ones(9)),
+           lambda: H.RankModel(None).predict(np.zeros((3, F + 1))),
+           lambda: H.RankModel(None).grad(np.zeros((3, F)), np.zeros(4)),
+           lambda: H.hmat_rankmodel_grad_noalloc(H.RankModel(None), np.zeros(F), np.zeros(1)),
+           lambda: H.hmat_multiply_batched([], [None], 1e-6)]
+    for call in bad:
+        with pytest.raises(H.HmatError) as e:
+            call()
+        assert e.value.status == H.HMAT_EINVAL
+
+
 def test_last_error_is_thread_local(H):
     import threading
     L = H.lib()

@@ -209,7 +209,10 @@ hmat_status hmat_build(const double *xyz, int64_t n, int dim, hmat_kernel kernel
  *                      its sum-expression (as hmat_sumexpr_counts);
  *   *csp               C_sp, the largest number of blocks sharing one row cluster.
  * EINVAL on NULL xyz, n < 1, dim outside 1..3, leaf_size outside 2..128, eta <= 0 or a
- * non-finite coordinate. */
+ * non-finite coordinate. Memory: a block tree with few admissible blocks (coincident points, or
+ * eta near 0) keeps every block inadmissible down to the leaves, and its plan then holds about
+ * (n / leaf_size)^3 H-pairs (8 bytes each), as the dense product it describes would need; the
+ * same holds for hmat_multiply on such inputs. */
 hmat_status hmat_plan_host(const double *xyz, int64_t n, int dim, int leaf_size, double eta, int64_t *perm,
                            int64_t *n_leaves, hmat_leaf *leaves, int64_t *n_lowrank, int64_t *n_hpairs,
                            int64_t max_leaves, int *csp);

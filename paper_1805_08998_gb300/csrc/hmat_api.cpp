@@ -133,6 +133,17 @@ DevBuf upload(const std::vector<T> &v, cudaStream_t s) {
   return b;
 }
 
+// An enum parameter arrives from C or ctypes as a plain int that may lie outside the enumeration,
+// and reading such a value as the C++ enum type is undefined; its bits are read as an int instead,
+// so that the range check is well defined.
+template <typename E>
+int enum_bits(const E &e) {
+  static_assert(sizeof(E) == sizeof(int), "enum parameters are int-sized");
+  int v;
+  std::memcpy(&v, &e, sizeof v);
+  return v;
+}
+
 double now_ms() {
   return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
@@ -324,7 +335,8 @@ hmat_status hmat_set_allocator(void *(*alloc)(size_t, void *, void *), void (*fr
   });
 }
 
-hmat_status hmat_points(hmat_ptdist dist, int dim, int64_t n, uint64_t seed, double *xyz) {
+hmat_status hmat_points(hmat_ptdist dist_in, int dim, int64_t n, uint64_t seed, double *xyz) {
+  const int dist = enum_bits(dist_in);
   return guard([&] {
     if (n < 0 || (n > 0 && !xyz)) fail(HMAT_EINVAL, "bad n or NULL xyz");
     auto draw = [&](uint64_t c) {  // c-th output of the splitmix64 stream
@@ -354,12 +366,13 @@ hmat_status hmat_points(hmat_ptdist dist, int dim, int64_t n, uint64_t seed, dou
   });
 }
 
-hmat_status hmat_build(const double *xyz, int64_t n, int dim, hmat_kernel kernel, const hmat_build_opts *opts,
+hmat_status hmat_build(const double *xyz, int64_t n, int dim, hmat_kernel kernel_in, const hmat_build_opts *opts,
                        const hmat_t tree_from, void *stream, hmat_t *out) {
   if (out) *out = nullptr;
   return guard([&] {
     if (!out || !xyz || !opts) fail(HMAT_EINVAL, "NULL argument");
     if (n < 1 || dim < 1 || dim > 3) fail(HMAT_EINVAL, "need n >= 1 and dim in 1..3");
+    const int kernel = enum_bits(kernel_in);
     if (kernel < HMAT_K_EXP || kernel > HMAT_K_POLY2) fail(HMAT_EINVAL, "unknown kernel");
     if (opts->factor_prec != 32 && opts->factor_prec != 64) fail(HMAT_EINVAL, "factor_prec must be 32 or 64");
     if (opts->leaf_size < 2 || opts->leaf_size > 128) fail(HMAT_EINVAL, "leaf_size must be in 2..128");

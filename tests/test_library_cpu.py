@@ -81,6 +81,14 @@ def test_argument_validation(H):
     assert L.hmat_set_allocator(ctypes.c_void_p(1), None, None) == H.HMAT_EINVAL
     with pytest.raises(H.HmatError):
         H.hmat_points(1, 2, 10, 0)
+    for dist in (2, -1, 1 << 30):  # enum arguments outside the enumeration
+        with pytest.raises(H.HmatError) as e:
+            H.hmat_points(dist, 3, 10, 0)
+        assert e.value.status == H.HMAT_EINVAL
+    for kernel in (-1, 3, 1 << 30):
+        with pytest.raises(H.HmatError) as e:
+            H.hmat_build(xyz, kernel, leaf_size=16)
+        assert e.value.status == H.HMAT_EINVAL
 
 
 def test_binding_checks_array_shapes(H):

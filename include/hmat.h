@@ -95,9 +95,10 @@ typedef enum {
 } hmat_compressor;
 
 typedef struct {
-  int leaf_size;       /* n_min: leaf clusters hold at most this many points (2..128; all leaves
+  int leaf_size;       /* n_min: leaf clusters hold at most this many points (2..64; all leaves
                           sit on one level, and n_min >= 2 keeps every cluster non-empty as
-                          Def. 2.2 requires) */
+                          Def. 2.2 requires; the device kernels stage whole leaves in shared
+                          memory and are laid out for at most 64 points) */
   double eta;          /* admissibility: max(diam tau, diam sigma) <= eta * dist(tau, sigma) */
   double aca_eps;      /* ACA stop tolerance for far leaves (Algorithm 6, eq. (truncaca)) */
   int factor_prec;     /* 64: store factors in FP64; 32: store factors in FP32 */
@@ -208,6 +209,7 @@ hmat_status hmat_build(const double *xyz, int64_t n, int dim, hmat_kernel kernel
  *   n_lowrank[max_leaves], n_hpairs[max_leaves]  per leaf, the low-rank terms and H-pairs of
  *                      its sum-expression (as hmat_sumexpr_counts);
  *   *csp               C_sp, the largest number of blocks sharing one row cluster.
+ * leaf_size may be 2..128 here (hmat_build takes 2..64).
  * EINVAL on NULL xyz, n < 1, dim outside 1..3, leaf_size outside 2..128, eta <= 0 or a
  * non-finite coordinate. Memory: a block tree with few admissible blocks (coincident points, or
  * eta near 0) keeps every block inadmissible down to the leaves, and its plan then holds about

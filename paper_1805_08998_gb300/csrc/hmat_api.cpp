@@ -375,7 +375,10 @@ hmat_status hmat_build(const double *xyz, int64_t n, int dim, hmat_kernel kernel
     const int kernel = enum_bits(kernel_in);
     if (kernel < HMAT_K_EXP || kernel > HMAT_K_POLY2) fail(HMAT_EINVAL, "unknown kernel");
     if (opts->factor_prec != 32 && opts->factor_prec != 64) fail(HMAT_EINVAL, "factor_prec must be 32 or 64");
-    if (opts->leaf_size < 2 || opts->leaf_size > 128) fail(HMAT_EINVAL, "leaf_size must be in 2..128");
+    // the device kernels stage whole leaves in shared memory, per warp; their layouts are sized
+    // for leaves of at most 64 points (an FP64 dense leaf of 107 or more points per warp would not
+    // fit the low-rank product kernel's shared memory at all)
+    if (opts->leaf_size < 2 || opts->leaf_size > 64) fail(HMAT_EINVAL, "leaf_size must be in 2..64");
     if (!(opts->eta > 0.0) || !(opts->aca_eps > 0.0)) fail(HMAT_EINVAL, "eta and aca_eps must be > 0");
     const int kmax = opts->aca_kmax > 0 ? opts->aca_kmax : 128;
     if (kmax > 128) fail(HMAT_EINVAL, "aca_kmax must be <= 128");

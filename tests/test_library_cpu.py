@@ -56,6 +56,9 @@ def test_argument_validation(H):
     with pytest.raises(H.HmatError) as e:  # n_min = 1 would make empty clusters (Def. 2.2)
         H.hmat_build(xyz, 0, leaf_size=1)
     assert e.value.status == H.HMAT_EINVAL
+    with pytest.raises(H.HmatError) as e:  # the kernels' shared-memory layouts hold leaves of <= 64 points
+        H.hmat_build(xyz, 0, leaf_size=65)
+    assert e.value.status == H.HMAT_EINVAL
     with pytest.raises(H.HmatError) as e:
         H.hmat_build(xyz, 0, leaf_size=16, eta=-1.0)
     assert e.value.status == H.HMAT_EINVAL

@@ -190,7 +190,7 @@ hmat_status hmat_points(hmat_ptdist dist, int dim, int64_t n, uint64_t seed, dou
  * far leaves by ACA (Algorithm 6) on the GPU. If tree_from is not NULL its cluster and block
  * tree are reused (xyz must then hold the same points; only kernel and factors differ), which
  * is how two factors of a product are put on one block tree (Sec. 3). Synchronises `stream`
- * once (to size the far-leaf storage). EINVAL on bad sizes, NaN/Inf points or opts;
+ * once (to size the far-leaf storage). EINVAL on bad sizes (n must be below 2^31), NaN/Inf points or opts;
  * EMISMATCH if tree_from was built on other points. */
 hmat_status hmat_build(const double *xyz, int64_t n, int dim, hmat_kernel kernel,
                        const hmat_build_opts *opts, const hmat_t tree_from, void *stream,

@@ -372,6 +372,8 @@ hmat_status hmat_build(const double *xyz, int64_t n, int dim, hmat_kernel kernel
   return guard([&] {
     if (!out || !xyz || !opts) fail(HMAT_EINVAL, "NULL argument");
     if (n < 1 || dim < 1 || dim > 3) fail(HMAT_EINVAL, "need n >= 1 and dim in 1..3");
+    // block sizes are 32-bit in the device tables
+    if (n > (int64_t)std::numeric_limits<int32_t>::max()) fail(HMAT_EINVAL, "n must be below 2^31");
     const int kernel = enum_bits(kernel_in);
     if (kernel < HMAT_K_EXP || kernel > HMAT_K_POLY2) fail(HMAT_EINVAL, "unknown kernel");
     if (opts->factor_prec != 32 && opts->factor_prec != 64) fail(HMAT_EINVAL, "factor_prec must be 32 or 64");

@@ -178,8 +178,9 @@ typedef struct {
   int64_t groups;                /* subtree groups the product ran in (1: one pass) */
 } hmat_stats_t;
 
-/* Fill xyz (n*dim doubles, row-major, caller-owned) with the seeded points of the given
- * distribution: splitmix64 stream of `seed`, u = (z >> 11) * 2^-53; cube: point i uses draws
+/* Synthetic inputs (the paper's experiments, Sec. 6.1, use Galerkin matrices on the unit sphere;
+ * seeded point sets in a cube or on the sphere stand in for them). Fill xyz (n*dim doubles,
+ * row-major, caller-owned) with the seeded points of the given distribution: splitmix64 stream of `seed`, u = (z >> 11) * 2^-53; cube: point i uses draws
  * dim*i .. dim*i+dim-1; sphere: draws 2i, 2i+1 -> z = 2u1 - 1, phi = 2 pi u2,
  * (sqrt(1-z^2) cos phi, sqrt(1-z^2) sin phi, z). EINVAL on a bad dim/n or NULL xyz. */
 hmat_status hmat_points(hmat_ptdist dist, int dim, int64_t n, uint64_t seed, double *xyz);
@@ -262,7 +263,9 @@ hmat_status hmat_product_error(const hmat_t A, const hmat_t B, const hmat_t C, i
 hmat_status hmat_multiply_batched(const hmat_t *A, const hmat_t *B, int count, const hmat_mult_opts *opts,
                                   void *stream, hmat_t *C);
 
-/* Dense copy of the whole matrix in ORIGINAL point order into the host buffer out
+/* Dense copy of the whole matrix (every leaf of the block tree expanded as in the definition of
+ * H(B, k), Sec. 2: U V^T on far leaves, the stored block on near leaves) in ORIGINAL point order
+ * into the host buffer out
  * (column-major, leading dimension ld >= n). Synchronises `stream` of the handle's last
  * use. Intended for checking small problems. */
 hmat_status hmat_to_dense(const hmat_t h, double *out, int64_t ld);
@@ -270,7 +273,8 @@ hmat_status hmat_to_dense(const hmat_t h, double *out, int64_t ld);
 /* Number of leaves of the block tree (far + near), numbered in depth-first order. */
 hmat_status hmat_leaf_count(const hmat_t h, int64_t *n_leaves);
 
-/* Geometry, kind and rank of leaf i (0 <= i < leaf count). */
+/* Geometry, kind and rank of leaf i (0 <= i < leaf count): tau x sigma, its level, far (in F, a
+ * low-rank matrix of R(tau x sigma, k), Sec. 2) or near (in N, dense). */
 hmat_status hmat_leaf_info(const hmat_t h, int64_t i, hmat_leaf *info);
 
 /* Copy leaf i to the host as FP64: far leaf -> U (row_size x rank) into U and V
@@ -290,7 +294,9 @@ hmat_status hmat_data_bytes(const hmat_t h, int64_t *bytes);
  * EINVAL if smaller than hmat_data_bytes). Pinned host memory makes it one DMA. Synchronises. */
 hmat_status hmat_data_get(const hmat_t h, void *out, int64_t bytes);
 
-/* Structure and, for products, work statistics of h. */
+/* Structure and, for products, work statistics of h: the counts of Sec. 2 (#F, #N, depth, C_sp)
+ * and the algorithmic flops and bytes of the product's steps (the quantities of Lemmas 5.1-5.3
+ * and Thm. 5.4 as the product actually ran them), with device times per phase. */
 hmat_status hmat_stats(const hmat_t h, hmat_stats_t *stats);
 
 /* Per leaf: number of low-rank terms and of H-pairs in the sum-expression S(leaf) that the
@@ -308,7 +314,12 @@ hmat_status hmat_sumexpr_counts(const hmat_t A, const hmat_t B, int64_t *n_lowra
 hmat_status hmat_rank_features(const hmat_t A, const hmat_t B, double eps, const hmat_t C, float *features,
                                float *ranks, int64_t *n_far);
 
-/* Train a rank model on the GPU on (features, ranks) samples (host arrays, count rows): features
+/* The learned rank proposal (no counterpart in the paper, whose Algorithm 8 starts every block
+ * from one sample): a small network predicts a far block's eps-rank from its features, and the
+ * product uses the prediction only to size the first sampling round; the stop test and the final
+ * truncation still decide rank and error.
+ *
+ * Train a rank model on the GPU on (features, ranks) samples (host arrays, count rows): features
  * are standardised with the sample mean and deviation, the target is log2(1 + rank), the loss
  * the mean squared error, optimised by Adam over full batches; forward and backward run in the
  * library's kernels (FP16 weights, FP32 accumulation). Synchronises. */
@@ -358,7 +369,8 @@ hmat_status hmat_rankmodel_grad_noalloc(const hmat_rankmodel_t m, const float *f
 
 void hmat_rankmodel_destroy(hmat_rankmodel_t m);
 
-/* Release h and its device memory (NULL is a no-op). */
+/* Handle management and errors (library conventions; no counterpart in the paper).
+ * Release h and its device memory (NULL is a no-op). */
 void hmat_destroy(hmat_t h);
 
 /* Message of the last failed call on this thread ("" if none). */

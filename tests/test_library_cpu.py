@@ -48,6 +48,22 @@ def test_points_match_shared_generator(H, dist, dim, n, seed):
         assert np.abs(a - b).max() <= 4e-16
 
 
+def test_generator_matches_published_splitmix64(H):
+    """The seeded stream behind every synthetic input is splitmix64: the shared module's outputs
+    and the library's cube points (u = (output >> 11) 2^-53, one draw per coordinate) reproduce the
+    generator's published outputs for seeds 0 and 1234567."""
+    ref = {}
+    for line in open(os.path.join(ROOT, "tests", "golden", "splitmix64.txt")):
+        f = line.split()
+        if f and f[0] == "seed":
+            ref[int(f[1])] = [int(x) for x in f[2:]]
+    for seed, outs in ref.items():
+        got = inputs.splitmix64(seed, len(outs))
+        assert [int(x) for x in got] == outs
+        u = H.hmat_points(0, 1, len(outs), seed)[:, 0]
+        assert [int(x) for x in (u * 2.0 ** 53).astype(np.uint64)] == [o >> 11 for o in outs]
+
+
 def test_argument_validation(H):
     xyz = inputs.points(0, 2, 100, 0)
     with pytest.raises(H.HmatError) as e:

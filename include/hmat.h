@@ -230,7 +230,10 @@ hmat_status hmat_plan_host(const double *xyz, int64_t n, int dim, int leaf_size,
  * far blocks are compressed by adaptive cross approximation (Algorithm 6; a round is then one
  * cross, a row and a column of every unfinished block) and the cross factors L U are truncated
  * to the eps-rank by a QR of L and the same FP64 eigen-truncation; with HMAT_COMP_LANCZOS by
- * Lanczos bidiagonalization (Algorithm 7), then the same truncation of Q (S^T Q)^T. */
+ * Lanczos bidiagonalization (Algorithm 7), then the same truncation of Q (S^T Q)^T. Host memory:
+ * the product's host tables (restriction plan, job and panel lists) are kept per calling thread
+ * after the call, so that the next product on that thread reuses their pages; they are released
+ * when the thread exits. */
 hmat_status hmat_multiply(const hmat_t A, const hmat_t B, const hmat_mult_opts *opts,
                           void *stream, hmat_t *C);
 

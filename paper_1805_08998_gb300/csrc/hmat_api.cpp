@@ -66,7 +66,22 @@ hmat_status guard(F &&f) {
 void *(*g_alloc)(size_t, void *, void *) = nullptr;
 void (*g_free)(void *, void *) = nullptr;
 void *g_ctx = nullptr;
-bool g_pool_set = false;
+// per device: the default pool's release threshold has been raised (set once; threads of a batched
+// product may race to set it, which is harmless, so the flag only has to be race-free itself)
+constexpr int kMaxDevices = 64;
+std::atomic<bool> g_pool_set[kMaxDevices];
+
+void keep_pool_memory() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return;
+  if (g_pool_set[dev].load(std::memory_order_acquire)) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t thr = std::numeric_limits<uint64_t>::max();
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  g_pool_set[dev].store(true, std::memory_order_release);
+}
 
 void *dev_alloc(size_t bytes, cudaStream_t s) {
   if (bytes == 0) bytes = 16;
@@ -75,16 +90,7 @@ void *dev_alloc(size_t bytes, cudaStream_t s) {
     if (!p) fail(HMAT_ENOMEM, "device allocation of " + std::to_string(bytes) + " bytes failed (custom allocator)");
     return p;
   }
-  if (!g_pool_set) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaMemPool_t pool;
-    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
-      uint64_t thr = std::numeric_limits<uint64_t>::max();
-      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
-    }
-    g_pool_set = true;
-  }
+  keep_pool_memory();
   void *p = nullptr;
   cudaError_t e = cudaMallocAsync(&p, bytes, s);
   if (e != cudaSuccess || !p) {

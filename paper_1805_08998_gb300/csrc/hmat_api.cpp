@@ -2253,11 +2253,21 @@ extern "C" hmat_status hmat_multiply_batched(const hmat_t *A, const hmat_t *B, i
         } catch (const std::exception &e) {
           st[i] = HMAT_EINVAL;
           msg[i] = e.what();
+        } catch (...) {
+          st[i] = HMAT_EINVAL;
+          msg[i] = "unknown exception";
         }
       }
     };
     std::vector<std::thread> th;
-    for (int w = 1; w < NS; w++) th.emplace_back(worker, w);
+    th.reserve(NS);
+    for (int w = 1; w < NS; w++) {
+      try {
+        th.emplace_back(worker, w);
+      } catch (...) {
+        break;  // no thread to be had: the threads already started take the remaining products
+      }
+    }
     worker(0);
     for (auto &x : th) x.join();
     for (int w = 0; w < NS; w++) {

@@ -58,6 +58,9 @@ hmat_status guard(F &&f) {
   } catch (const std::exception &e) {
     g_last_error = e.what();
     return HMAT_EINVAL;
+  } catch (...) {  // nothing crosses the C-ABI
+    g_last_error = "unknown exception";
+    return HMAT_EINVAL;
   }
 }
 

@@ -373,7 +373,10 @@ hmat_status hmat_rankmodel_grad_noalloc(const hmat_rankmodel_t m, const float *f
 void hmat_rankmodel_destroy(hmat_rankmodel_t m);
 
 /* Handle management and errors (library conventions; no counterpart in the paper).
- * Release h and its device memory (NULL is a no-op). */
+ * Release h and its device memory (NULL is a no-op). A handle's device memory is freed in stream
+ * order on the stream of the call that made it (hmat_build, hmat_multiply; for
+ * hmat_multiply_batched, the caller's stream), so that stream must still exist when the handle is
+ * destroyed: destroy handles before their stream. */
 void hmat_destroy(hmat_t h);
 
 /* Message of the last failed call on this thread ("" if none). */

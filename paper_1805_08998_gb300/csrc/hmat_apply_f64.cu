@@ -3,8 +3,11 @@
 
 namespace hm {
 
+// the transposed direction is instantiated in hmat_apply_f64_trans.cu
+cudaError_t launch_apply_f64_trans(int P, const ApplyArgs &a, cudaStream_t s);
+
 cudaError_t launch_apply_f64(int P, bool trans, const ApplyArgs &a, cudaStream_t s) {
-  return apply_detail::launch_apply_t<double>(P, trans, a, s);
+  return trans ? launch_apply_f64_trans(P, a, s) : apply_detail::launch_apply_dir<double, false>(P, a, s);
 }
 
 cudaError_t launch_panels_f64(const PanelArgs &a, bool leaf_kind, cudaStream_t s) {

@@ -1,5 +1,6 @@
-// hmat_apply_launch.cuh -- launch helpers of the application and panel kernels, instantiated
-// once per element type (hmat_apply_f32.cu, hmat_apply_f64.cu) so the two compile in parallel.
+// hmat_apply_launch.cuh -- launch helpers of the application and panel kernels, instantiated per
+// element type and direction (hmat_apply_f32.cu / hmat_apply_f32_trans.cu, hmat_apply_f64.cu /
+// hmat_apply_f64_trans.cu) so that the four translation units compile in parallel.
 #pragma once
 #include "hmat_apply.cuh"
 
@@ -38,11 +39,11 @@ inline size_t smem_bytes(size_t es, int P, const ApplyArgs &a) {
   return a.gstage ? cw : (size_t)(a.smem_in + a.smem_out + a.smem_rho) * SP * es + cw;
 }
 
-template <typename T>
-static cudaError_t launch_apply_t(int P, bool trans, const ApplyArgs &a, cudaStream_t s) {
+// one direction of the application: TRANS = false for S X (a3), true for S^T X (a6)
+template <typename T, bool TRANS>
+static cudaError_t launch_apply_dir(int P, const ApplyArgs &a, cudaStream_t s) {
   const size_t smem = smem_bytes(sizeof(T), P, a);
-  if (P == 8) return trans ? launch_rb<T, 8, true>(a, smem, s) : launch_rb<T, 8, false>(a, smem, s);
-  return trans ? launch_rb<T, 16, true>(a, smem, s) : launch_rb<T, 16, false>(a, smem, s);
+  return P == 8 ? launch_rb<T, 8, TRANS>(a, smem, s) : launch_rb<T, 16, TRANS>(a, smem, s);
 }
 
 template <typename T>

@@ -38,6 +38,40 @@ def test_exports_every_declared_symbol(H):
     assert sorted(H.EXPORTS) == declared
 
 
+def test_header_is_plain_c(H, tmp_path):
+    """include/hmat.h is a C header: a C99 program that includes it compiles without warnings
+    under -Wall -Wextra -pedantic, links against libhmat.so and calls it."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "abi.c"
+    src.write_text("""#include "hmat.h"
+#include <stdio.h>
+int main(void) {
+  hmat_build_opts b = {32, 1.0, 1e-10, 64, 0};
+  hmat_mult_opts m = {0};
+  hmat_stats_t st;
+  hmat_leaf lf;
+  double xyz[6];
+  hmat_status s = hmat_points(HMAT_PTS_SPHERE, 3, 2, 7, xyz);
+  (void)b; (void)m; (void)st; (void)lf;
+  printf("%d %.17g\\n", (int)s, xyz[5]);
+  return s == HMAT_OK ? 0 : 1;
+}
+""")
+    lib_dir = os.path.dirname(H.LIB_PATH)
+    exe = tmp_path / "abi"
+    r = subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I",
+                        os.path.join(ROOT, "include"), str(src), "-o", str(exe), "-L", lib_dir, "-lhmat",
+                        "-Wl,-rpath," + lib_dir], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    st, z = r.stdout.split()
+    assert int(st) == 0 and float(z) == inputs.points(1, 3, 2, 7)[1, 2]
+
+
 @pytest.mark.parametrize("dist,dim,n,seed", [(0, 1, 17, 3), (0, 2, 1000, 0), (0, 3, 333, 9), (1, 3, 500, 0)])
 def test_points_match_shared_generator(H, dist, dim, n, seed):
     a = H.hmat_points(dist, dim, n, seed)

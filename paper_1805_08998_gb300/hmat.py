@@ -338,8 +338,9 @@ def hmat_plan_host(points, leaf_size: int = 64, eta: float = 1.0) -> PlanHost:
     _check(L.hmat_plan_host(P.ctypes.data_as(_PD), n, dim, leaf_size, eta, perm.ctypes.data_as(_PI64),
                             ctypes.byref(nl), lv, lr.ctypes.data_as(_PI64), hp.ctypes.data_as(_PI64), k,
                             ctypes.byref(csp)))
-    cols = {f: np.array([getattr(lv[i], f) for i in range(k)], np.int64)
-            for f in ("row_begin", "row_size", "col_begin", "col_size", "level", "far", "rank")}
+    rec = np.ctypeslib.as_array(lv)[:k]  # the hmat_leaf records as a structured array (no copy)
+    cols = {f: rec[f].astype(np.int64) for f in ("row_begin", "row_size", "col_begin", "col_size", "level", "far",
+                                                 "rank")}
     return PlanHost(perm, LeafArrays(**cols), lr, hp, int(csp.value))
 
 

@@ -18,9 +18,9 @@
  *   - Host buffers are owned by the caller. Device memory is owned by the library and is
  *     taken from the allocator set with hmat_set_allocator (default: the CUDA stream-ordered
  *     pool, cudaMallocAsync/cudaFreeAsync, on the given stream). Three small kinds of buffer
- *     are taken with plain cudaMalloc instead, because they can outlive the stream they were
- *     made on: a block tree's point and block tables (shared by every handle on that tree,
- *     n * dim * 8 + 32 bytes per block), a rank model's weights (about 30 KB) and the
+ *     are taken with plain cudaMalloc instead: a block tree's point and block tables
+ *     (n * dim * 8 + 32 bytes per block, shared by every handle on that tree, so they may
+ *     outlive the stream they were made on), a rank model's weights (about 30 KB) and the
  *     optimizer state of hmat_rankmodel_train (freed before it returns).
  *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream). Work is
  *     enqueued on it; calls that read results back to the host synchronise it (stated per call).
@@ -180,9 +180,10 @@ typedef struct {
 
 /* Synthetic inputs (the paper's experiments, Sec. 6.1, use Galerkin matrices on the unit sphere;
  * seeded point sets in a cube or on the sphere stand in for them). Fill xyz (n*dim doubles,
- * row-major, caller-owned) with the seeded points of the given distribution: splitmix64 stream of `seed`, u = (z >> 11) * 2^-53; cube: point i uses draws
- * dim*i .. dim*i+dim-1; sphere: draws 2i, 2i+1 -> z = 2u1 - 1, phi = 2 pi u2,
- * (sqrt(1-z^2) cos phi, sqrt(1-z^2) sin phi, z). EINVAL on a bad dim/n or NULL xyz. */
+ * row-major, caller-owned) with the seeded points of the given distribution: splitmix64 stream
+ * of `seed`, u = (z >> 11) * 2^-53; cube: point i uses draws dim*i .. dim*i+dim-1; sphere: draws
+ * 2i, 2i+1 -> z = 2u1 - 1, phi = 2 pi u2, (sqrt(1-z^2) cos phi, sqrt(1-z^2) sin phi, z).
+ * EINVAL on a bad dim/n, an unknown distribution or NULL xyz. */
 hmat_status hmat_points(hmat_ptdist dist, int dim, int64_t n, uint64_t seed, double *xyz);
 
 /* Build the H-matrix of kernel `kernel` on the points xyz (n x dim, row-major, original
@@ -191,8 +192,8 @@ hmat_status hmat_points(hmat_ptdist dist, int dim, int64_t n, uint64_t seed, dou
  * far leaves by ACA (Algorithm 6) on the GPU. If tree_from is not NULL its cluster and block
  * tree are reused (xyz must then hold the same points; only kernel and factors differ), which
  * is how two factors of a product are put on one block tree (Sec. 3). Synchronises `stream`
- * once (to size the far-leaf storage). EINVAL on bad sizes (n must be below 2^31), NaN/Inf points or opts;
- * EMISMATCH if tree_from was built on other points. */
+ * once (to size the far-leaf storage). EINVAL on bad sizes (n must be below 2^31), NaN/Inf
+ * points, an unknown kernel or bad opts; EMISMATCH if tree_from was built on other points. */
 hmat_status hmat_build(const double *xyz, int64_t n, int dim, hmat_kernel kernel,
                        const hmat_build_opts *opts, const hmat_t tree_from, void *stream,
                        hmat_t *out);
@@ -268,9 +269,8 @@ hmat_status hmat_multiply_batched(const hmat_t *A, const hmat_t *B, int count, c
 
 /* Dense copy of the whole matrix (every leaf of the block tree expanded as in the definition of
  * H(B, k), Sec. 2: U V^T on far leaves, the stored block on near leaves) in ORIGINAL point order
- * into the host buffer out
- * (column-major, leading dimension ld >= n). Synchronises `stream` of the handle's last
- * use. Intended for checking small problems. */
+ * into the host buffer out (column-major, leading dimension ld >= n). Synchronises `stream` of
+ * the handle's last use. Intended for checking small problems. */
 hmat_status hmat_to_dense(const hmat_t h, double *out, int64_t ld);
 
 /* Number of leaves of the block tree (far + near), numbered in depth-first order. */
@@ -317,10 +317,10 @@ hmat_status hmat_sumexpr_counts(const hmat_t A, const hmat_t B, int64_t *n_lowra
 hmat_status hmat_rank_features(const hmat_t A, const hmat_t B, double eps, const hmat_t C, float *features,
                                float *ranks, int64_t *n_far);
 
-/* The learned rank proposal (no counterpart in the paper, whose Algorithm 8 starts every block
- * from one sample): a small network predicts a far block's eps-rank from its features, and the
- * product uses the prediction only to size the first sampling round; the stop test and the final
- * truncation still decide rank and error.
+/* The learned rank proposal (no counterpart in the paper, whose Algorithm 8 keeps drawing samples
+ * until its stop test holds, with no prior guess of the rank): a small network predicts a far
+ * block's eps-rank from its features, and the product uses the prediction only to size the first
+ * sampling round; the stop test and the final truncation still decide rank and error.
  *
  * Train a rank model on the GPU on (features, ranks) samples (host arrays, count rows): features
  * are standardised with the sample mean and deviation, the target is log2(1 + rank), the loss

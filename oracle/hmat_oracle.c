@@ -595,6 +595,76 @@ int64_t or_eps_rank(const double *s, int64_t p, double eps) {
   return k;
 }
 
+/* Singular values of an m x n column-major M whose numerical rank is far below min(m, n)
+ * (the large far blocks of a product). Householder QR with column pivoting (Businger and
+ * Golub 1965; Golub and Van Loan, "Matrix Computations", Sec. 5.4.1): at step j the remaining
+ * column of largest norm is swapped into place and reflected onto e_j; the column norms are
+ * recomputed exactly at every step. The factorisation stops at the first step whose remaining
+ * (m - j) x (n - j) block has Frobenius norm <= tol * ||M||_F. The singular values of the k
+ * leading rows of R are those of M P Q-rotated with the remaining block set to zero; they come
+ * from the one-sided Jacobi SVD above. Writes them (descending) to s (room for min(m, n)),
+ * returns k and sets *resid to the remaining block's Frobenius norm, which bounds the dropped
+ * energy: sum_{i >= k} s_i(M)^2 <= resid^2 (the best rank-k error is at most that of Q R_k P^T). */
+int64_t or_svd_values_qrcp(const double *M, int64_t m, int64_t n, double tol, double *s, double *resid) {
+  int64_t p = m < n ? m : n;
+  double *A = (double *)malloc(sizeof(double) * (m * n > 0 ? m * n : 1));
+  double *cn = (double *)malloc(sizeof(double) * (n > 0 ? n : 1));
+  double *v = (double *)malloc(sizeof(double) * (m > 0 ? m : 1));
+  double fro2 = 0.0;
+  for (int64_t i = 0; i < m * n; i++) { A[i] = M[i]; fro2 += M[i] * M[i]; }
+  double rem = 0.0;
+  int64_t k = 0;
+  for (int64_t j = 0; j < p; j++) {
+#pragma omp parallel for schedule(static)
+    for (int64_t c = j; c < n; c++) {
+      double t = 0.0;
+      for (int64_t r = j; r < m; r++) t += A[c * m + r] * A[c * m + r];
+      cn[c] = t;
+    }
+    rem = 0.0;
+    int64_t piv = j;
+    for (int64_t c = j; c < n; c++) {
+      rem += cn[c];
+      if (cn[c] > cn[piv]) piv = c;
+    }
+    if (sqrt(rem) <= tol * sqrt(fro2)) break;
+    if (piv != j)
+      for (int64_t r = 0; r < m; r++) { double t = A[j * m + r]; A[j * m + r] = A[piv * m + r]; A[piv * m + r] = t; }
+    /* reflector H = I - 2 v v^T / (v^T v) with H x = alpha e_1, x = A[j:m, j] */
+    double nx = 0.0;
+    for (int64_t r = j; r < m; r++) nx += A[j * m + r] * A[j * m + r];
+    nx = sqrt(nx);
+    double x0 = A[j * m + j];
+    double alpha = x0 >= 0.0 ? -nx : nx;
+    v[j] = x0 - alpha;
+    double vtv = v[j] * v[j];
+    for (int64_t r = j + 1; r < m; r++) { v[r] = A[j * m + r]; vtv += v[r] * v[r]; }
+    if (vtv > 0.0) {
+#pragma omp parallel for schedule(static)
+      for (int64_t c = j + 1; c < n; c++) {
+        double d = 0.0;
+        for (int64_t r = j; r < m; r++) d += v[r] * A[c * m + r];
+        double f = 2.0 * d / vtv;
+        for (int64_t r = j; r < m; r++) A[c * m + r] -= f * v[r];
+      }
+    }
+    A[j * m + j] = alpha;
+    for (int64_t r = j + 1; r < m; r++) A[j * m + r] = 0.0;
+    k = j + 1;
+    rem = 0.0;
+  }
+  *resid = sqrt(rem);
+  if (k > 0) {
+    double *R = (double *)malloc(sizeof(double) * k * n);
+    for (int64_t c = 0; c < n; c++)
+      for (int64_t r = 0; r < k; r++) R[c * k + r] = r <= c ? A[c * m + r] : 0.0;
+    or_svd(R, k, n, s, NULL, NULL);
+    free(R);
+  }
+  free(A); free(cn); free(v);
+  return k;
+}
+
 /* ------------------------------------------------------------------ */
 /* Sum-expressions by Algorithm 3 / Algorithm 4                        */
 /* ------------------------------------------------------------------ */

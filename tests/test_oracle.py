@@ -287,6 +287,79 @@ def test_svd_rank_deficient_and_zero(oracle):
     assert (s == 0).all()
 
 
+def _with_spectrum(rng, m, n, s):
+    """An m x n matrix with the given singular values (random orthonormal factors)."""
+    k = len(s)
+    U, _ = np.linalg.qr(rng.standard_normal((m, k)))
+    V, _ = np.linalg.qr(rng.standard_normal((n, k)))
+    return (U * s) @ V.T
+
+
+@pytest.mark.parametrize("m,n", [(200, 150), (150, 200), (257, 257)])
+def test_svd_values_qrcp_against_jacobi_and_lapack(oracle, m, n):
+    """The pivoted-QR singular values: equal to the full one-sided Jacobi's and to LAPACK's above
+    the stopping level; the undetermined remainder bounds the dropped energy (the best rank-k
+    error cannot exceed that of the truncated factorisation)."""
+    rng = np.random.default_rng(m + 7 * n)
+    sv = np.logspace(0, -15, 40)
+    M = _with_spectrum(rng, m, n, sv) + 1e-16 * rng.standard_normal((m, n))
+    s, resid = oracle.svd_values_lowrank(M, tol=1e-13)
+    s_full, _, _ = oracle.svd(M, vectors=False)
+    s_ref = np.linalg.svd(M, compute_uv=False)
+    k = len(s)
+    assert 0 < k < 40
+    assert np.abs(s - s_full[:k]).max() <= 1e-13 * s_full[0]
+    assert np.abs(s - s_ref[:k]).max() <= 1e-13 * s_ref[0]
+    nf = np.linalg.norm(M)
+    assert resid <= 1e-13 * nf
+    assert np.sum(s_ref[k:] ** 2) <= resid ** 2 * (1 + 1e-6) + 1e-30
+    # the remainder is the part the pivoted factorisation could not yet drop: it is not much
+    # below the stopping level (the step before met none of it)
+    assert s[-1] >= 1e-13 * nf * 1e-3
+
+
+def test_svd_values_qrcp_exact_rank_zero_and_full(oracle):
+    rng = np.random.default_rng(11)
+    sv = np.array([5.0, 2.0, 1.0, 1e-3, 1e-6])
+    M = _with_spectrum(rng, 90, 70, sv)
+    s, resid = oracle.svd_values_lowrank(M, tol=1e-13)
+    assert len(s) == 5 and np.abs(s - sv).max() <= 1e-13 * sv[0] and resid <= 1e-13 * np.linalg.norm(M)
+    s, resid = oracle.svd_values_lowrank(np.zeros((20, 30)))
+    assert len(s) == 0 and resid == 0.0
+    # tol = 0: every step runs (up to an exactly zero remainder); the values are the full SVD's
+    M = rng.standard_normal((25, 12))
+    s, resid = oracle.svd_values_lowrank(M, tol=0.0)
+    assert len(s) == 12 and resid == 0.0
+    assert np.abs(s - np.linalg.svd(M, compute_uv=False)).max() <= 1e-13 * s[0]
+    # column pivoting matters: a tiny column first and a dominant one last
+    M = np.zeros((10, 3))
+    M[:, 0] = 1e-9 * rng.standard_normal(10)
+    M[:, 2] = rng.standard_normal(10)
+    s, resid = oracle.svd_values_lowrank(M, tol=1e-6)
+    assert len(s) == 1 and abs(s[0] - np.linalg.norm(M[:, 2])) <= 1e-14 * s[0]
+
+
+def test_truth_for_large_block_matches_full_svd(oracle):
+    """truth_for_block on a block above QRCP_MIN: the eps-rank and tail equal those of the
+    full one-sided Jacobi SVD of the same exact product block."""
+    P = inputs.points(1, 3, 8192, 5)
+    T = oracle.Tree(P, 64, 1.0)
+    A = oracle.HMatrix(T, oracle.KERNEL_EXP, 1e-10)
+    sizes = np.array([T.leaf_ranges(l) for l in range(T.nleaf)])
+    big = [l for l in range(T.nleaf) if T.leaf_blocks[l, 2] == 1 and min(sizes[l, 1], sizes[l, 3]) >= oracle.QRCP_MIN]
+    assert big
+    l = big[0]
+    r0, m, c0, n = T.leaf_ranges(l)
+    blk = oracle.block_product(A, A, r0, m, c0, n)
+    s_full, _, _ = oracle.svd(blk, vectors=False)
+    for eps in (1e-4, 1e-6, 1e-8, 1e-10):
+        tr = oracle.truth_for_block(blk, eps, l)
+        assert len(tr.s) < min(m, n)          # the pivoted QR path was taken
+        assert tr.k_eps == oracle.eps_rank(s_full, eps)
+        assert abs(tr.tail - np.sqrt(np.sum(s_full[tr.k_eps:] ** 2))) <= 1e-12 * tr.norm
+        assert abs(tr.norm - np.linalg.norm(blk)) <= 1e-13 * tr.norm
+
+
 def test_eps_rank_closed_forms(oracle):
     s = np.array([1.0, 1e-3, 1e-7])
     tot = np.sqrt(np.sum(s ** 2))

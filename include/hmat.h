@@ -345,8 +345,10 @@ hmat_status hmat_rankmodel_create(const float *weights, const float *mean, const
 hmat_status hmat_rankmodel_grad(const hmat_rankmodel_t m, const float *features, const float *ranks, int64_t count,
                                 float *grad, float *loss);
 
-/* The same gradient and loss as hmat_rankmodel_grad, computed without allocating any device
- * memory (the paper has no counterpart of this call; it is a library convenience). It is for
+/* The same gradient and loss as hmat_rankmodel_grad (the same FP32 standardisation, the targets
+ * evaluated in FP64 and rounded to FP32; the sums differ only in the order of their atomic
+ * accumulation), computed without allocating any device memory (the paper has no counterpart
+ * of this call; it is a library convenience). It is for
  * callers that must not allocate: code that runs under a fixed device-memory budget or beside
  * an allocator it must not re-enter (a custom allocator hook that itself fine-tunes the model,
  * a serving loop whose memory is reserved up front), where a stray allocation can fail or
@@ -356,11 +358,12 @@ hmat_status hmat_rankmodel_grad(const hmat_rankmodel_t m, const float *features,
  *   - count must be 1 .. HMAT_RANKGRAD_NOALLOC_MAX; more samples -> HMAT_EINVAL, nothing runs;
  *   - features (count x HMAT_RANK_FEATURES, row-major) and ranks (count) are raw host values,
  *     standardised on the device with the model's mean and deviation; grad
- *     (HMAT_RANK_PARAMS) and *loss are host outputs;
+ *     (HMAT_RANK_PARAMS) and *loss are host outputs; loss may be NULL;
  *   - the gradient and loss accumulators in the array are set to zero by every call before
  *     it accumulates, so no state carries over between calls;
- *   - the first call on a device (with that device current) looks up the array's device
- *     address and sets the network kernel's shared-memory limit; make one call before any
+ *   - every call looks up the array's address on the current device (cudaGetSymbolAddress,
+ *     which allocates nothing) and sets the network kernel's shared-memory limit; the first
+ *     call on a device also loads the library's kernels there, so make one call before any
  *     stream capture begins;
  *   - calls on one device share the array: two calls that overlap in time (other threads,
  *     other streams) race on it and may return wrong results; serialise them;

@@ -453,17 +453,44 @@ static void dense_rec(const or_hmat *h, int b, int64_t r0, int64_t mr, int64_t c
     for (int c = 0; c < bk->nchild; c++) dense_rec(h, bk->child[c], r0, mr, c0, nc, out, ld);
     return;
   }
-  for (int64_t j = b0; j < b1; j++)
-    for (int64_t i = a0; i < a1; i++)
-      out[(j - c0) * ld + (i - r0)] = leaf_entry(h, bk->leaf, i - ct->begin, j - cs->begin);
+  if (bk->kind == 2) {
+    for (int64_t j = b0; j < b1; j++)
+      for (int64_t i = a0; i < a1; i++)
+        out[(j - c0) * ld + (i - r0)] = leaf_entry(h, bk->leaf, i - ct->begin, j - cs->begin);
+    return;
+  }
+  /* far leaf: the same sums as leaf_entry (over q in ascending order), column by column */
+  const int64_t m = ct->size, n = cs->size;
+  const double *U = h->U[bk->leaf], *V = h->V[bk->leaf];
+  for (int64_t j = b0; j < b1; j++) {
+    double *o = out + (j - c0) * ld - r0;
+    for (int64_t i = a0; i < a1; i++) o[i] = 0.0;
+    for (int q = 0; q < h->rank[bk->leaf]; q++) {
+      const double vj = V[q * n + (j - cs->begin)];
+      const double *u = U + q * m - ct->begin;
+      for (int64_t i = a0; i < a1; i++) o[i] += u[i] * vj;
+    }
+  }
 }
 
+/* The window is cut along its longer side into parts filled on separate threads; every entry
+ * is the same leaf_entry value either way. */
 void or_hmat_dense_sub(const void *hh, int64_t r0, int64_t mr, int64_t c0, int64_t nc,
                        double *out, int64_t ld) {
   const or_hmat *h = (const or_hmat *)hh;
   for (int64_t j = 0; j < nc; j++)
     for (int64_t i = 0; i < mr; i++) out[j * ld + i] = 0.0;
-  dense_rec(h, 0, r0, mr, c0, nc, out, ld);
+  int by_cols = nc >= mr;
+  int64_t len = by_cols ? nc : mr;
+  int64_t parts = len >= 1024 ? 64 : 1;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t q = 0; q < parts; q++) {
+    int64_t lo = len * q / parts, hi = len * (q + 1) / parts;
+    if (by_cols)
+      dense_rec(h, 0, r0, mr, c0 + lo, hi - lo, out + lo * ld, ld);
+    else
+      dense_rec(h, 0, r0 + lo, hi - lo, c0, nc, out + lo, ld);
+  }
 }
 
 /* ------------------------------------------------------------------ */

@@ -231,6 +231,27 @@ def block_product(A: HMatrix, B: HMatrix, r0: int, m: int, c0: int, n: int, chun
     return out.T.copy()
 
 
+def block_product_blas(A: HMatrix, B: HMatrix, r0: int, m: int, c0: int, n: int, chunk: int = 0) -> np.ndarray:
+    """The exact block C|tau x sigma = A|tau x I * B|I x sigma, as block_product computes it, with
+    the row slab of A and the column slab of B densified chunk by chunk by the oracle's own leaf
+    evaluation and each chunk's product taken by numpy's matmul (BLAS) as a library primitive.
+    For the samples of the largest products (N = 524288), where the plain loop takes seconds
+    per block. The default chunk keeps each slab near 256 MB."""
+    N = A.tree.n
+    if chunk <= 0:
+        chunk = max(8192, min(N, (1 << 25) // max(m, n, 1)))
+    chunk = min(chunk, max(N, 1))
+    out = np.zeros((m, n), np.float64)
+    Ab = np.empty((m, chunk), np.float64, order="F")   # column-major, leading dimension m
+    for k0 in range(0, N, chunk):
+        kc = min(chunk, N - k0)
+        Bb = np.empty((kc, n), np.float64, order="F")  # column-major, leading dimension kc
+        lib().or_hmat_dense_sub(A._h, r0, m, k0, kc, Ab.ctypes.data_as(_PD), m)
+        lib().or_hmat_dense_sub(B._h, k0, kc, c0, n, Bb.ctypes.data_as(_PD), kc)
+        out += Ab[:, :kc] @ Bb
+    return out
+
+
 def svd(M: np.ndarray, vectors: bool = True):
     """One-sided Jacobi SVD (own code). Returns (s, U, V) with M = U diag(s) V^T."""
     M = np.asfortranarray(M, dtype=np.float64)

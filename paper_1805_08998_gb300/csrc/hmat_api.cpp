@@ -964,7 +964,7 @@ hmat_status hmat_rankmodel_grad(const hmat_rankmodel_t m, const float *features,
 hmat_status hmat_rankmodel_grad_noalloc(const hmat_rankmodel_t m, const float *features, const float *ranks,
                                         int64_t count, float *grad, float *loss, void *stream) {
   return guard([&] {
-    if (!m || !features || !ranks || !grad || !loss || count < 1) fail(HMAT_EINVAL, "NULL argument or no samples");
+    if (!m || !features || !ranks || !grad || count < 1) fail(HMAT_EINVAL, "NULL argument or no samples");
     if (count > HMAT_RANKGRAD_NOALLOC_MAX)
       fail(HMAT_EINVAL, "count exceeds HMAT_RANKGRAD_NOALLOC_MAX (16384 samples), the capacity of the fixed scratch");
     ck(mlp_grad_noalloc(m->w16, m->mean, m->dev, features, ranks, (int)count, grad, loss, (cudaStream_t)stream),

@@ -6,7 +6,6 @@
 // it for the requested number of epochs.
 #include <cmath>
 #include <cstdint>
-#include <mutex>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
@@ -282,35 +281,28 @@ struct Standardise {
   float mean[F], dev[F];
 };
 
-// in place: x <- (x - mean) / dev per feature; y <- log2(1 + max(y, 0))
+// in place: x <- (x - mean) / dev per feature (FP32, as the allocating call does on the host);
+// y <- log2(1 + max(y, 0)), evaluated in FP64 and rounded to FP32 like the allocating call's
+// targets
 __global__ void k_standardise(float *x, float *y, int count, Standardise sd) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < count * F) {
     const int k = i % F;
     x[i] = (x[i] - sd.mean[k]) / sd.dev[k];
   }
-  if (i < count) y[i] = log2f(1.f + fmaxf(y[i], 0.f));
+  if (i < count) y[i] = (float)log2(1.0 + fmax((double)y[i], 0.0));
 }
 
-// The scratch array's device address, looked up once per device (with that device current) on
-// the first call made on it; later calls on the device reuse it.
-constexpr int NOALLOC_DEVICES = 64;
-static std::mutex g_noalloc_mu;
-static float *g_noalloc_ptr[NOALLOC_DEVICES];
-
+// The scratch array's device address on the current device. It is looked up on every call
+// (cudaGetSymbolAddress allocates nothing): a cached address would go stale if the device's
+// primary context were reset and the module reloaded. The network kernel's shared-memory limit
+// is set on every call for the same reason.
 static cudaError_t noalloc_scratch(float **out) {
-  int d = 0;
-  cudaError_t e = cudaGetDevice(&d);
+  float *p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress((void **)&p, g_noalloc_scratch);
   if (e != cudaSuccess) return e;
-  if (d < 0 || d >= NOALLOC_DEVICES) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lk(g_noalloc_mu);
-  if (!g_noalloc_ptr[d]) {
-    float *p = nullptr;
-    if ((e = cudaGetSymbolAddress((void **)&p, g_noalloc_scratch)) != cudaSuccess) return e;
-    if ((e = set_mlp_smem()) != cudaSuccess) return e;
-    g_noalloc_ptr[d] = p;
-  }
-  *out = g_noalloc_ptr[d];
+  if ((e = set_mlp_smem()) != cudaSuccess) return e;
+  *out = p;
   return cudaSuccess;
 }
 
@@ -334,7 +326,7 @@ cudaError_t mlp_grad_noalloc(const void *w16, const float *mean, const float *de
   // the gradient and the loss are accumulated with atomics: mlp_grad_ops first sets both to zero
   if ((e = mlp_grad_ops(w16, x, y, count, g, l, s))) return e;
   if ((e = cudaMemcpyAsync(grad, g, sizeof(float) * RANK_PARAMS, cudaMemcpyDeviceToHost, s))) return e;
-  if ((e = cudaMemcpyAsync(loss, l, sizeof(float), cudaMemcpyDeviceToHost, s))) return e;
+  if (loss && (e = cudaMemcpyAsync(loss, l, sizeof(float), cudaMemcpyDeviceToHost, s))) return e;
   return cudaStreamSynchronize(s);
 }
 

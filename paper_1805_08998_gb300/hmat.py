@@ -292,6 +292,28 @@ def hmat_multiply_batched(As, Bs, eps: float, mode: int = MODE_F64, rank_proposa
     return out
 
 
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+_allocator_refs = None  # the callbacks handed to the library, kept alive while it may call them
+
+
+def hmat_set_allocator(alloc=None, free=None) -> None:
+    """Route the library's device allocations through alloc(nbytes, stream) -> device pointer
+    (int; 0 or None for failure) and free(ptr); both None restores the default pool. The callables
+    must not raise (an exception inside a C callback is printed and ignored)."""
+    global _allocator_refs
+    if (alloc is None) != (free is None):
+        raise _shape_error("alloc and free must both be given or both be None")
+    if alloc is None:
+        _check(lib().hmat_set_allocator(None, None, None))
+        _allocator_refs = None
+        return
+    a = ALLOC_FN(lambda nbytes, stream, ctx: alloc(nbytes, stream) or None)
+    f = FREE_FN(lambda ptr, ctx: free(ptr))
+    _check(lib().hmat_set_allocator(a, f, None))
+    _allocator_refs = (a, f)
+
+
 def hmat_matvec(Hm: HMatrix, x, stream=None) -> np.ndarray:
     """y = H x for x of shape (n,) or (n, ncols), original point order."""
     x = np.asarray(x, np.float64)
@@ -437,15 +459,17 @@ class RankModel:
         return g, loss.value
 
 
-def hmat_rankmodel_grad_noalloc(model: RankModel, features, ranks, stream=None):
+def hmat_rankmodel_grad_noalloc(model: RankModel, features, ranks, stream=None, want_loss: bool = True):
     """hmat_rankmodel_grad without device allocation (fixed scratch; at most
-    RANKGRAD_NOALLOC_MAX samples; concurrent calls on one device race)."""
+    RANKGRAD_NOALLOC_MAX samples; concurrent calls on one device race). With want_loss=False the
+    loss pointer is NULL and the loss returned is None."""
     X, y = _samples(features, ranks)
     g = np.zeros(RANK_PARAMS, np.float32)
     loss = ctypes.c_float()
     _check(lib().hmat_rankmodel_grad_noalloc(model.handle, X.ctypes.data_as(_PF), y.ctypes.data_as(_PF), X.shape[0],
-                                             g.ctypes.data_as(_PF), ctypes.byref(loss), _stream_ptr(stream)))
-    return g, loss.value
+                                             g.ctypes.data_as(_PF), ctypes.byref(loss) if want_loss else None,
+                                             _stream_ptr(stream)))
+    return g, (loss.value if want_loss else None)
 
 
 def hmat_rank_features(A: HMatrix, B: HMatrix, eps: float, C: HMatrix | None = None):

@@ -23,7 +23,10 @@ products D X and D^T Y with vectors or blocks of vectors. Random numbers are inp
       Algorithm 8 (Sec. 4.3) in its blocked form: each round samples Y = D Omega_round (the next
       p columns of omega), projects Y twice against the basis Q, orthonormalizes the new columns
       by Gram-Schmidt applied twice and drops a column whose remaining norm is at most
-      0.1 eps ||D||_est (||D||_est^2 = ||Y_0||_F^2 / p from the first round), and appends
+      0.1 eps ||D||_est (||D||_est^2 = ||Y_0||_F^2 / p from the first round); a kept column left
+      with less than kappa = 1000 u / eps of its original norm is projected once more against the
+      whole basis before it is normalised (Alg. 8 orthogonalises every new sample against all
+      earlier ones; at eps = 1e-12 the block form otherwise loses orthogonality), and appends
       W_new = D^T Q_new. It stops when ||W_new||_F <= (eps/2) ||W_old||_F (eq. (truncaca) with the
       block's energy), when no column is kept, when Q has min(m, n) columns, or when the next round
       would pass rmax columns. Returns (Q, W = D^T Q, rounds).
@@ -157,6 +160,24 @@ def _gs2_drop(Y: np.ndarray, drop: float) -> np.ndarray:
     return np.array(kept).T if kept else np.zeros((Y.shape[0], 0))
 
 
+def _gs2_drop_recheck(Y: np.ndarray, drop: float, Q: np.ndarray, ny: np.ndarray, kappa: float) -> np.ndarray:
+    """_gs2_drop for the columns of a sample block already projected against the basis Q; a kept
+    column left with less than kappa of its original norm ny[j] is projected once more against
+    the whole basis (Q and the columns kept before it), since its components along Q, of the
+    order of the rounding of ny[j], grow by ny[j] / ||v|| when it is normalised."""
+    kept = []
+    for j in range(Y.shape[1]):
+        v = _orth2(Y[:, j].copy(), kept)
+        nv = float(np.linalg.norm(v))
+        if drop < nv < kappa * ny[j]:
+            B = np.hstack([Q] + ([np.array(kept).T] if kept else []))
+            v = v - B @ (B.T @ v)
+            nv = float(np.linalg.norm(v))
+        if nv > drop:
+            kept.append(v / nv)
+    return np.array(kept).T if kept else np.zeros((Y.shape[0], 0))
+
+
 def randomized(D: np.ndarray, omega: np.ndarray, eps: float, p: int, rmax: int):
     """Blocked adaptive range finder of D with the Gaussian columns omega (n x >= rounds * p)."""
     D = np.asarray(D, np.float64)
@@ -171,11 +192,12 @@ def randomized(D: np.ndarray, omega: np.ndarray, eps: float, p: int, rmax: int):
             break
         rounds += 1
         Y = D @ Om
+        ny = np.linalg.norm(Y, axis=0)
         if est is None:
             est = np.sqrt(float(np.sum(Y * Y)) / p)
         for _ in range(2):
             Y = Y - Q @ (Q.T @ Y)
-        Qn = _gs2_drop(Y, 0.1 * eps * est)
+        Qn = _gs2_drop_recheck(Y, 0.1 * eps * est, Q, ny, 1000.0 * 2.0 ** -53 / eps)
         if Qn.shape[1] == 0:
             break
         Wn = D.T @ Qn

@@ -339,6 +339,23 @@ def test_svd_values_qrcp_exact_rank_zero_and_full(oracle):
     assert len(s) == 1 and abs(s[0] - np.linalg.norm(M[:, 2])) <= 1e-14 * s[0]
 
 
+def test_block_product_blas_matches_plain_loop(oracle):
+    """The BLAS-chunked exact block equals the oracle's plain loop and the dense product."""
+    P = inputs.points(1, 3, 3000, 2)
+    T = oracle.Tree(P, 32, 1.0)
+    A = oracle.HMatrix(T, oracle.KERNEL_EXP, 1e-8)
+    B = oracle.HMatrix(T, oracle.KERNEL_INVQ, 1e-8)
+    DC = oracle.matmul(A.dense(), B.dense())
+    sizes = np.array([T.leaf_ranges(l) for l in range(T.nleaf)])
+    far = np.nonzero(T.leaf_blocks[:, 2] == 1)[0]
+    for l in [far[0], far[len(far) // 2], far[np.argmax(sizes[far, 1])], int(np.nonzero(T.leaf_blocks[:, 2] == 2)[0][0])]:
+        r0, m, c0, n = T.leaf_ranges(int(l))
+        ref = oracle.block_product(A, B, r0, m, c0, n)
+        got = oracle.block_product_blas(A, B, r0, m, c0, n, chunk=700)
+        assert np.abs(got - ref).max() <= 1e-13 * np.abs(ref).max()
+        assert np.abs(got - DC[r0:r0 + m, c0:c0 + n]).max() <= 1e-13 * np.abs(ref).max()
+
+
 def test_truth_for_large_block_matches_full_svd(oracle):
     """truth_for_block on a block above QRCP_MIN: the eps-rank and tail equal those of the
     full one-sided Jacobi SVD of the same exact product block."""
@@ -686,3 +703,29 @@ def test_fixed_rank_subspace_iteration():
         assert np.abs(L.T @ L - np.eye(L.shape[1])).max() <= 1e-12
         err = np.linalg.norm(G - L @ U.T)
         assert best <= err * (1 + 1e-12) and err <= 1.01 * best, (q, err, best)
+
+
+def test_randomized_meets_paper_eps_on_product_blocks(oracle):
+    """The blocked Alg. 8 at the paper's eps = 1e-12 (Sec. 6) on exact far blocks of a product of
+    ACA inputs (N = 2048 in 2-D, exp(-r), ACA to 1e-14): every block within 1.5 eps of the block
+    at rank <= eps-rank + 2 (numpy's SVD). Without the final projection of a column that kept
+    little of its norm against the whole basis, the basis loses orthogonality at this eps and
+    190 of these 1262 blocks miss the bar."""
+    from oracle import compressors as CO
+    P = inputs.points(0, 2, 2048, 0)
+    T = oracle.Tree(P, 32, 1.0)
+    A = oracle.HMatrix(T, oracle.KERNEL_EXP, 1e-14)
+    DC = oracle.matmul(A.dense(), A.dense())
+    eps = 1e-12
+    far = T.far_leaves()
+    for l in far[::4]:
+        l = int(l)
+        r0, m, c0, n = T.leaf_ranges(l)
+        D = DC[r0:r0 + m, c0:c0 + n]
+        om = np.random.default_rng(1000 + l).standard_normal((n, 400))
+        Q, W, _ = CO.randomized(D, om, eps, 8, 96)
+        L, U = CO.truncate(Q, W, eps)
+        s = np.linalg.svd(D, compute_uv=False)
+        err = np.linalg.norm(D - L @ U.T) / np.linalg.norm(D)
+        assert err <= 1.5 * eps, (l, err)
+        assert L.shape[1] <= oracle.eps_rank(s, eps) + 2

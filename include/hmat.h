@@ -176,6 +176,16 @@ typedef struct {
   int64_t sample_passes;         /* sum over far blocks of the rounds each one took part in
                                     (cross approximation: crosses; Lanczos: steps) */
   int64_t groups;                /* subtree groups the product ran in (1: one pass) */
+  double bytes_apply_unique;     /* the minimum bytes of the same launches: per pass, every stored
+                                    factor element that an active target's sum-expression
+                                    references counted once (the rows of a term's factors in the
+                                    union of its active targets' clusters; an H-pair block once),
+                                    plus the In/Out panels */
+  int64_t apply_gstage_targets;  /* far targets whose application panels were staged in global
+                                    memory (too large for shared memory) */
+  int64_t apply_split_targets;   /* far targets whose application was split over several thread
+                                    blocks (partial outputs added atomically) */
+  int apply_max_split;           /* the largest such split (thread blocks per target) */
 } hmat_stats_t;
 
 /* Synthetic inputs (the paper's experiments, Sec. 6.1, use Galerkin matrices on the unit sphere;

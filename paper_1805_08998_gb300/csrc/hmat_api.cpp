@@ -194,6 +194,170 @@ std::vector<double> block_storage(const Tree &t, const std::vector<LeafDev> &lv)
   return st;
 }
 
+// Unique elements of the sum-expression applications, summed over the passes of a product (the
+// algorithmic minimum of what a pass must read and write): in each pass, every stored factor
+// element that an active target's sum-expression references counts once, plus the targets' In
+// and Out panels ((m + n) * pcols elements each).
+//  - A low-rank term created at block beta reaches the targets below beta by index shift, so a
+//    pass reads the rows of its factors that lie in the union of the row clusters (column
+//    clusters) of the active targets below beta.
+//  - A factor of an input leaf that several terms share (U of A's leaf, V of B's leaf) counts the
+//    union over all of them once.
+//  - The H-pair blocks of A and of B count their stored elements once per pass; a block inside
+//    another referenced block adds nothing.
+// Unions of clusters are bitsets over the leaf clusters (every leaf of the cluster tree sits on
+// level depth), built bottom-up over the block tree: children are tau-major and have larger ids
+// than their parents. Target i is active in passes 0 .. 2 max(1, rounds_of[i]) - 1, the count
+// bytes_apply_use uses; the S and S^T passes of a round share their active set.
+double apply_unique_elems(const Tree &t, const Plan &plan, const std::vector<LeafDev> &lA,
+                          const std::vector<LeafDev> &lB, const std::vector<double> &storA,
+                          const std::vector<double> &storB, const std::vector<TargetDev> &tg,
+                          const std::vector<PairDev> &pairs, const std::vector<int32_t> &rounds_of, int pcols) {
+  const size_t nf = tg.size(), ncl = t.cl.size(), nblk = t.bl.size();
+  if (nf == 0) return 0.0;
+  const int D = t.depth;
+  const size_t nlc = (size_t)1 << D;
+  std::vector<int32_t> lc0(ncl, 0);  // first leaf cluster of every cluster (parents precede children)
+  std::vector<int64_t> lcs(nlc, 0);
+  for (size_t c = 0; c < ncl; c++) {
+    const Cluster &k = t.cl[c];
+    if (k.child[0] >= 0) {
+      lc0[k.child[0]] = lc0[c];
+      lc0[k.child[1]] = lc0[c] + (int32_t)(((int64_t)1 << (D - k.level)) / 2);
+    } else {
+      lcs[lc0[c]] = k.size;
+    }
+  }
+  std::vector<int64_t> pre(nlc + 1, 0);  // prefix sums of the leaf clusters' sizes
+  for (size_t i = 0; i < nlc; i++) pre[i + 1] = pre[i] + lcs[i];
+  auto nbits = [&](int level) { return (int64_t)1 << (D - level); };
+  auto nwords = [&](int level) { return (size_t)std::max<int64_t>(1, nbits(level) / 64); };
+  // points in the set bits of a bitset over the leaf clusters first .. first + nbits(level) - 1
+  auto points = [&](const uint64_t *w, int level, int32_t first) {
+    const int64_t nb = nbits(level);
+    int64_t sum = 0;
+    for (int64_t i0 = 0; i0 < nb; i0 += 64) {
+      uint64_t x = w[i0 >> 6];
+      if (nb >= 64 && x == ~0ull) {
+        sum += pre[first + i0 + 64] - pre[first + i0];
+        continue;
+      }
+      while (x) {
+        const int b = __builtin_ctzll(x);
+        if (i0 + b < nb) sum += lcs[first + i0 + b];
+        x &= x - 1;
+      }
+    }
+    return sum;
+  };
+  auto fill = [&](uint64_t *w, int level) {
+    const int64_t nb = nbits(level);
+    if (nb >= 64) std::fill(w, w + nb / 64, ~0ull);
+    else w[0] = (1ull << nb) - 1;
+  };
+  // OR the bitset of a child (half the bits) into half `half` of its parent's bitset
+  auto or_half = [&](uint64_t *dst, int dlevel, const uint64_t *src, int half) {
+    const int64_t sb = nbits(dlevel) / 2;
+    if (sb >= 64) {
+      const size_t sw = (size_t)sb / 64;
+      for (size_t w = 0; w < sw; w++) dst[half * sw + w] |= src[w];
+    } else {
+      dst[0] |= (src[0] & ((1ull << sb) - 1)) << (half * sb);
+    }
+  };
+  std::vector<size_t> bo(nblk + 1, 0);
+  for (size_t b = 0; b < nblk; b++) bo[b + 1] = bo[b] + nwords(t.bl[b].level);
+  std::vector<uint64_t> rows(bo[nblk]), cols(bo[nblk]);
+  auto leaf_words = [&](const std::vector<LeafDev> &lv, std::vector<size_t> &off) {
+    off.assign(lv.size() + 1, 0);
+    for (size_t l = 0; l < lv.size(); l++) off[l + 1] = off[l] + nwords(t.bl[t.leaf_block[l]].level);
+  };
+  std::vector<size_t> oa, ob;
+  leaf_words(lA, oa);
+  leaf_words(lB, ob);
+  std::vector<uint64_t> objA(oa.back()), objB(ob.back());
+  std::vector<int32_t> touchA, touchB, listA, listB;
+  std::vector<int32_t> markA(lA.size(), -1), markB(lB.size(), -1), stampA(nblk, -1), stampB(nblk, -1);
+  int rmax = 0;
+  for (size_t i = 0; i < nf; i++) rmax = std::max(rmax, std::max(1, rounds_of[i]));
+  double total = 0.0;
+  for (int j = 0; j < rmax; j++) {
+    std::fill(rows.begin(), rows.end(), 0ull);
+    std::fill(cols.begin(), cols.end(), 0ull);
+    double u = 0.0;
+    listA.clear();
+    listB.clear();
+    for (size_t i = 0; i < nf; i++) {
+      if (std::max(1, rounds_of[i]) <= j) continue;
+      const TargetDev &d = tg[i];
+      const int lev = t.bl[d.blk].level;
+      fill(&rows[bo[d.blk]], lev);
+      fill(&cols[bo[d.blk]], lev);
+      u += (double)(d.m + d.n) * pcols;
+      for (int32_t q = d.pair_lo; q < d.pair_hi; q++) {
+        const PairDev &pr = pairs[q];
+        if (stampA[pr.blkA] != j) { stampA[pr.blkA] = j; listA.push_back(pr.blkA); }
+        if (stampB[pr.blkB] != j) { stampB[pr.blkB] = j; listB.push_back(pr.blkB); }
+      }
+    }
+    for (int b = (int)nblk - 1; b >= 0; b--) {
+      const Block &bk = t.bl[b];
+      if (bk.kind != BK_INNER) continue;
+      for (int k = 0; k < bk.nchild; k++) {
+        const int c = bk.child[k];
+        or_half(&rows[bo[b]], bk.level, &rows[bo[c]], k / 2);
+        or_half(&cols[bo[b]], bk.level, &cols[bo[c]], k % 2);
+      }
+    }
+    touchA.clear();
+    touchB.clear();
+    for (size_t b = 0; b < nblk; b++) {
+      if (plan.blk_term_lo[b] == plan.blk_term_hi[b]) continue;
+      const Block &bk = t.bl[b];
+      const uint64_t *rw = &rows[bo[b]], *cw = &cols[bo[b]];
+      bool any = false;
+      for (size_t w = 0; w < nwords(bk.level) && !any; w++) any = rw[w] != 0;
+      if (!any) continue;
+      const size_t nw = nwords(bk.level);
+      for (int32_t q = plan.blk_term_lo[b]; q < plan.blk_term_hi[b]; q++) {
+        const PlanTerm &pt = plan.terms[q];
+        if (pt.type == JOB_FF_R || pt.type == JOB_FH) {  // L = U of A's leaf a (rows tau), R new
+          uint64_t *o = &objA[oa[pt.a]];
+          if (markA[pt.a] != j) { markA[pt.a] = j; std::fill(o, o + nw, 0ull); touchA.push_back(pt.a); }
+          for (size_t w = 0; w < nw; w++) o[w] |= rw[w];
+          u += (double)pt.rank * points(cw, bk.level, lc0[bk.sigma]);
+        } else {  // L new, R = V of B's leaf b (rows sigma)
+          uint64_t *o = &objB[ob[pt.b]];
+          if (markB[pt.b] != j) { markB[pt.b] = j; std::fill(o, o + nw, 0ull); touchB.push_back(pt.b); }
+          for (size_t w = 0; w < nw; w++) o[w] |= cw[w];
+          u += (double)pt.rank * points(rw, bk.level, lc0[bk.tau]);
+        }
+      }
+    }
+    for (int32_t a : touchA) {
+      const Block &bk = t.bl[t.leaf_block[a]];
+      u += (double)lA[a].rank * points(&objA[oa[a]], bk.level, lc0[bk.tau]);
+    }
+    for (int32_t b : touchB) {
+      const Block &bk = t.bl[t.leaf_block[b]];
+      u += (double)lB[b].rank * points(&objB[ob[b]], bk.level, lc0[bk.sigma]);
+    }
+    // H-pair blocks: only those with no referenced ancestor
+    for (int side = 0; side < 2; side++) {
+      const std::vector<int32_t> &lst = side ? listB : listA;
+      const std::vector<int32_t> &stp = side ? stampB : stampA;
+      const std::vector<double> &stor = side ? storB : storA;
+      for (int32_t b : lst) {
+        bool inside = false;
+        for (int p = t.bl[b].parent; p >= 0 && !inside; p = t.bl[p].parent) inside = stp[p] == j;
+        if (!inside) u += stor[b];
+      }
+    }
+    total += 2.0 * u;
+  }
+  return total;
+}
+
 void ensure_tree_device(Tree &t, cudaStream_t s) {
   if (t.d_pts) return;
   ck(cudaMalloc(&t.d_pts, sizeof(double) * t.pts.size()), "cudaMalloc points");
@@ -1719,6 +1883,15 @@ void Product::run() {
     cl.split = std::max(1, std::min(8, (int)std::ceil(ppt / 2.0)));
     if (split_env) cl.split = std::max(1, std::min(16, std::atoi(split_env)));
   }
+  for (int c = 0; c < NCLS; c++) {
+    if (cls[c].count == 0) continue;
+    if (c == 0) {
+      S.apply_gstage_targets += cls[c].count;
+    } else if (cls[c].split > 1) {
+      S.apply_split_targets += cls[c].count;
+      S.apply_max_split = std::max(S.apply_max_split, cls[c].split);
+    }
+  }
 
   // ---- a8 on a second stream, concurrent with the far-field rounds: C's buffer starts with the
   // near leaves (their offsets are known now); they are evaluated into a staging buffer that is
@@ -2024,10 +2197,12 @@ void Product::run() {
   std::vector<TargetState> st(nf);
   if (nf) ck(cudaMemcpyAsync(st.data(), d_st.p, sizeof(TargetState) * nf, cudaMemcpyDeviceToHost, s), "states");
   ck(cudaStreamSynchronize(s), "states");
+  std::vector<int32_t> rounds_of(nf);
   for (int i = 0; i < nf; i++) {
     S.first_round_cols += ftg[i].p0;
     if (st[i].nfwd <= 1 && st[i].rank != -2) S.done_in_first_round++;
     S.sample_passes += st[i].nfwd;
+    rounds_of[i] = st[i].nfwd;
   }
   {
     std::vector<int32_t> ids_small, ids_big;
@@ -2067,6 +2242,25 @@ void Product::run() {
       for (auto &e : fe) cudaEventDestroy(e);
     }
     launches += (ids_small.empty() ? 0 : 1) + (ids_big.empty() ? 0 : 1);
+    // the unique bytes of the passes, counted on the host while the device truncates
+    const double uniq = (double)es * apply_unique_elems(t, plan, A->leaves, B->leaves, storA, storB, ftg,
+                                                        fpairs, rounds_of, single ? 1 : p);
+    S.bytes_apply_unique += uniq;
+    if (tr.on) {  // each size class on its own: what separate launches of the classes must read
+      double sum = 0.0;
+      for (int c = 0; c < NCLS; c++) {
+        if (cls[c].count == 0) continue;
+        const std::vector<TargetDev> sub(ftg.begin() + cls[c].first, ftg.begin() + cls[c].first + cls[c].count);
+        const std::vector<int32_t> sr(rounds_of.begin() + cls[c].first,
+                                      rounds_of.begin() + cls[c].first + cls[c].count);
+        const double u = (double)es * apply_unique_elems(t, plan, A->leaves, B->leaves, storA, storB, sub, fpairs,
+                                                         sr, single ? 1 : p);
+        sum += u;
+        std::fprintf(stderr, "hmat trace: class %2d unique bytes over its passes %.4g GB\n", c, u * 1e-9);
+      }
+      std::fprintf(stderr, "hmat trace: unique bytes over all passes %.4g GB (classes on their own: %.4g GB)\n",
+                   uniq * 1e-9, sum * 1e-9);
+    }
     if (nf) ck(cudaMemcpyAsync(st.data(), d_st.p, sizeof(TargetState) * nf, cudaMemcpyDeviceToHost, s), "states");
     ck(cudaStreamSynchronize(s), "final");
   }

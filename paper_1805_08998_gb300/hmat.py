@@ -81,7 +81,9 @@ class Stats(ctypes.Structure):
                 ("bytes_apply_use", ctypes.c_double), ("launches", ctypes.c_int64),
                 ("n_ff_jobs", ctypes.c_int64), ("n_panels", ctypes.c_int64),
                 ("first_round_cols", ctypes.c_int64), ("done_in_first_round", ctypes.c_int64),
-                ("sample_passes", ctypes.c_int64), ("groups", ctypes.c_int64)]
+                ("sample_passes", ctypes.c_int64), ("groups", ctypes.c_int64),
+                ("bytes_apply_unique", ctypes.c_double), ("apply_gstage_targets", ctypes.c_int64),
+                ("apply_split_targets", ctypes.c_int64), ("apply_max_split", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -589,6 +589,14 @@ __global__ void __launch_bounds__(NT) k_gaussian(const TargetDev *tg, const Targ
 // a4: orthogonalisation of the new samples (FP64)
 // ---------------------------------------------------------------------------------------
 
+// A sample column projected against the basis keeps components along it of the order of the
+// rounding of its original norm, u ||y||, which normalisation scales by ||y|| / ||v||. A kept
+// column with ||v|| < kappa ||y||, kappa = 1000 u / eps, is therefore projected once more against
+// the whole basis (old and new columns) before it is normalised, so that the basis stays
+// orthonormal well below eps: about 1e-7 at eps = 1e-6 (rarely met: such columns are dropped),
+// about 0.1 at eps = 1e-12 (met by most late samples, whose energy is mostly in the basis).
+__device__ __forceinline__ double orth_recheck_ratio(double eps) { return 1000.0 * 0x1.0p-53 / eps; }
+
 // Q buffer of target b: qw + q_off, m x rmax FP64; the new columns are built in place at
 // columns r .. r+p-1. Also writes Q_new in T precision into x_base (input of the S^T pass).
 template <typename T>
@@ -599,6 +607,7 @@ __global__ void __launch_bounds__(NT) k_orth(const TargetDev *tg, const int32_t 
   constexpr int QCH = 64;  // basis columns projected per chunk
   __shared__ double Cm[QCH * PMAX];
   __shared__ double red[NT / 32];
+  __shared__ double ny2c[PMAX];  // each sample column's squared norm before any projection
   const int b = ids[blockIdx.x];
   if (st[b].active == 0) return;
   const TargetDev t = tg[b];
@@ -608,13 +617,18 @@ __global__ void __launch_bounds__(NT) k_orth(const TargetDev *tg, const int32_t 
   double *Q = qw + (side ? t.w_off : t.q_off);
   double *Y = Q + (int64_t)r * m;  // m x p workspace inside Q
   const T *Ys = y_base + t.y_off;
-  double part = 0.0;
-  for (int64_t o = threadIdx.x; o < m * p; o += NT) {
-    const double v = (double)Ys[o];
-    Y[o] = v;
-    part += v * v;
+  double ny2 = 0.0;
+  for (int c = 0; c < p; c++) {
+    double part = 0.0;
+    for (int64_t i = threadIdx.x; i < m; i += NT) {
+      const double v = (double)Ys[i + (int64_t)c * m];
+      Y[i + (int64_t)c * m] = v;
+      part += v * v;
+    }
+    const double nc = block_sum(part, red);
+    if (threadIdx.x == 0) ny2c[c] = nc;
+    ny2 += nc;
   }
-  const double ny2 = block_sum(part, red);
   if (round == 0 && threadIdx.x == 0) st[b].est2 = ny2 / p;
   __syncthreads();
   const double est2 = st[b].est2;
@@ -648,29 +662,58 @@ __global__ void __launch_bounds__(NT) k_orth(const TargetDev *tg, const int32_t 
   // drop = 0.1 * eps * sqrt(est2) carries negligible energy for the eps target and is dropped;
   // the block's kept columns are compacted to the front.
   const double drop2 = (0.1 * eps) * (0.1 * eps) * est2;
+  const double kappa = orth_recheck_ratio(eps), kappa2 = kappa * kappa;
   int kept = 0;
   for (int j = 0; j < p; j++) {
     double *y = Y + (int64_t)j * m;
-    for (int pass = 0; pass < 2 && kept > 0; pass++) {
-      const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-      for (int l = w; l < kept; l += NT / 32) {
-        const double *ql = Y + (int64_t)l * m;
-        double s = 0.0;
-        for (int64_t i = lane; i < m; i += 32) s += ql[i] * y[i];
-        for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
-        if (lane == 0) G[l] = s;
+    // passes 0, 1: against the columns kept in this round; pass 2 (only for a column that kept
+    // less than kappa of its norm): once more against the whole basis, old and new
+    double nrm2 = 0.0;
+    for (int pass = 0; pass < 3; pass++) {
+      if (pass == 2) {
+        if (!(nrm2 > drop2 && nrm2 < kappa2 * ny2c[j])) break;
+        const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        for (int c0 = 0; c0 < r; c0 += QCH) {
+          const int rc = min(QCH, r - c0);
+          for (int q = w; q < rc; q += NT / 32) {
+            const double *qc = Q + (int64_t)(c0 + q) * m;
+            double s = 0.0;
+            for (int64_t i = lane; i < m; i += 32) s += qc[i] * y[i];
+            for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+            if (lane == 0) Cm[q] = s;
+          }
+          __syncthreads();
+          for (int64_t i = threadIdx.x; i < m; i += NT) {
+            double s = 0.0;
+            for (int q = 0; q < rc; q++) s += Q[(int64_t)(c0 + q) * m + i] * Cm[q];
+            y[i] -= s;
+          }
+          __syncthreads();
+        }
       }
-      __syncthreads();
-      for (int64_t i = threadIdx.x; i < m; i += NT) {
-        double s = 0.0;
-        for (int l = 0; l < kept; l++) s += Y[i + (int64_t)l * m] * G[l];
-        y[i] -= s;
+      if (kept > 0) {
+        const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        for (int l = w; l < kept; l += NT / 32) {
+          const double *ql = Y + (int64_t)l * m;
+          double s = 0.0;
+          for (int64_t i = lane; i < m; i += 32) s += ql[i] * y[i];
+          for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+          if (lane == 0) G[l] = s;
+        }
+        __syncthreads();
+        for (int64_t i = threadIdx.x; i < m; i += NT) {
+          double s = 0.0;
+          for (int l = 0; l < kept; l++) s += Y[i + (int64_t)l * m] * G[l];
+          y[i] -= s;
+        }
+        __syncthreads();
       }
-      __syncthreads();
+      if (pass >= 1) {
+        double part2 = 0.0;
+        for (int64_t i = threadIdx.x; i < m; i += NT) part2 += y[i] * y[i];
+        nrm2 = block_sum(part2, red);
+      }
     }
-    double part2 = 0.0;
-    for (int64_t i = threadIdx.x; i < m; i += NT) part2 += y[i] * y[i];
-    const double nrm2 = block_sum(part2, red);
     if (nrm2 > drop2) {
       const double inv = 1.0 / sqrt(nrm2);
       double *dst = Y + (int64_t)kept * m;
@@ -716,13 +759,16 @@ __global__ void __launch_bounds__(NT) k_orth_warp(const TargetDev *tg, const int
   const bool v0 = i0 < m, v1 = i1 < m;
   double y[OW][2];
   double part = 0.0;
+  double nyl = 0.0;  // lane c holds the squared norm of sample column c before any projection
 #pragma unroll
   for (int c = 0; c < OW; c++) {
     y[c][0] = (c < p && v0) ? (double)Ys[i0 + (int64_t)c * m] : 0.0;
     y[c][1] = (c < p && v1) ? (double)Ys[i1 + (int64_t)c * m] : 0.0;
-    part += y[c][0] * y[c][0] + y[c][1] * y[c][1];
+    const double nc = warp_sum(y[c][0] * y[c][0] + y[c][1] * y[c][1]);
+    if (lane == c) nyl = nc;
+    part += nc;
   }
-  const double ny2 = warp_sum(part);
+  const double ny2 = part;
   double est2;
   if (round == 0) {
     est2 = ny2 / p;
@@ -745,6 +791,7 @@ __global__ void __launch_bounds__(NT) k_orth_warp(const TargetDev *tg, const int
     }
   // Gram-Schmidt twice among the new columns, with dropping
   const double drop2 = (0.1 * eps) * (0.1 * eps) * est2;
+  const double kappa = orth_recheck_ratio(eps), kappa2 = kappa * kappa;
   unsigned keep = 0u;
 #pragma unroll
   for (int j = 0; j < OW; j++) {
@@ -759,7 +806,27 @@ __global__ void __launch_bounds__(NT) k_orth_warp(const TargetDev *tg, const int
         y[j][1] -= d * y[l][1];
       }
     }
-    const double nrm2 = warp_sum(y[j][0] * y[j][0] + y[j][1] * y[j][1]);
+    double nrm2 = warp_sum(y[j][0] * y[j][0] + y[j][1] * y[j][1]);
+    const double nyj = __shfl_sync(0xffffffffu, nyl, j);
+    if (nrm2 > drop2 && nrm2 < kappa2 * nyj) {
+      // once more against the whole basis (see orth_recheck_ratio)
+      for (int q = 0; q < r; q++) {
+        const double *qc = Q + (int64_t)q * m;
+        const double q0 = v0 ? qc[i0] : 0.0, q1 = v1 ? qc[i1] : 0.0;
+        const double d = warp_sum(q0 * y[j][0] + q1 * y[j][1]);
+        y[j][0] -= d * q0;
+        y[j][1] -= d * q1;
+      }
+#pragma unroll
+      for (int l = 0; l < OW; l++) {
+        if (l >= j) break;
+        if (!((keep >> l) & 1u)) continue;
+        const double d = warp_sum(y[l][0] * y[j][0] + y[l][1] * y[j][1]);
+        y[j][0] -= d * y[l][0];
+        y[j][1] -= d * y[l][1];
+      }
+      nrm2 = warp_sum(y[j][0] * y[j][0] + y[j][1] * y[j][1]);
+    }
     if (nrm2 > drop2) {
       const double inv = 1.0 / sqrt(nrm2);
       y[j][0] *= inv;
@@ -850,9 +917,23 @@ __global__ void __launch_bounds__(NT) k_absorb_w(const TargetDev *tg, TargetStat
 
 constexpr int JMAX = 96;  // max basis size handled by the Jacobi core solver (even)
 
+// Whether the eps-rank needs a second Gram. The computed Gram of W carries rounding of order
+// r sqrt(n) u trace(W^T W) in its entries, so its small eigenvalues are known only to that
+// absolute level. When that level exceeds a tenth of the truncation threshold eps^2 trace
+// (which would move the tail sum, and so the error reached, by up to a few per cent), Q and W
+// are first rotated by the Gram's eigenvectors; the rotated W has columns
+// orthogonal up to that rounding, and the Gram of such a matrix carries rounding relative to
+// each pair of columns' own norms (Demmel and Veselic, "Jacobi's method is more accurate than
+// QR"), which resolves eigenvalues far below eps^2 trace.
+__device__ __forceinline__ bool core_needs_refinement(double eps, int r, int64_t n) {
+  return eps * eps < 10.0 * r * sqrt((double)n) * 0x1.0p-53;
+}
+
 // Eigen-decomposition of G = W^T W (r x r) by cyclic Jacobi with a round-robin ordering
 // (r/2 disjoint rotations per step, all applied at once), then the eps-rank: the smallest k
 // with sum_{i >= k} lambda_i <= eps^2 sum_i lambda_i; finally Q <- Q V_k and W <- W V_k in place.
+// With core_needs_refinement, the Gram and Jacobi run twice: the first pass's eigenvectors
+// rotate all r columns of Q and W in place, and the eps-rank and V_k come from the second.
 __global__ void __launch_bounds__(NT) k_final(const TargetDev *tg, TargetState *st, const int32_t *ids, double eps,
                                               double *qw) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -872,6 +953,26 @@ __global__ void __launch_bounds__(NT) k_final(const TargetDev *tg, TargetState *
     return;
   }
   const int rr = r + (r & 1);  // padded to even
+  const int npass = core_needs_refinement(eps, r, n) ? 2 : 1;
+  int sweeps_total = 0;
+  for (int pass = 0; pass < npass; pass++) {
+  if (pass == 1) {
+    // Q <- Q V and W <- W V with every column (V from the first pass); rows are independent
+    for (int mat = 0; mat < 2; mat++) {
+      double *M = mat == 0 ? Q : W;
+      const int64_t rows = mat == 0 ? m : n;
+      for (int64_t i = threadIdx.x; i < rows; i += NT) {
+        double row[JMAX];
+        for (int q = 0; q < r; q++) row[q] = M[i + (int64_t)q * rows];
+        for (int j = 0; j < r; j++) {
+          double sum = 0.0;
+          for (int q = 0; q < r; q++) sum += row[q] * V[q + j * JMAX];
+          M[i + (int64_t)j * rows] = sum;
+        }
+      }
+    }
+    __syncthreads();
+  }
   // G = W^T W
   {
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -899,6 +1000,7 @@ __global__ void __launch_bounds__(NT) k_final(const TargetDev *tg, TargetState *
   for (int i = 0; i < r; i++) trace += G[i + i * JMAX];
   const double skip = 1e-2 * eps * eps * trace / r;
   const int npair = rr / 2;
+  int pass_sweeps = 0;
   for (int sweep = 0; sweep < 40; sweep++) {
     if (threadIdx.x == 0) changed_s = 0;
     __syncthreads();
@@ -949,9 +1051,12 @@ __global__ void __launch_bounds__(NT) k_final(const TargetDev *tg, TargetState *
     }
     const int ch = changed_s;
     __syncthreads();
-    if (threadIdx.x == 0) st[b].sweeps = sweep + 1;
+    pass_sweeps = sweep + 1;
     if (!ch) break;
   }
+  sweeps_total += pass_sweeps;
+  }  // pass
+  if (threadIdx.x == 0) st[b].sweeps = sweeps_total;
   // order eigenvalues descending, eps-rank
   if (threadIdx.x == 0) {
     for (int i = 0; i < rr; i++) order[i] = i;
@@ -1057,6 +1162,23 @@ __global__ void __launch_bounds__(WF_WARPS * 32) k_final_warp(const TargetDev *t
     return;
   }
   const int rr = r + (r & 1);
+  const int npass = core_needs_refinement(eps, r, n) ? 2 : 1;
+  int sweeps_total = 0;
+  for (int pass = 0; pass < npass; pass++) {
+  if (pass == 1) {
+    // Q <- Q V and W <- W V with every column: V from the first pass, staged in G's storage
+    // with zero rows from r to WJ (rows of S.V beyond rr were never written)
+    for (int o = lane; o < WJ * r; o += 32) {
+      const int i = o % WJ, j = o / WJ;
+      S.G[i + j * WJ] = i < r ? S.V[i + j * WJ] : 0.0;
+    }
+    __syncwarp();
+    if (r <= 8) warp_rotate_rows<8>(Q, W, m, n, r, r, S.G);
+    else if (r <= 16) warp_rotate_rows<16>(Q, W, m, n, r, r, S.G);
+    else if (r <= 24) warp_rotate_rows<24>(Q, W, m, n, r, r, S.G);
+    else warp_rotate_rows<WJ>(Q, W, m, n, r, r, S.G);
+    __syncwarp();
+  }
   // G = W^T W (upper triangle by pairs, mirrored)
   for (int o = lane; o < rr * rr; o += 32) {
     const int i = o % rr, j = o / rr;
@@ -1076,6 +1198,7 @@ __global__ void __launch_bounds__(WF_WARPS * 32) k_final_warp(const TargetDev *t
   for (int i = 0; i < r; i++) trace += S.G[i + i * WJ];
   const double skip = 1e-2 * eps * eps * trace / r;
   const int npair = rr / 2;
+  int pass_sweeps = 0;
   for (int sweep = 0; sweep < 40; sweep++) {
     bool changed = false;
     for (int step = 0; step < rr - 1; step++) {
@@ -1121,9 +1244,12 @@ __global__ void __launch_bounds__(WF_WARPS * 32) k_final_warp(const TargetDev *t
       }
       __syncwarp();
     }
-    if (lane == 0) st[b].sweeps = sweep + 1;
+    pass_sweeps = sweep + 1;
     if (!__any_sync(0xffffffffu, changed)) break;
   }
+  sweeps_total += pass_sweeps;
+  }  // pass
+  if (lane == 0) st[b].sweeps = sweeps_total;
   int k = 0;
   if (lane == 0) {
     for (int i = 0; i < rr; i++) S.order[i] = i;

@@ -84,7 +84,7 @@ def check_sampled(oracle, T, Ao, Bo, C, eps, near_rtol, far, near, tol_factor=1.
     worst = 0.0
     for l in far:
         r0, m, c0, n = T.leaf_ranges(l)
-        blk = oracle.block_product(Ao, Bo, r0, m, c0, n)
+        blk = oracle.block_product_blas(Ao, Bo, r0, m, c0, n)
         U, V = C.leaf_get(l)
         nb = np.linalg.norm(blk)
         err = np.linalg.norm(blk - U @ V.T) / nb if nb > 0 else np.linalg.norm(U @ V.T)
@@ -94,7 +94,7 @@ def check_sampled(oracle, T, Ao, Bo, C, eps, near_rtol, far, near, tol_factor=1.
         worst = max(worst, err)
     for l in near:
         r0, m, c0, n = T.leaf_ranges(l)
-        blk = oracle.block_product(Ao, Bo, r0, m, c0, n)
+        blk = oracle.block_product_blas(Ao, Bo, r0, m, c0, n)
         D = C.leaf_get(l)
         e = np.linalg.norm(D - blk) / max(np.linalg.norm(blk), 1e-300)
         assert e <= near_rtol, (l, e)

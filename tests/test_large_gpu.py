@@ -46,3 +46,55 @@ def test_sphere_n32768_sampled(H, oracle, workload, mode, near_rtol):
     far, near = sampled_far_near(T, 48, 16, seed=7)
     worst = check_sampled(oracle, T, Ao, Bo, C, EPS, near_rtol, far, near)
     print(f"{mode}: {len(far)} far blocks, worst relative error {worst:.3g}; {len(near)} near blocks")
+
+
+@pytest.fixture(scope="module")
+def largest_blocks(workload, oracle):
+    """Sixteen of the far blocks of the top size class (1024 x 1024, level 5; 180 of them), chosen
+    with a seeded generator, and the oracle's exact blocks A|tau x I * B|I x sigma."""
+    T, Ao, Bo, _, _ = workload
+    sizes = np.array([T.leaf_ranges(l) for l in range(T.nleaf)])
+    far = np.nonzero(T.leaf_blocks[:, 2] == 1)[0]
+    top = far[sizes[far, 1] == sizes[far, 1].max()]
+    assert sizes[top[0], 1] >= 1024 and len(top) >= 16
+    pick = np.random.default_rng(5).choice(top, size=16, replace=False)
+    blocks = {}
+    for l in pick.tolist():
+        r0, m, c0, n = T.leaf_ranges(l)
+        blocks[l] = oracle.block_product_blas(Ao, Bo, r0, m, c0, n)
+    return blocks
+
+
+@pytest.mark.parametrize("mode", ["mixed", "f64"])
+def test_sphere_n32768_largest_blocks(H, oracle, workload, largest_blocks, mode):
+    """The largest far blocks, whose sum-expressions carry the most terms (Lemma 5.3), against the
+    oracle at 1.5 eps and rank <= eps-rank + 2, in the launch configuration the benchmark times.
+    Mixed form: the 1024-row targets' applications are split over several thread blocks each
+    (the per-class counts of the product say so). FP64 path: their panels do not fit in shared
+    memory and are staged in global memory."""
+    T, Ao, Bo, A, B = workload
+    md = H.MODE_MIXED if mode == "mixed" else H.MODE_F64
+    C = H.hmat_multiply(A, B, EPS, mode=md, block_width=8, seed=0)
+    assert C.last_status == H.HMAT_OK
+    st = C.stats()
+    if mode == "mixed":
+        assert st["apply_split_targets"] >= len(largest_blocks) and st["apply_max_split"] >= 4, st
+    else:
+        assert st["apply_gstage_targets"] >= 180, st
+    # the unique bytes of the passes are at most their per-use bytes, and include the panels
+    assert 0 < st["bytes_apply_unique"] <= st["bytes_apply_use"]
+    worst = 0.0
+    for l, blk in largest_blocks.items():
+        U, V = C.leaf_get(l)
+        nb = np.linalg.norm(blk)
+        err = np.linalg.norm(blk - U @ V.T) / nb
+        tr = oracle.truth_for_block(blk, EPS, l)
+        assert err <= 1.5 * EPS, (l, err, U.shape[1], tr.k_eps)
+        assert U.shape[1] <= tr.k_eps + 2, (l, U.shape[1], tr.k_eps)
+        # Eckart-Young: no rank-k approximation beats the singular-value tail at k
+        assert err * nb >= np.sqrt(np.sum(tr.s[U.shape[1]:] ** 2)) * (1 - 1e-3) - 1e-13 * nb
+        worst = max(worst, err)
+    print(f"{mode}: {len(largest_blocks)} blocks of {U.shape[0]} rows, worst relative error {worst / EPS:.3f} eps; "
+          f"split targets {st['apply_split_targets']} (max {st['apply_max_split']}), "
+          f"global-staging targets {st['apply_gstage_targets']}, "
+          f"unique/use bytes {st['bytes_apply_unique'] / st['bytes_apply_use']:.3f}")

@@ -7,11 +7,25 @@ import numpy as np
 import pytest
 
 from paper_1805_08998_gb300 import inputs
-from parity_util import sampled_far_near
 
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
 N, LEAF, ACA = 524288, 64, 1e-8
+# 256 far blocks stratified by level (the block sizes are 512, 256, 128 and 64 rows: exact
+# oracle blocks cost 2 m n N flops each, so the larger levels get fewer) and 16 near blocks
+PER_LEVEL = {10: 4, 11: 12, 12: 120, 13: 120}
+N_NEAR = 16
+
+
+def sample_levels(T, per_level, n_near, seed):
+    rng = np.random.default_rng(seed)
+    lv, kind = T.leaf_blocks[:, 3], T.leaf_blocks[:, 2]
+    far = []
+    for level, k in sorted(per_level.items()):
+        cand = np.nonzero((lv == level) & (kind == 1))[0]
+        far += rng.choice(cand, size=min(k, len(cand)), replace=False).tolist()
+    near = rng.choice(np.nonzero(kind != 1)[0], size=n_near, replace=False).tolist()
+    return far, near
 
 
 @pytest.fixture(scope="module")
@@ -30,11 +44,11 @@ def sweep(H, oracle):
     Ao = oracle.HMatrix(T, oracle.KERNEL_EXP, ACA, prec32=True)
     A = H.hmat_build(P, H.K_EXP, leaf_size=LEAF, eta=1.0, aca_eps=ACA, factor_prec=32)
     assert np.array_equal(A.permutation(), T.perm)
-    far, near = sampled_far_near(T, 12, 4, seed=11, max_mn=128 * 128)
+    far, near = sample_levels(T, PER_LEVEL, N_NEAR, seed=11)
     blocks = {}
     for l in far + near:
         r0, m, c0, n = T.leaf_ranges(l)
-        blocks[l] = oracle.block_product(Ao, Ao, r0, m, c0, n, chunk=8192)
+        blocks[l] = oracle.block_product_blas(Ao, Ao, r0, m, c0, n)
     return T, A, far, near, blocks
 
 
@@ -42,6 +56,7 @@ def sweep(H, oracle):
                                                  (1e-8, "f64", 1e-10)])
 def test_sweep_n524288(H, oracle, sweep, eps, mode, near_rtol):
     T, A, far, near, blocks = sweep
+    assert len(far) == sum(PER_LEVEL.values()) == 256
     C = H.hmat_multiply(A, A, eps, mode=H.MODE_MIXED if mode == "mixed" else H.MODE_F64, seed=1)
     assert C.last_status == H.HMAT_OK
     assert C.stats()["groups"] > 1

@@ -212,7 +212,8 @@ std::vector<double> block_storage(const Tree &t, const std::vector<LeafDev> &lv)
 double apply_unique_elems(const Tree &t, const Plan &plan, const std::vector<LeafDev> &lA,
                           const std::vector<LeafDev> &lB, const std::vector<double> &storA,
                           const std::vector<double> &storB, const std::vector<TargetDev> &tg,
-                          const std::vector<PairDev> &pairs, const std::vector<int32_t> &rounds_of, int pcols) {
+                          const std::vector<PairDev> &pairs, const std::vector<int32_t> &rounds_of, int pcols,
+                          double *parts = nullptr) {
   const size_t nf = tg.size(), ncl = t.cl.size(), nblk = t.bl.size();
   if (nf == 0) return 0.0;
   const int D = t.depth;
@@ -280,11 +281,11 @@ double apply_unique_elems(const Tree &t, const Plan &plan, const std::vector<Lea
   std::vector<int32_t> markA(lA.size(), -1), markB(lB.size(), -1), stampA(nblk, -1), stampB(nblk, -1);
   int rmax = 0;
   for (size_t i = 0; i < nf; i++) rmax = std::max(rmax, std::max(1, rounds_of[i]));
-  double total = 0.0;
+  double total = 0.0, tot_panels = 0.0, tot_pairs = 0.0;
   for (int j = 0; j < rmax; j++) {
     std::fill(rows.begin(), rows.end(), 0ull);
     std::fill(cols.begin(), cols.end(), 0ull);
-    double u = 0.0;
+    double u = 0.0, u_panels = 0.0, u_pairs = 0.0;
     listA.clear();
     listB.clear();
     for (size_t i = 0; i < nf; i++) {
@@ -293,7 +294,7 @@ double apply_unique_elems(const Tree &t, const Plan &plan, const std::vector<Lea
       const int lev = t.bl[d.blk].level;
       fill(&rows[bo[d.blk]], lev);
       fill(&cols[bo[d.blk]], lev);
-      u += (double)(d.m + d.n) * pcols;
+      u_panels += (double)(d.m + d.n) * pcols;
       for (int32_t q = d.pair_lo; q < d.pair_hi; q++) {
         const PairDev &pr = pairs[q];
         if (stampA[pr.blkA] != j) { stampA[pr.blkA] = j; listA.push_back(pr.blkA); }
@@ -319,18 +320,20 @@ double apply_unique_elems(const Tree &t, const Plan &plan, const std::vector<Lea
       for (size_t w = 0; w < nwords(bk.level) && !any; w++) any = rw[w] != 0;
       if (!any) continue;
       const size_t nw = nwords(bk.level);
+      const double prow = (double)points(rw, bk.level, lc0[bk.tau]);
+      const double pcol = (double)points(cw, bk.level, lc0[bk.sigma]);
       for (int32_t q = plan.blk_term_lo[b]; q < plan.blk_term_hi[b]; q++) {
         const PlanTerm &pt = plan.terms[q];
         if (pt.type == JOB_FF_R || pt.type == JOB_FH) {  // L = U of A's leaf a (rows tau), R new
           uint64_t *o = &objA[oa[pt.a]];
           if (markA[pt.a] != j) { markA[pt.a] = j; std::fill(o, o + nw, 0ull); touchA.push_back(pt.a); }
           for (size_t w = 0; w < nw; w++) o[w] |= rw[w];
-          u += (double)pt.rank * points(cw, bk.level, lc0[bk.sigma]);
+          u += (double)pt.rank * pcol;
         } else {  // L new, R = V of B's leaf b (rows sigma)
           uint64_t *o = &objB[ob[pt.b]];
           if (markB[pt.b] != j) { markB[pt.b] = j; std::fill(o, o + nw, 0ull); touchB.push_back(pt.b); }
           for (size_t w = 0; w < nw; w++) o[w] |= cw[w];
-          u += (double)pt.rank * points(rw, bk.level, lc0[bk.tau]);
+          u += (double)pt.rank * prow;
         }
       }
     }
@@ -350,10 +353,17 @@ double apply_unique_elems(const Tree &t, const Plan &plan, const std::vector<Lea
       for (int32_t b : lst) {
         bool inside = false;
         for (int p = t.bl[b].parent; p >= 0 && !inside; p = t.bl[p].parent) inside = stp[p] == j;
-        if (!inside) u += stor[b];
+        if (!inside) u_pairs += stor[b];
       }
     }
-    total += 2.0 * u;
+    total += 2.0 * (u + u_panels + u_pairs);
+    tot_panels += 2.0 * u_panels;
+    tot_pairs += 2.0 * u_pairs;
+  }
+  if (parts) {  // (low-rank terms, H-pair blocks, panels)
+    parts[0] = total - tot_pairs - tot_panels;
+    parts[1] = tot_pairs;
+    parts[2] = tot_panels;
   }
   return total;
 }
@@ -1875,13 +1885,11 @@ void Product::run() {
   // with a long serial chain of H-pairs: their H-pairs and terms are split over K blocks per
   // target (about two H-pairs of inner blocks per block, at most 8), which add their partial
   // outputs into a zeroed output.
-  const char *split_env = std::getenv("HMAT_APPLY_SPLIT");
   for (int c = 1; c < NCLS; c++) {
     ClassLaunch &cl = cls[c];
     if (cl.count == 0 || apply_rows_per_lane(cl.dmax) > 0) continue;
     const double ppt = (double)cl.inner_pairs / cl.count;
     cl.split = std::max(1, std::min(8, (int)std::ceil(ppt / 2.0)));
-    if (split_env) cl.split = std::max(1, std::min(16, std::atoi(split_env)));
   }
   for (int c = 0; c < NCLS; c++) {
     if (cls[c].count == 0) continue;
@@ -2204,6 +2212,23 @@ void Product::run() {
     S.sample_passes += st[i].nfwd;
     rounds_of[i] = st[i].nfwd;
   }
+  // The unique bytes of the passes (a statistic), counted on a host thread while the device
+  // truncates and writes C; joined before the group's statistics are summed (or on unwinding).
+  double uniq_elems = 0.0;
+  struct Joiner {
+    std::thread th;
+    ~Joiner() {
+      if (th.joinable()) th.join();
+    }
+  } uniq_thread;
+  uniq_thread.th = std::thread([&]() {
+    try {
+      uniq_elems = apply_unique_elems(t, plan, A->leaves, B->leaves, storA, storB, ftg, fpairs, rounds_of,
+                                      single ? 1 : p);
+    } catch (...) {
+      uniq_elems = 0.0;
+    }
+  });
   {
     std::vector<int32_t> ids_small, ids_big;
     for (int i = 0; i < nf; i++) (st[i].r <= 32 ? ids_small : ids_big).push_back(i);
@@ -2242,11 +2267,10 @@ void Product::run() {
       for (auto &e : fe) cudaEventDestroy(e);
     }
     launches += (ids_small.empty() ? 0 : 1) + (ids_big.empty() ? 0 : 1);
-    // the unique bytes of the passes, counted on the host while the device truncates
-    const double uniq = (double)es * apply_unique_elems(t, plan, A->leaves, B->leaves, storA, storB, ftg,
-                                                        fpairs, rounds_of, single ? 1 : p);
-    S.bytes_apply_unique += uniq;
     if (tr.on) {  // each size class on its own: what separate launches of the classes must read
+      double parts[3] = {0, 0, 0};
+      const double uniq = (double)es * apply_unique_elems(t, plan, A->leaves, B->leaves, storA, storB, ftg,
+                                                          fpairs, rounds_of, single ? 1 : p, parts);
       double sum = 0.0;
       for (int c = 0; c < NCLS; c++) {
         if (cls[c].count == 0) continue;
@@ -2258,8 +2282,9 @@ void Product::run() {
         sum += u;
         std::fprintf(stderr, "hmat trace: class %2d unique bytes over its passes %.4g GB\n", c, u * 1e-9);
       }
-      std::fprintf(stderr, "hmat trace: unique bytes over all passes %.4g GB (classes on their own: %.4g GB)\n",
-                   uniq * 1e-9, sum * 1e-9);
+      std::fprintf(stderr, "hmat trace: unique bytes over all passes %.4g GB (classes on their own: %.4g GB); "
+                   "terms %.4g GB, H-pair blocks %.4g GB, panels %.4g GB\n", uniq * 1e-9, sum * 1e-9,
+                   es * parts[0] * 1e-9, es * parts[1] * 1e-9, es * parts[2] * 1e-9);
     }
     if (nf) ck(cudaMemcpyAsync(st.data(), d_st.p, sizeof(TargetState) * nf, cudaMemcpyDeviceToHost, s), "states");
     ck(cudaStreamSynchronize(s), "final");
@@ -2328,6 +2353,8 @@ void Product::run() {
     for (int q = d.pair_lo; q < d.pair_hi; q++) rr += t.cl[t.bl[npairs[q].blkA].sigma].size;
     fn += 2.0 * d.m * d.n * (kk + rr);
   }
+  uniq_thread.th.join();
+  S.bytes_apply_unique += (double)es * uniq_elems;
   S.bytes_apply_use += bu;
   S.flops_apply += fa;
   S.bytes_apply += ba;

@@ -186,6 +186,10 @@ typedef struct {
   int64_t apply_split_targets;   /* far targets whose application was split over several thread
                                     blocks (partial outputs added atomically) */
   int apply_max_split;           /* the largest such split (thread blocks per target) */
+  double bytes_terms_use;        /* algorithmic bytes of the low-rank products (a2): every panel
+                                    reads its H-block's stored elements once plus its input and
+                                    output columns; every far x far product reads its four factors
+                                    and writes the new one */
 } hmat_stats_t;
 
 /* Synthetic inputs (the paper's experiments, Sec. 6.1, use Galerkin matrices on the unit sphere;
@@ -262,7 +266,10 @@ hmat_status hmat_matvec(const hmat_t H, const double *x, double *y, int64_t ncol
 /* Estimate of the relative Frobenius error ||C - A B||_F / ||A B||_F of a product (the paper's
  * check of its products, Sec. 6: `iters` subspace iterations on a block of `size` Gaussian
  * vectors (splitmix64 stream of `seed`), the operator applied as C v - A (B v)). The same
- * iteration on C estimates the denominator. A, B, C on one block tree. Synchronises. */
+ * iteration on C estimates the denominator. Every step runs on the device (the H-matrix
+ * products, C v - A (B v), Cholesky QR twice of the block, the norms); only the two norms are
+ * read back. size must be 1..128 (the paper uses 100). A, B, C on one block tree.
+ * Synchronises. */
 hmat_status hmat_product_error(const hmat_t A, const hmat_t B, const hmat_t C, int iters, int size, uint64_t seed,
                                double *rel_err);
 

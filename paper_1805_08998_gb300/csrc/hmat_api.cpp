@@ -798,54 +798,6 @@ void from_panel(const Tree &t, const std::vector<double> &pan, int64_t ncols, in
     for (int64_t i = 0; i < t.n; i++) y[t.perm[i] + (c0 + c) * t.n] = pan[i * SP + c];
 }
 
-// Orthonormal columns of the n x s column-major X (tree order) by Cholesky QR applied twice; a
-// zero block stays zero. Returns false when X is zero.
-bool orthonormalise(std::vector<double> &X, int64_t n, int s) {
-  for (int pass = 0; pass < 2; pass++) {
-    std::vector<double> G((size_t)s * s, 0.0);
-    std::mutex mu;
-    parallel_for(64, [&](size_t ch) {
-      std::vector<double> g((size_t)s * s, 0.0);
-      for (int64_t i = n * (int64_t)ch / 64; i < n * (int64_t)(ch + 1) / 64; i++)
-        for (int a = 0; a < s; a++) {
-          const double xa = X[i + (int64_t)a * n];
-          if (xa == 0.0) continue;
-          for (int b = a; b < s; b++) g[a + (size_t)b * s] += xa * X[i + (int64_t)b * n];
-        }
-      std::lock_guard<std::mutex> lk(mu);
-      for (size_t k = 0; k < g.size(); k++) G[k] += g[k];
-    });
-    double tr = 0.0;
-    for (int a = 0; a < s; a++) tr += G[a + (size_t)a * s];
-    if (!(tr > 0.0)) return false;
-    for (int a = 0; a < s; a++) G[a + (size_t)a * s] += 1e-15 * tr;  // keeps a rank-deficient block finite
-    // G = R^T R (upper R stored in G's upper triangle)
-    for (int j = 0; j < s; j++) {
-      for (int k = 0; k < j; k++) {
-        double v = G[k + (size_t)j * s];
-        for (int l = 0; l < k; l++) v -= G[l + (size_t)k * s] * G[l + (size_t)j * s];
-        G[k + (size_t)j * s] = v / G[k + (size_t)k * s];
-      }
-      double d = G[j + (size_t)j * s];
-      for (int l = 0; l < j; l++) d -= G[l + (size_t)j * s] * G[l + (size_t)j * s];
-      G[j + (size_t)j * s] = std::sqrt(std::max(d, 1e-300));
-    }
-    // X <- X R^{-1}, row by row
-    parallel_for(64, [&](size_t ch) {
-      std::vector<double> row(s);
-      for (int64_t i = n * (int64_t)ch / 64; i < n * (int64_t)(ch + 1) / 64; i++) {
-        for (int j = 0; j < s; j++) {
-          double v = X[i + (int64_t)j * n];
-          for (int k = 0; k < j; k++) v -= row[k] * G[k + (size_t)j * s];
-          row[j] = v / G[j + (size_t)j * s];
-        }
-        for (int j = 0; j < s; j++) X[i + (int64_t)j * n] = row[j];
-      }
-    });
-  }
-  return true;
-}
-
 }  // namespace
 
 extern "C" {
@@ -875,6 +827,7 @@ hmat_status hmat_product_error(const hmat_t A, const hmat_t B, const hmat_t C, i
                                double *rel_err) {
   return guard([&] {
     if (!A || !B || !C || !rel_err || iters < 0 || size < 1) fail(HMAT_EINVAL, "NULL argument or bad iters/size");
+    if (size > 128) fail(HMAT_EINVAL, "size must be at most 128");
     if (A->tree != C->tree && !same_points(*A->tree, C->tree->orig.data(), C->tree->n, C->tree->dim))
       fail(HMAT_EMISMATCH, "A and C are not on one block tree");
     if (A->tree != B->tree && !same_points(*A->tree, B->tree->orig.data(), B->tree->n, B->tree->dim))
@@ -883,57 +836,44 @@ hmat_status hmat_product_error(const hmat_t A, const hmat_t B, const hmat_t C, i
     const int64_t n = t.n;
     cudaStream_t s = C->stream;
     DevMatvec ma(A, s), mb(B, s), mc(C, s);
+    // the n x size blocks as row-major panels of panel_width() columns, all on the device
     const int P = panel_width(), SP = panel_row_stride(P);
-    const size_t pan_elems = (size_t)n * SP;
-    DevBuf dx(sizeof(double) * pan_elems, s), d1(sizeof(double) * pan_elems, s), d2(sizeof(double) * pan_elems, s);
-    std::vector<double> pan(pan_elems), out1(pan_elems), out2(pan_elems);
-    // Y = E X with E = C - A B (which = 0), or Y = C X (which = 1); X, Y n x size, tree order
-    auto apply = [&](int which, const std::vector<double> &X, std::vector<double> &Y) {
-      Y.assign((size_t)n * size, 0.0);
-      for (int c0 = 0; c0 < size; c0 += P) {
-        std::fill(pan.begin(), pan.end(), 0.0);
-        for (int c = 0; c < P && c0 + c < size; c++)
-          for (int64_t i = 0; i < n; i++) pan[i * SP + c] = X[i + (int64_t)(c0 + c) * n];
-        ck(cudaMemcpyAsync(dx.p, pan.data(), sizeof(double) * pan_elems, cudaMemcpyHostToDevice, s), "upload");
-        mc.apply(dx.as<double>(), d1.as<double>(), s);
+    const int npan = (size + P - 1) / P;
+    const int64_t pan = n * SP, blk = (int64_t)npan * pan;
+    DevBuf dX(sizeof(double) * blk, s), dY(sizeof(double) * blk, s);
+    DevBuf d2(sizeof(double) * pan, s), d3(sizeof(double) * pan, s);
+    DevBuf dG(sizeof(double) * size * size, s), dzero(sizeof(int) * 2, s), dsum(sizeof(double) * 2, s);
+    ck(cudaMemsetAsync(dzero.p, 0, sizeof(int) * 2, s), "memset");
+    ck(cudaMemsetAsync(dsum.p, 0, sizeof(double) * 2, s), "memset");
+    double *X = dX.as<double>(), *Y = dY.as<double>();
+    // Y = E X with E = C - A B (which = 0), or Y = C X (which = 1), panel by panel
+    auto apply = [&](int which, const double *Xb, double *Yb) {
+      for (int q = 0; q < npan; q++) {
+        mc.apply(Xb + q * pan, Yb + q * pan, s);
         if (which == 0) {
-          mb.apply(dx.as<double>(), d2.as<double>(), s);
-          ma.apply(d2.as<double>(), dx.as<double>(), s);
-          ck(cudaMemcpyAsync(out2.data(), dx.p, sizeof(double) * pan_elems, cudaMemcpyDeviceToHost, s), "download");
+          mb.apply(Xb + q * pan, d2.as<double>(), s);
+          ma.apply(d2.as<double>(), d3.as<double>(), s);
+          ck(launch_est_sub(Yb + q * pan, d3.as<double>(), pan, s), "difference");
         }
-        ck(cudaMemcpyAsync(out1.data(), d1.p, sizeof(double) * pan_elems, cudaMemcpyDeviceToHost, s), "download");
-        ck(cudaStreamSynchronize(s), "matvec");
-        for (int c = 0; c < P && c0 + c < size; c++)
-          for (int64_t i = 0; i < n; i++)
-            Y[i + (int64_t)(c0 + c) * n] = out1[i * SP + c] - (which == 0 ? out2[i * SP + c] : 0.0);
       }
     };
-    // block power iteration on a Gaussian start (splitmix64 + Box-Muller), then the Frobenius
-    // norm of the operator on the final orthonormal block
-    auto estimate = [&](int which) {
-      std::vector<double> X((size_t)n * size), Y;
-      for (size_t k = 0; k < X.size(); k++) {
-        auto mix = [](uint64_t z) {
-          z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-          z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-          return z ^ (z >> 31);
-        };
-        const double u1 = ((mix(seed + (2 * k + 1) * 0x9E3779B97F4A7C15ull) >> 11) + 1) * 0x1.0p-53;
-        const double u2 = (mix(seed + (2 * k + 2) * 0x9E3779B97F4A7C15ull) >> 11) * 0x1.0p-53;
-        X[k] = std::sqrt(-2.0 * std::log(u1)) * std::cos(6.283185307179586 * u2);
-      }
-      if (!orthonormalise(X, n, size)) return 0.0;
+    // block power iteration on a Gaussian start, orthonormalised by Cholesky QR twice at every
+    // step, then the squared Frobenius norm of the operator on the final block
+    for (int which = 0; which < 2; which++) {
+      ck(launch_est_gaussian(X, n, size, seed, s), "start block");
+      ck(launch_est_orth(X, n, size, dG.as<double>(), dzero.as<int>() + which, s), "orthonormalise");
       for (int it = 0; it < iters; it++) {
         apply(which, X, Y);
-        if (!orthonormalise(Y, n, size)) return 0.0;
-        X.swap(Y);
+        ck(launch_est_orth(Y, n, size, dG.as<double>(), dzero.as<int>() + which, s), "orthonormalise");
+        std::swap(X, Y);
       }
       apply(which, X, Y);
-      double f = 0.0;
-      for (double v : Y) f += v * v;
-      return std::sqrt(f);
-    };
-    const double e = estimate(0), c = estimate(1);
+      ck(launch_est_norm2(Y, blk, dsum.as<double>() + which, s), "norm");
+    }
+    double sums[2] = {0.0, 0.0};
+    ck(cudaMemcpyAsync(sums, dsum.p, sizeof(sums), cudaMemcpyDeviceToHost, s), "norms");
+    ck(cudaStreamSynchronize(s), "error estimate");
+    const double e = std::sqrt(sums[0]), c = std::sqrt(sums[1]);
     *rel_err = c > 0.0 ? e / c : e;
   });
 }
@@ -1463,14 +1403,14 @@ void Product::run() {
   for (int k = 0; k < NB + 2; k++) pk[k].clear();
   int pdim[NB + 2] = {0};
   int64_t term_elems = 0;
-  double flops_terms = 0;
+  double flops_terms = 0, elems_terms_use = 0;
   double kind_flops[NB + 2] = {0}, kind_cols[NB + 2] = {0};
   {
     // two passes over chunks of the terms on a thread pool, with the serial order preserved:
     // (1) per chunk: storage, flops, far x far count, panels per kind; (2) fill at the offsets
     struct Chunk {
       int64_t elems = 0, nff = 0;
-      double flops = 0;
+      double flops = 0, elems_use = 0;
       int64_t npk[NB + 2] = {0};
       int pd[NB + 2] = {0};
       double fk[NB + 2] = {0}, ck[NB + 2] = {0};  // per kind: flops, columns (for the trace)
@@ -1505,10 +1445,17 @@ void Product::run() {
         if (pt.type == JOB_FF_R || pt.type == JOB_FF_L) {
           const LeafDev &la = A->leaves[pt.a], &lb = B->leaves[pt.b];
           k.flops += 2.0 * la.n * la.rank * lb.rank + 2.0 * rows * la.rank * lb.rank;
+          // V_a and U_b (rho' rows), the far factor that is kept (rows of the new one), the new factor
+          k.elems_use += (double)la.n * la.rank + (double)lb.m * lb.rank +
+                         (double)rows * (pt.type == JOB_FF_R ? lb.rank : la.rank) + (double)rows * pt.rank;
           k.nff++;
         } else {
           const int hb = pt.type == JOB_HF ? pt.a : pt.b;
           k.flops += 2.0 * (pt.type == JOB_HF ? storA[hb] : storB[hb]) * pt.rank;
+          // every panel reads the H-block once, plus its input columns and its output columns
+          const int64_t inrows = pt.type == JOB_HF ? t.cl[t.bl[hb].sigma].size : t.cl[t.bl[hb].tau].size;
+          k.elems_use += (double)((pt.rank + PW - 1) / PW) * (pt.type == JOB_HF ? storA[hb] : storB[hb]) +
+                         (double)(inrows + rows) * pt.rank;
           int dmx;
           const int kind = kind_of(pt, dmx);
           k.npk[kind] += (pt.rank + PW - 1) / PW;
@@ -1525,6 +1472,7 @@ void Product::run() {
       eoff[c + 1] = eoff[c] + ch[c].elems;
       foff[c + 1] = foff[c] + ch[c].nff;
       flops_terms += ch[c].flops;
+      elems_terms_use += ch[c].elems_use;
       for (int k = 0; k < NB + 2; k++) {
         poff[c + 1][k] = poff[c][k] + ch[c].npk[k];
         pdim[k] = std::max(pdim[k], ch[c].pd[k]);
@@ -1567,6 +1515,7 @@ void Product::run() {
   }
   tr.mark("jobs and panels");
   S.flops_terms += flops_terms;
+  S.bytes_terms_use += (double)es * elems_terms_use;
   std::vector<int2> blk_terms(t.bl.size());
   for (size_t b = 0; b < t.bl.size(); b++) blk_terms[b] = make_int2(plan.blk_term_lo[b], plan.blk_term_hi[b]);
 

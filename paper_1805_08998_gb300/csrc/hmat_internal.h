@@ -253,6 +253,13 @@ cudaError_t launch_final(const TargetDev *tg, TargetState *st, const int32_t *id
 cudaError_t launch_write_far(int prec, const TargetDev *tg, const TargetState *st, int ntg,
                              const double *qw, const LeafDev *leafC, void *dataC, cudaStream_t s);
 cudaError_t launch_convert(int prec, const void *src, double *dst, int64_t count, cudaStream_t s);
+// the global error estimator's device steps, on blocks of size <= 128 columns held as row-major
+// panels of 16 columns (row stride 17) in tree order: the Gaussian start, Y -= Z, Cholesky QR
+// twice (G: size x size scratch; *zero set when the block is zero) and the sum of squares into *out
+cudaError_t launch_est_gaussian(double *X, int64_t n, int size, uint64_t seed, cudaStream_t s);
+cudaError_t launch_est_sub(double *Y, const double *Z, int64_t count, cudaStream_t s);
+cudaError_t launch_est_orth(double *X, int64_t n, int size, double *G, int *zero, cudaStream_t s);
+cudaError_t launch_est_norm2(const double *Y, int64_t count, double *out, cudaStream_t s);
 // atomicMin of the index of every non-finite entry into *first (initialise to ~0ull)
 cudaError_t launch_find_nonfinite(int prec, const void *x, int64_t count, unsigned long long *first, cudaStream_t s);
 

@@ -2140,6 +2140,175 @@ cudaError_t launch_write_far(int prec, const TargetDev *tg, const TargetState *s
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------------------
+// The global error estimator (Sec. 6): a block of `size` columns as ceil(size / 16) row-major
+// panels of 16 columns (row stride 17, the layout of the H-matrix times panel kernel), n rows in
+// tree order; column c is slot c % 16 of panel c / 16.
+// ---------------------------------------------------------------------------------------
+constexpr int EP = 16, ESP = 17;
+__device__ __forceinline__ int64_t est_at(int64_t n, int64_t i, int c) {
+  return (int64_t)(c / EP) * n * ESP + i * ESP + (c % EP);
+}
+
+__device__ __forceinline__ uint64_t est_mix(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// Gaussian start block: entry (i, c), k = i + c n, from two splitmix64 draws of the counters
+// 2k + 1 and 2k + 2 (uniforms in (0, 1] and [0, 1)) by Box-Muller; padding slots zero
+__global__ void k_est_gaussian(double *X, int64_t n, int size, uint64_t seed) {
+  const int npan = (size + EP - 1) / EP;
+  const int64_t total = (int64_t)npan * n * ESP;
+  for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < total; o += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = o / (n * ESP), r = o % (n * ESP);
+    const int64_t i = r / ESP;
+    const int c = (int)(p * EP + r % ESP);
+    double v = 0.0;
+    if (r % ESP < EP && c < size) {
+      const uint64_t k = (uint64_t)i + (uint64_t)c * (uint64_t)n;
+      const double u1 = (double)((est_mix(seed + (2 * k + 1) * 0x9E3779B97F4A7C15ull) >> 11) + 1) * 0x1.0p-53;
+      const double u2 = (double)(est_mix(seed + (2 * k + 2) * 0x9E3779B97F4A7C15ull) >> 11) * 0x1.0p-53;
+      v = sqrt(-2.0 * log(u1)) * cos(6.283185307179586 * u2);
+    }
+    X[o] = v;
+  }
+}
+
+// Y -= Z over count entries
+__global__ void k_est_sub(double *Y, const double *Z, int64_t count) {
+  for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < count; o += (int64_t)gridDim.x * blockDim.x)
+    Y[o] -= Z[o];
+}
+
+// G (size x size, upper triangle, zeroed beforehand) += X^T X over the rows of this block's chunk
+constexpr int EST_ROWS = 16;
+__global__ void __launch_bounds__(NT) k_est_gram(const double *X, int64_t n, int size, double *G) {
+  __shared__ double xs[EST_ROWS][128];
+  const int npairs = size * (size + 1) / 2;
+  constexpr int PER = 128 * 129 / 2 / NT + 1;  // pairs per thread for size <= 128
+  double acc[PER];
+  int16_t pa[PER], pb[PER];  // this thread's pairs (a <= b), row-major over the upper triangle
+#pragma unroll
+  for (int j = 0; j < PER; j++) {
+    acc[j] = 0.0;
+    const int e = threadIdx.x + j * NT;
+    int a = 0, rem = e;
+    if (e < npairs)
+      while (rem >= size - a) { rem -= size - a; a++; }
+    pa[j] = (int16_t)(e < npairs ? a : -1);
+    pb[j] = (int16_t)(e < npairs ? a + rem : -1);
+  }
+  const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t i0 = blockIdx.x * chunk, i1 = min(n, i0 + chunk);
+  for (int64_t ib = i0; ib < i1; ib += EST_ROWS) {
+    const int nr = (int)(i1 - ib < EST_ROWS ? i1 - ib : EST_ROWS);
+    __syncthreads();
+    for (int o = threadIdx.x; o < EST_ROWS * size; o += NT) {
+      const int r = o / size, c = o % size;
+      xs[r][c] = r < nr ? X[est_at(n, ib + r, c)] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < PER; j++) {
+      if (pa[j] >= 0) {
+        const int a = pa[j], b = pb[j];
+        double sum = 0.0;
+#pragma unroll
+        for (int r = 0; r < EST_ROWS; r++) sum += xs[r][a] * xs[r][b];
+        acc[j] += sum;
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < PER; j++)
+    if (pa[j] >= 0) atomicAdd(&G[pa[j] + (int64_t)pb[j] * size], acc[j]);
+}
+
+// Cholesky G + 1e-15 trace I = R^T R in place (upper R), one block; a zero Gram sets *zero = 1 and
+// leaves R = I (the block is then zero and stays zero)
+__global__ void __launch_bounds__(NT) k_est_chol(double *G, int size, int *zero) {
+  __shared__ double tr_s;
+  if (threadIdx.x == 0) {
+    double tr = 0.0;
+    for (int a = 0; a < size; a++) tr += G[a + (int64_t)a * size];
+    tr_s = tr;
+  }
+  __syncthreads();
+  const double tr = tr_s;
+  if (!(tr > 0.0)) {
+    for (int o = threadIdx.x; o < size * size; o += NT) G[o] = (o % size == o / size) ? 1.0 : 0.0;
+    if (threadIdx.x == 0) *zero = 1;
+    return;
+  }
+  for (int a = threadIdx.x; a < size; a += NT) G[a + (int64_t)a * size] += 1e-15 * tr;
+  __syncthreads();
+  for (int k = 0; k < size; k++) {
+    if (threadIdx.x == 0) G[k + (int64_t)k * size] = sqrt(fmax(G[k + (int64_t)k * size], 1e-300));
+    __syncthreads();
+    const double rkk = G[k + (int64_t)k * size];
+    for (int j = k + 1 + threadIdx.x; j < size; j += NT) G[k + (int64_t)j * size] /= rkk;
+    __syncthreads();
+    const int m = size - k - 1;
+    for (int o = threadIdx.x; o < m * m; o += NT) {
+      const int i = k + 1 + o % m, j = k + 1 + o / m;
+      if (i <= j) G[i + (int64_t)j * size] -= G[k + (int64_t)i * size] * G[k + (int64_t)j * size];
+    }
+    __syncthreads();
+  }
+}
+
+// X <- X R^{-1} row by row (R upper, size x size), one thread per row
+__global__ void __launch_bounds__(NT) k_est_trsm(double *X, int64_t n, int size, const double *R) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double row[128];
+  for (int j = 0; j < size; j++) {
+    double v = X[est_at(n, i, j)];
+    for (int k = 0; k < j; k++) v -= row[k] * R[k + (int64_t)j * size];
+    row[j] = v / R[j + (int64_t)j * size];
+  }
+  for (int j = 0; j < size; j++) X[est_at(n, i, j)] = row[j];
+}
+
+// *out += sum of squares of the block's entries
+__global__ void __launch_bounds__(NT) k_est_norm2(const double *Y, int64_t count, double *out) {
+  __shared__ double red[NT / 32];
+  double v = 0.0;
+  for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < count; o += (int64_t)gridDim.x * blockDim.x)
+    v += Y[o] * Y[o];
+  v = block_sum(v, red);
+  if (threadIdx.x == 0) atomicAdd(out, v);
+}
+
+cudaError_t launch_est_gaussian(double *X, int64_t n, int size, uint64_t seed, cudaStream_t s) {
+  k_est_gaussian<<<152 * 8, NT, 0, s>>>(X, n, size, seed);
+  return cudaGetLastError();
+}
+cudaError_t launch_est_sub(double *Y, const double *Z, int64_t count, cudaStream_t s) {
+  k_est_sub<<<152 * 8, NT, 0, s>>>(Y, Z, count);
+  return cudaGetLastError();
+}
+// X <- X R^{-1} with X^T X = R^T R, twice (Cholesky QR twice); G is size x size scratch
+cudaError_t launch_est_orth(double *X, int64_t n, int size, double *G, int *zero, cudaStream_t s) {
+  if (size > 128) return cudaErrorInvalidValue;
+  for (int pass = 0; pass < 2; pass++) {
+    cudaError_t e = cudaMemsetAsync(G, 0, sizeof(double) * size * size, s);
+    if (e != cudaSuccess) return e;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(152 * 4, (n + 255) / 256));
+    k_est_gram<<<grid, NT, 0, s>>>(X, n, size, G);
+    k_est_chol<<<1, NT, 0, s>>>(G, size, zero);
+    k_est_trsm<<<(unsigned)((n + NT - 1) / NT), NT, 0, s>>>(X, n, size, G);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+cudaError_t launch_est_norm2(const double *Y, int64_t count, double *out, cudaStream_t s) {
+  k_est_norm2<<<152 * 4, NT, 0, s>>>(Y, count, out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_convert(int prec, const void *src, double *dst, int64_t count, cudaStream_t s) {
   if (count == 0) return cudaSuccess;
   const int blocks = (int)std::min<int64_t>((count + NT - 1) / NT, 152 * 16);

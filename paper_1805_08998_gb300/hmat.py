@@ -83,7 +83,8 @@ class Stats(ctypes.Structure):
                 ("first_round_cols", ctypes.c_int64), ("done_in_first_round", ctypes.c_int64),
                 ("sample_passes", ctypes.c_int64), ("groups", ctypes.c_int64),
                 ("bytes_apply_unique", ctypes.c_double), ("apply_gstage_targets", ctypes.c_int64),
-                ("apply_split_targets", ctypes.c_int64), ("apply_max_split", ctypes.c_int)]
+                ("apply_split_targets", ctypes.c_int64), ("apply_max_split", ctypes.c_int),
+                ("bytes_terms_use", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

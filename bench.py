@@ -415,6 +415,11 @@ def run_ours(args):
     achieved_use = (apply_bytes / max(apply_launches, 1)) / (per_launch_ms * 1e-3) / 1e9
     peak, peak_kind = _peaks()
     traffic = _traffic_from_profile()
+    # the low-rank products (a2, panels and far x far products): per-use bytes over the phase's
+    # device time (CUDA events on the call's stream around the phase)
+    terms_ms = np.mean([s["ms_terms"] for s in stats])
+    terms_bytes = np.mean([s["bytes_terms_use"] for s in stats])
+    terms_gbs = terms_bytes / (terms_ms * 1e-3) / 1e9
     # the FP64 path's application kernel against the FP64 pipe (nominal 1.25 TFLOP/s)
     apply64_ms = np.mean([s["ms_apply"] for s in s64])
     apply64_flops = np.mean([s["flops_apply"] for s in s64])
@@ -462,6 +467,13 @@ def run_ours(args):
                          if traffic else None,
                          "dram_gbs": (traffic / (per_launch_ms * 1e-3) / 1e9) if traffic else None,
                          "dram_frac": (traffic / (per_launch_ms * 1e-3) / 1e9 / peak) if traffic else None},
+            "roofline_a2": {"kernel": "k_panel, k_panel_leaf, k_ff_warp, k_term_jobs (low-rank products)",
+                            "bound": "hbm", "achieved": terms_gbs, "peak": peak, "unit": "GB/s",
+                            "frac": terms_gbs / peak, "peak_source": peak_kind, "ms_per_step": terms_ms,
+                            "bytes_per_step": terms_bytes,
+                            "bytes_basis": "per use: every panel reads its H-block once plus its input and "
+                                           "output columns; every far x far product its four factors and "
+                                           "the new one"},
             "cpu_baseline": {"value": W["n"] / t_est, "unit": UNIT, "cores": thr, "kind": "oracle",
                              "sample": desc},
             "config1_measured": {"config": CONFIG1, "gpu_f64_ms": c1_gpu_ms,

@@ -392,8 +392,8 @@ __global__ void __launch_bounds__(AT) k_apply(ApplyArgs a) {
   const T *X = (const T *)a.x_base + t.x_off;  // Omega or Q_new, column-major inlen x p
   T *Out = (T *)a.y_base + t.y_off;            // column-major outlen x p
   const int p = a.round == 0 ? t.p0 : a.p;     // this target's columns this round (<= P)
-  for (int o = threadIdx.x; o < inlen * P; o += AT) {
-    const int i = o / P, c = o - i * P;
+  for (int o = threadIdx.x; o < inlen * P; o += AT) {  // threads along the rows: coalesced reads
+    const int c = o / inlen, i = o - c * inlen;
     Xs[i * SP + c] = c < p ? X[i + (int64_t)c * inlen] : T(0);
   }
   for (int o = threadIdx.x; o < outlen * SP; o += AT) Ys[o] = T(0);
@@ -550,11 +550,13 @@ __device__ __forceinline__ PanelJob panel_job(const PanelArgs &a, const PanelDev
   return q;
 }
 
+// the panel's input columns into the row-major staging (row stride SP); threads run along the
+// rows of each column, so the global reads are coalesced
 template <typename T, int P, int SP>
 __device__ __forceinline__ void panel_stage(T *Xs, const PanelJob &q, int inlen, const T *src, int lane0,
                                             int nthreads) {
   for (int o = lane0; o < inlen * P; o += nthreads) {
-    const int i = o / P, c = o - i * P;
+    const int c = o / inlen, i = o - c * inlen;
     Xs[i * SP + c] = c < q.ncol ? src[q.src + (int64_t)c * q.src_ld + i] : T(0);
   }
 }
@@ -589,7 +591,6 @@ __global__ void __launch_bounds__(AT) k_panel_leaf(PanelArgs a) {
   }
 }
 
-// one block per panel of an inner H-block; leaves split over warps, shared-memory atomics
 // one panel of an inner H-block; leaves split over warps, shared-memory atomics
 template <typename T, int P, bool GSTAGE>
 __device__ __forceinline__ void panel_body(const PanelArgs &a, int pi, unsigned char *smem_raw) {

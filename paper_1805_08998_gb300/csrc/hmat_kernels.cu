@@ -581,8 +581,11 @@ __global__ void __launch_bounds__(NT) k_gaussian(const TargetDev *tg, const Targ
   const TargetDev t = tg[b];
   if (round == 0) p = t.p0;
   T *X = x_base + t.x_off;
-  for (int c = 0; c < p; c++)
-    for (int i = threadIdx.x; i < t.n; i += NT) X[i + (int64_t)c * t.n] = T(omega(seed, t.leaf, round, c, i));
+  // all n p entries over the block's threads (a 64-row target would otherwise keep a quarter busy)
+  for (int o = threadIdx.x; o < t.n * p; o += NT) {
+    const int c = o / t.n, i = o - c * t.n;
+    X[o] = T(omega(seed, t.leaf, round, c, i));
+  }
 }
 
 // ---------------------------------------------------------------------------------------

@@ -591,9 +591,10 @@ __global__ void __launch_bounds__(AT) k_panel_leaf(PanelArgs a) {
   }
 }
 
-// one panel of an inner H-block; leaves split over warps, shared-memory atomics
-template <typename T, int P, bool GSTAGE>
+// one panel of an inner H-block; leaves split over the block's NW warps, shared-memory atomics
+template <typename T, int P, bool GSTAGE, int NW>
 __device__ __forceinline__ void panel_body(const PanelArgs &a, int pi, unsigned char *smem_raw) {
+  constexpr int NTH = NW * 32;
   const PanelJob pj = panel_job(a, a.panels[a.first + pi], P);
   const BlockDev bk = a.blocks[pj.blk];
   const bool trans = pj.trans;
@@ -612,31 +613,33 @@ __device__ __forceinline__ void panel_body(const PanelArgs &a, int pi, unsigned 
   const int warp = threadIdx.x >> 5;
   T *cw = cwall + warp * a.smem_cw * SP;
   const T *src = (const T *)(trans ? a.dataA : a.dataB);
-  panel_stage<T, P, SP>(Xs, pj, inlen, src, threadIdx.x, AT);
-  for (int o = threadIdx.x; o < outlen * SP; o += AT) Os[o] = T(0);
+  panel_stage<T, P, SP>(Xs, pj, inlen, src, threadIdx.x, NTH);
+  for (int o = threadIdx.x; o < outlen * SP; o += NTH) Os[o] = T(0);
   __syncthreads();
   const LeafDev *leaves = trans ? a.leafB : a.leafA;
   const T *data = (const T *)(trans ? a.dataB : a.dataA);
-  for (int l = bk.leaf_lo + warp; l < bk.leaf_hi; l += NWARP)
+  for (int l = bk.leaf_lo + warp; l < bk.leaf_hi; l += NW)
     warp_leaf<T, P, SP>(leaves[l], data, trans, bk.row, bk.col, Xs, Os, cw);
   __syncthreads();
   T *out = (T *)a.terms;
-  for (int o = threadIdx.x; o < outlen * pj.ncol; o += AT) {
+  for (int o = threadIdx.x; o < outlen * pj.ncol; o += NTH) {
     const int c = o / outlen, i = o - c * outlen;
     out[pj.dst + (int64_t)c * pj.dst_ld + i] = Os[i * SP + c];
   }
 }
 
 // shared-memory staging: one block per panel; global staging: a bounded number of blocks loops
-// over the panels, block b using staging slot b
-template <typename T, int P, bool GSTAGE>
-__global__ void __launch_bounds__(AT) k_panel(PanelArgs a) {
+// over the panels, block b using staging slot b. NW warps per block: 4 for H-blocks of at most
+// 128 rows (at most 4 leaves of 64 rows, so that fewer warps wait idle at the block barriers),
+// else 8.
+template <typename T, int P, bool GSTAGE, int NW = NWARP>
+__global__ void __launch_bounds__(NW * 32) k_panel(PanelArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   if (!GSTAGE) {
-    panel_body<T, P, false>(a, blockIdx.x, smem_raw);
+    panel_body<T, P, false, NW>(a, blockIdx.x, smem_raw);
   } else {
     for (int pi = blockIdx.x; pi < a.count; pi += gridDim.x) {
-      panel_body<T, P, true>(a, pi, smem_raw);
+      panel_body<T, P, true, NW>(a, pi, smem_raw);
       __syncthreads();  // the staging slot and shared memory are reused by the next panel
     }
   }

@@ -65,6 +65,11 @@ static cudaError_t launch_panels_t(const PanelArgs &a, bool leaf_kind, cudaStrea
     if ((e = raise_smem_limit(k_panel<T, P, true>, smem)))
       return e;
     k_panel<T, P, true><<<std::min(a.count, PANEL_GSTAGE_SLOTS), AT, smem, s>>>(a);
+  } else if (a.smem_in <= 128 && a.smem_out <= 128) {  // small H-blocks: four warps per panel
+    const size_t smem4 = (size_t)(a.smem_in + a.smem_out) * SP * es + (size_t)4 * a.smem_cw * SP * es;
+    if ((e = raise_smem_limit(k_panel<T, P, false, 4>, smem4)))
+      return e;
+    k_panel<T, P, false, 4><<<a.count, 128, smem4, s>>>(a);
   } else {
     if ((e = raise_smem_limit(k_panel<T, P, false>, smem)))
       return e;

@@ -1,6 +1,7 @@
-"""Fixed-rank mode (Algorithm 9: k Gaussian samples, q subspace iterations, no eps test) against
-the best rank-k approximation of every far block of the exact product (Eckart-Young: the SVD
-tail after k singular values)."""
+"""Fixed-rank mode (Algorithm 9: k Gaussian samples, q subspace iterations, no eps test) on every
+far block of the exact product: against the oracle's Algorithm 9 fed the same Gaussian samples
+(the device's counter-based generator restated on the oracle's side), and against the best
+rank-k approximation (Eckart-Young: the SVD tail after k singular values)."""
 import numpy as np
 import pytest
 
@@ -61,6 +62,39 @@ def test_fixed_rank_near_optimal(H, oracle, case, k, q, mode):
     med_bar, max_bar = (1.5, 8.0) if q >= 1 else (6.0, 100.0)
     print(f"k={k} q={q} {mode}: median err/best {np.median(ratio):.3f}, max {np.max(ratio):.3f}")
     assert np.median(ratio) <= med_bar and np.max(ratio) <= max_bar
+
+
+@pytest.mark.parametrize("k,q,mode", [(4, 1, "f64"), (8, 1, "f64"), (8, 0, "f64"), (6, 2, "mixed")])
+def test_fixed_rank_matches_oracle_alg9(H, oracle, case, k, q, mode):
+    """Same samples, same steps: the block error of the device result equals that of the oracle's
+    Algorithm 9 on the exact block. The two sides' samples can differ in the last bit or two of an
+    FP32 entry (each evaluates the Box-Muller transform itself); perturbing every sample of these
+    blocks by two units in the last place moves the oracle's error by at most 7e-5 of itself, so
+    the bar is 1e-3 of the error plus the rounding floor of the arithmetic."""
+    from oracle import compressors, gaussian
+    T, A, DC = case
+    md = H.MODE_F64 if mode == "f64" else H.MODE_MIXED
+    seed = 5
+    C = H.hmat_multiply(A, A, 1e-12 if mode == "f64" else 1e-7, mode=md, fixed_rank=k, power_iters=q, seed=seed)
+    assert C.last_status == H.HMAT_OK
+    floor_rel = 1e-13 if mode == "f64" else 5e-7
+    worst, checked = 0.0, 0
+    for l in range(T.nleaf):
+        if T.leaf_blocks[l, 2] != 1:
+            continue
+        r0, m, c0, n = T.leaf_ranges(l)
+        D = DC[r0:r0 + m, c0:c0 + n]
+        L, U = compressors.fixed_rank(D, gaussian.omega(seed, l, 0, n, k), q)
+        e_or = np.linalg.norm(D - L @ U.T)
+        Ug, Vg = C.leaf_get(l)
+        e_gpu = np.linalg.norm(D - Ug @ Vg.T)
+        nb = np.linalg.norm(D)
+        dev = abs(e_gpu - e_or) - floor_rel * nb
+        assert dev <= 1e-3 * e_or, (l, m, n, e_gpu / nb, e_or / nb)
+        worst = max(worst, dev / max(e_or, 1e-300))
+        checked += 1
+    assert checked > 100
+    print(f"k={k} q={q} {mode}: {checked} blocks, worst |e_gpu - e_oracle| beyond the floor {worst:.2e} of e_oracle")
 
 
 def test_fixed_rank_invalid(H):

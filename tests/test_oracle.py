@@ -729,3 +729,30 @@ def test_randomized_meets_paper_eps_on_product_blocks(oracle):
         err = np.linalg.norm(D - L @ U.T) / np.linalg.norm(D)
         assert err <= 1.5 * eps, (l, err)
         assert L.shape[1] <= oracle.eps_rank(s, eps) + 2
+
+
+def test_gaussian_test_matrix_generator():
+    """The oracle-side Gaussian generator: its stream is the published splitmix64 (checked
+    against the independent stream of the input module at the counters it names), its entries
+    are standard normal (Kolmogorov-Smirnov against N(0, 1) on 200 000 draws), and different
+    leaves, rounds and columns draw uncorrelated samples."""
+    import math
+    from scipy import stats
+    from oracle import gaussian
+    seed = 12345
+    G = gaussian.omega(seed, 7, 2, 300, 5)
+    assert G.shape == (300, 5) and np.array_equal(G, G.astype(np.float32).astype(np.float64))
+    for i, c in ((0, 0), (299, 4), (17, 3)):
+        t = (((7 * 64 + 2) * 64 + c) << 24) + i
+        z1, z2 = (int(v) for v in inputs.splitmix64(seed, 2, 2 * t))
+        u1 = ((z1 >> 40) + 1) * 2.0 ** -24
+        u2 = (z2 >> 40) * 2.0 ** -24
+        assert G[i, c] == float(np.float32(math.sqrt(-2.0 * math.log(u1)) * math.cos(2.0 * math.pi * u2)))
+    big = gaussian.omega(3, 11, 0, 40000, 5).ravel()
+    assert stats.kstest(big, "norm").pvalue > 1e-3
+    assert abs(big.mean()) < 0.02 and abs(big.var() - 1.0) < 0.02
+    cols = np.hstack([gaussian.omega(3, leaf, rd, 20000, 2) for leaf, rd in ((0, 0), (1, 0), (0, 1))])
+    cc = np.corrcoef(cols.T)
+    assert np.abs(cc - np.eye(6)).max() < 0.05
+    with pytest.raises(ValueError):
+        gaussian.omega(3, 0, 64, 10, 2)

@@ -55,7 +55,7 @@ typedef enum {
   HMAT_ECUDA = 3,      /* a CUDA runtime call or kernel launch failed */
   HMAT_ENOTCONV = 4,   /* some far block hit max_rank / max_rounds before the stop test held;
                           the result is complete and usable, see hmat_stats.not_converged */
-  HMAT_ETIMEOUT = 5,   /* reserved: a bounded device wait gave up */
+  HMAT_ETIMEOUT = 5,   /* a bounded device wait gave up (the tensor-core near field of an FP32 product) */
   HMAT_EMISMATCH = 6   /* the two factors of a product are not on the same block tree */
 } hmat_status;
 

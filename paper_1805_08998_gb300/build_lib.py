@@ -17,9 +17,9 @@ NVCC = os.path.join(CUDA, "bin", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 CU_SOURCES = ["hmat_kernels.cu", "hmat_apply.cu", "hmat_apply_f32.cu", "hmat_apply_f32_trans.cu",
-              "hmat_apply_f64.cu", "hmat_apply_f64_trans.cu", "hmat_rank.cu"]
+              "hmat_apply_f64.cu", "hmat_apply_f64_trans.cu", "hmat_rank.cu", "hmat_near_tc.cu"]
 CPP_SOURCES = ["hmat_tree.cpp", "hmat_api.cpp"]
-HEADERS = ["hmat_internal.h", "hmat_tree.h", "hmat_apply.cuh", "hmat_apply_launch.cuh"]
+HEADERS = ["hmat_internal.h", "hmat_tree.h", "hmat_apply.cuh", "hmat_apply_launch.cuh", "hmat_tc.cuh"]
 
 
 def _newer(out: str, deps) -> bool:

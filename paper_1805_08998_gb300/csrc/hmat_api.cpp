@@ -1879,12 +1879,21 @@ void Product::run() {
   DevBuf d_near(es * std::max<int64_t>(near_elems, 1), s2.st);
   DevBuf d_near_leaves = upload(C->leaves, s2.st);
   DevBuf d_ntg = upload(ntg, s2.st), d_npairs = upload(npairs, s2.st);
+  DevBuf d_nerr(sizeof(int), s2.st);
+  ck(cudaMemsetAsync(d_nerr.p, 0, sizeof(int), s2.st), "memset");
   ck(cudaEventRecord(s2.e0, s), "event");
   ck(cudaStreamWaitEvent(s2.st, s2.e0, 0), "stream wait");
+  cudaEvent_t ne[2] = {nullptr, nullptr};  // (trace) the near field's own device time
+  if (tr.on) {
+    cudaEventCreate(&ne[0]);
+    cudaEventCreate(&ne[1]);
+    cudaEventRecord(ne[0], s2.st);
+  }
   ck(launch_near_eval(cprec, d_ntg.as<TargetDev>(), (int)ntg.size(), d_blkterms.as<int2>(), d_terms.as<TermDev>(),
                       d_npairs.as<PairDev>(), t.d_blocks, A->d_leaves.as<LeafDev>(), B->d_leaves.as<LeafDev>(), dataA,
-                      dataB, d_near_leaves.as<LeafDev>(), d_near.p, s2.st),
+                      dataB, d_near_leaves.as<LeafDev>(), d_near.p, d_nerr.as<int>(), s2.st),
      "near field");
+  if (tr.on) cudaEventRecord(ne[1], s2.st);
   ck(cudaEventRecord(s2.e1, s2.st), "event");
 
   tr.mark("near field launched");
@@ -2264,7 +2273,17 @@ void Product::run() {
     ck(cudaMemcpyAsync(go.data.p, d_near.p, es * near_elems, cudaMemcpyDeviceToDevice, s), "near copy");
   launches += (nf > 0 ? 1 : 0) + (ntg.empty() ? 0 : 1);
   ck(cudaEventRecord(ev[4], s), "event");
+  int near_err = 0;
+  ck(cudaMemcpyAsync(&near_err, d_nerr.p, sizeof(int), cudaMemcpyDeviceToHost, s), "near status");
   ck(cudaStreamSynchronize(s), "product");
+  if (tr.on) {
+    float nms = 0;
+    cudaEventElapsedTime(&nms, ne[0], ne[1]);
+    std::fprintf(stderr, "hmat trace: near field kernel: %zu leaves, %.3f ms (on its own stream)\n", ntg.size(), nms);
+    cudaEventDestroy(ne[0]);
+    cudaEventDestroy(ne[1]);
+  }
+  if (near_err) fail(HMAT_ETIMEOUT, "near field: a bounded tensor-core wait gave up");
   tr.mark("C written, synchronised");
   double ms_apply = 0;
   for (size_t i = 0; i + 1 < aev.size(); i += 2) {

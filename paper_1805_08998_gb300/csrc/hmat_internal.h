@@ -185,10 +185,16 @@ cudaError_t launch_term_jobs(int prec, const TermJob *jobs, const int32_t *ids, 
 cudaError_t launch_make_terms(int prec, const TermJob *jobs, int njobs, const BlockDev *blocks,
                               const LeafDev *leafA, const LeafDev *leafB, const void *dataA,
                               const void *dataB, const void *termbuf, TermDev *terms, cudaStream_t s);
+// a8: FP64 on the FP64 pipe; FP32 on the tensor cores (3 x TF32), which set *err when one of
+// their bounded waits gives up
 cudaError_t launch_near_eval(int prec, const TargetDev *tg, int ntg, const int2 *blk_terms,
                              const TermDev *terms, const PairDev *pairs, const BlockDev *blocks,
                              const LeafDev *leafA, const LeafDev *leafB, const void *dataA,
-                             const void *dataB, const LeafDev *leafC, void *dataC, cudaStream_t s);
+                             const void *dataB, const LeafDev *leafC, void *dataC, int *err, cudaStream_t s);
+cudaError_t launch_near_tc(const TargetDev *tg, int ntg, const int2 *blk_terms, const TermDev *terms,
+                           const PairDev *pairs, const BlockDev *blocks, const LeafDev *leafA, const LeafDev *leafB,
+                           const float *dataA, const float *dataB, const LeafDev *leafC, float *dataC, int *err,
+                           cudaStream_t s);
 cudaError_t launch_apply(int prec, bool trans, const ApplyArgs &a, cudaStream_t s);
 size_t apply_smem_bytes(int prec, int P, const ApplyArgs &a);
 int apply_rows_per_lane(int dmax);

@@ -1984,14 +1984,13 @@ cudaError_t launch_make_terms(int prec, const TermJob *jobs, int njobs, const Bl
 cudaError_t launch_near_eval(int prec, const TargetDev *tg, int ntg, const int2 *blk_terms, const TermDev *terms,
                              const PairDev *pairs, const BlockDev *blocks, const LeafDev *leafA,
                              const LeafDev *leafB, const void *dataA, const void *dataB, const LeafDev *leafC,
-                             void *dataC, cudaStream_t s) {
+                             void *dataC, int *err, cudaStream_t s) {
   if (ntg == 0) return cudaSuccess;
-  if (prec == 64)
-    k_near_eval<double><<<ntg, NT, 0, s>>>(tg, blk_terms, terms, pairs, blocks, leafA, leafB, (const double *)dataA,
-                                           (const double *)dataB, leafC, (double *)dataC);
-  else
-    k_near_eval<float><<<ntg, NT, 0, s>>>(tg, blk_terms, terms, pairs, blocks, leafA, leafB, (const float *)dataA,
-                                          (const float *)dataB, leafC, (float *)dataC);
+  if (prec != 64)
+    return launch_near_tc(tg, ntg, blk_terms, terms, pairs, blocks, leafA, leafB, (const float *)dataA,
+                          (const float *)dataB, leafC, (float *)dataC, err, s);
+  k_near_eval<double><<<ntg, NT, 0, s>>>(tg, blk_terms, terms, pairs, blocks, leafA, leafB, (const double *)dataA,
+                                         (const double *)dataB, leafC, (double *)dataC);
   return cudaGetLastError();
 }
 

@@ -631,7 +631,7 @@ __device__ __forceinline__ void panel_body(const PanelArgs &a, int pi, unsigned 
 // shared-memory staging: one block per panel; global staging: a bounded number of blocks loops
 // over the panels, block b using staging slot b. NW warps per block: 4 for H-blocks of at most
 // 128 rows (at most 4 leaves of 64 rows, so that fewer warps wait idle at the block barriers),
-// else 8.
+// 16 for H-blocks of more than 512 rows (whose staging lets one block per SM), else 8.
 template <typename T, int P, bool GSTAGE, int NW = NWARP>
 __global__ void __launch_bounds__(NW * 32) k_panel(PanelArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];

@@ -70,6 +70,13 @@ static cudaError_t launch_panels_t(const PanelArgs &a, bool leaf_kind, cudaStrea
     if ((e = raise_smem_limit(k_panel<T, P, false, 4>, smem4)))
       return e;
     k_panel<T, P, false, 4><<<a.count, 128, smem4, s>>>(a);
+  } else if (a.smem_in > 512 && (size_t)(a.smem_in + a.smem_out) * SP * es + (size_t)16 * a.smem_cw * SP * es <=
+                                      (size_t)max_dynamic_smem()) {
+    // H-blocks of more than 512 rows: one block fits an SM, so it runs sixteen warps
+    const size_t smem16 = (size_t)(a.smem_in + a.smem_out) * SP * es + (size_t)16 * a.smem_cw * SP * es;
+    if ((e = raise_smem_limit(k_panel<T, P, false, 16>, smem16)))
+      return e;
+    k_panel<T, P, false, 16><<<a.count, 512, smem16, s>>>(a);
   } else {
     if ((e = raise_smem_limit(k_panel<T, P, false>, smem)))
       return e;

@@ -6,10 +6,12 @@
 // contribution (a term, K = its rank; a leaf pair, K = the inner leaf's size) is staged in chunks
 // of 32 along K into shared memory, split into a TF32 part and its FP32 remainder, and multiplied
 // by three kind::tf32 MMAs per K = 8 (hi hi, hi lo, lo hi) into an FP32 accumulator in TMEM.
-// When a contribution's last chunk is done its tile is read back (tcgen05.ld) and added to the
-// block with a compensated (Neumaier) sum, so the error does not grow with the number of
-// contributions. Two shared-memory stages and two TMEM accumulators let the staging of the next
-// chunk and the read-back of the last contribution run while the tensor cores work.
+// Groups of up to FOLD_GROUP consecutive contributions accumulate in one TMEM accumulator; when a
+// group's last chunk is done its tile is read back (tcgen05.ld) and added to the block with a
+// compensated (Neumaier) sum, so the error grows with the size of a group (a few roundings) and
+// not with the number of contributions. Two shared-memory stages and two TMEM accumulators let
+// the staging of the next chunk and the read-back of the last group run while the tensor cores
+// work.
 #include "hmat_internal.h"
 #include "hmat_tc.cuh"
 
@@ -26,6 +28,7 @@ constexpr uint32_t SBO = (KC / 4) * 128;  // bytes between groups of 8 rows
 constexpr uint32_t TMEM_COLS = 2 * TM;    // two accumulators of 64 columns
 constexpr int WAIT_POLLS = 1 << 22;       // bounded mbarrier waits
 constexpr uint32_t IDESC = tc::idesc_tf32(TM, TM);
+constexpr int FOLD_GROUP = 4;             // contributions summed in TMEM between two folds
 static_assert(NTC == 128 && KC == 32 && TM == 64, "stage_chunk's thread-to-element map assumes these sizes");
 
 // one contribution restricted to the output tile: A(i, k) = A[i + k a_k] (i < mt),
@@ -171,9 +174,10 @@ __global__ void __launch_bounds__(NTC, 2)
       Contrib cur;
       bool more = wk.next(cur);
       int h = 0;               // chunk of the current contribution
-      uint32_t ci = 0;         // contributions begun in this tile: accumulator ci & 1
+      int cg = 0;              // contributions of the current group done
+      uint32_t gi = 0;         // groups begun in this tile: accumulator gi & 1
       bool have_prev = false;  // a chunk in flight from the previous step
-      bool prev_last = false;  // ... that ends its contribution
+      bool prev_last = false;  // ... that ends its group
       uint32_t prev_acc = 0;
       while (more || have_prev) {
         const uint32_t s = u & 1;
@@ -190,11 +194,11 @@ __global__ void __launch_bounds__(NTC, 2)
           const float *st = stages + s * STAGE_ELEMS;
           const uint32_t a_hi = tc::smem_addr(st), a_lo = tc::smem_addr(st + TILE_ELEMS);
           const uint32_t b_hi = tc::smem_addr(st + 2 * TILE_ELEMS), b_lo = tc::smem_addr(st + 3 * TILE_ELEMS);
-          const uint32_t d = tmem + (ci & 1) * TM;
+          const uint32_t d = tmem + (gi & 1) * TM;
           const int kc = min(KC, cur.K - h * KC);
           for (int kk = 0; kk * 8 < kc; kk++) {
             const uint32_t off = kk * 2 * LBO;  // two core matrices along K per K = 8
-            const uint32_t first = (h == 0 && kk == 0) ? 0u : 1u;
+            const uint32_t first = (cg == 0 && h == 0 && kk == 0) ? 0u : 1u;  // a group starts from zero
             tc::mma_tf32(d, tc::desc_kmajor(a_lo + off, LBO, SBO), tc::desc_kmajor(b_hi + off, LBO, SBO), IDESC, first);
             tc::mma_tf32(d, tc::desc_kmajor(a_hi + off, LBO, SBO), tc::desc_kmajor(b_lo + off, LBO, SBO), IDESC, 1);
             tc::mma_tf32(d, tc::desc_kmajor(a_hi + off, LBO, SBO), tc::desc_kmajor(b_hi + off, LBO, SBO), IDESC, 1);
@@ -226,14 +230,18 @@ __global__ void __launch_bounds__(NTC, 2)
         }
         have_prev = more;
         if (more) {
-          prev_acc = ci & 1;
+          prev_acc = gi & 1;
           u++;
           h++;
-          prev_last = h * KC >= cur.K;
-          if (prev_last) {
+          prev_last = false;
+          if (h * KC >= cur.K) {  // the contribution is done
             h = 0;
-            ci++;
             more = wk.next(cur);
+            if (++cg == FOLD_GROUP || !more) {  // ... and so is its group
+              prev_last = true;
+              cg = 0;
+              gi++;
+            }
           }
         }
       }

@@ -190,6 +190,8 @@ typedef struct {
                                     reads its H-block's stored elements once plus its input and
                                     output columns; every far x far product reads its four factors
                                     and writes the new one */
+  double ms_near_kernel;         /* device time of the near-field kernel (a8), from CUDA events on
+                                    the second stream it runs on, concurrently with the sampling */
 } hmat_stats_t;
 
 /* Synthetic inputs (the paper's experiments, Sec. 6.1, use Galerkin matrices on the unit sphere;

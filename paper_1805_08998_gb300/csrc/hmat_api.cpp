@@ -1883,17 +1883,22 @@ void Product::run() {
   ck(cudaMemsetAsync(d_nerr.p, 0, sizeof(int), s2.st), "memset");
   ck(cudaEventRecord(s2.e0, s), "event");
   ck(cudaStreamWaitEvent(s2.st, s2.e0, 0), "stream wait");
-  cudaEvent_t ne[2] = {nullptr, nullptr};  // (trace) the near field's own device time
-  if (tr.on) {
-    cudaEventCreate(&ne[0]);
-    cudaEventCreate(&ne[1]);
-    cudaEventRecord(ne[0], s2.st);
-  }
+  // the near field's own device time, on its stream
+  struct NearEvents {
+    cudaEvent_t e[2] = {nullptr, nullptr};
+    ~NearEvents() {
+      for (cudaEvent_t x : e)
+        if (x) cudaEventDestroy(x);
+    }
+  } ne;
+  ck(cudaEventCreate(&ne.e[0]), "event");
+  ck(cudaEventCreate(&ne.e[1]), "event");
+  ck(cudaEventRecord(ne.e[0], s2.st), "event");
   ck(launch_near_eval(cprec, d_ntg.as<TargetDev>(), (int)ntg.size(), d_blkterms.as<int2>(), d_terms.as<TermDev>(),
                       d_npairs.as<PairDev>(), t.d_blocks, A->d_leaves.as<LeafDev>(), B->d_leaves.as<LeafDev>(), dataA,
                       dataB, d_near_leaves.as<LeafDev>(), d_near.p, d_nerr.as<int>(), s2.st),
      "near field");
-  if (tr.on) cudaEventRecord(ne[1], s2.st);
+  ck(cudaEventRecord(ne.e[1], s2.st), "event");
   ck(cudaEventRecord(s2.e1, s2.st), "event");
 
   tr.mark("near field launched");
@@ -2276,12 +2281,13 @@ void Product::run() {
   int near_err = 0;
   ck(cudaMemcpyAsync(&near_err, d_nerr.p, sizeof(int), cudaMemcpyDeviceToHost, s), "near status");
   ck(cudaStreamSynchronize(s), "product");
-  if (tr.on) {
+  {
     float nms = 0;
-    cudaEventElapsedTime(&nms, ne[0], ne[1]);
-    std::fprintf(stderr, "hmat trace: near field kernel: %zu leaves, %.3f ms (on its own stream)\n", ntg.size(), nms);
-    cudaEventDestroy(ne[0]);
-    cudaEventDestroy(ne[1]);
+    cudaEventElapsedTime(&nms, ne.e[0], ne.e[1]);
+    S.ms_near_kernel += nms;
+    if (tr.on)
+      std::fprintf(stderr, "hmat trace: near field kernel: %zu leaves, %.3f ms (on its own stream)\n", ntg.size(),
+                   nms);
   }
   if (near_err) fail(HMAT_ETIMEOUT, "near field: a bounded tensor-core wait gave up");
   tr.mark("C written, synchronised");

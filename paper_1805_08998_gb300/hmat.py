@@ -84,7 +84,7 @@ class Stats(ctypes.Structure):
                 ("sample_passes", ctypes.c_int64), ("groups", ctypes.c_int64),
                 ("bytes_apply_unique", ctypes.c_double), ("apply_gstage_targets", ctypes.c_int64),
                 ("apply_split_targets", ctypes.c_int64), ("apply_max_split", ctypes.c_int),
-                ("bytes_terms_use", ctypes.c_double)]
+                ("bytes_terms_use", ctypes.c_double), ("ms_near_kernel", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

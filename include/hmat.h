@@ -275,6 +275,15 @@ hmat_status hmat_matvec(const hmat_t H, const double *x, double *y, int64_t ncol
 hmat_status hmat_product_error(const hmat_t A, const hmat_t B, const hmat_t C, int iters, int size, uint64_t seed,
                                double *rel_err);
 
+/* Check, on the current device, that the library's bounded tensor-core waits give up and
+ * report: one thread block allocates tensor memory, waits on an mbarrier that nothing arrives on
+ * for `polls` polls (1..2^22; the tensor-core near field gives up after 2^18, about a second on
+ * GB300), frees the tensor memory and reports. Returns HMAT_ETIMEOUT when the wait gave up (the expected result; the CUDA context
+ * stays usable), HMAT_OK if it completed (it cannot), HMAT_EINVAL for polls out of range and
+ * HMAT_ECUDA on a CUDA error. A test hook for the failure path of the FP32 near field; the paper
+ * has no counterpart. Synchronises. */
+hmat_status hmat_check_bounded_wait(int polls);
+
 /* count independent products C[i] = A[i] B[i] (each pair on one block tree; the trees of
  * different pairs may differ) with the same options, in one call: the products are planned on
  * host threads and run on up to 8 streams of their own, largest first, so that the GPU works on

@@ -823,6 +823,18 @@ hmat_status hmat_matvec(const hmat_t H, const double *x, double *y, int64_t ncol
   });
 }
 
+hmat_status hmat_check_bounded_wait(int polls) {
+  return guard([&] {
+    if (polls < 1 || polls > (1 << 22)) fail(HMAT_EINVAL, "polls must be in 1..2^22");
+    DevBuf d(sizeof(int), nullptr);
+    ck(cudaMemsetAsync(d.p, 0, sizeof(int), nullptr), "memset");
+    ck(launch_tc_wait_check(polls, d.as<int>(), nullptr), "bounded wait");
+    int gave_up = 0;
+    ck(cudaMemcpy(&gave_up, d.p, sizeof(int), cudaMemcpyDeviceToHost), "bounded wait");
+    if (gave_up) fail(HMAT_ETIMEOUT, "the bounded wait gave up (expected)");
+  });
+}
+
 hmat_status hmat_product_error(const hmat_t A, const hmat_t B, const hmat_t C, int iters, int size, uint64_t seed,
                                double *rel_err) {
   return guard([&] {

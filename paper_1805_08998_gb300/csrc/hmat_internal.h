@@ -191,6 +191,8 @@ cudaError_t launch_near_eval(int prec, const TargetDev *tg, int ntg, const int2 
                              const TermDev *terms, const PairDev *pairs, const BlockDev *blocks,
                              const LeafDev *leafA, const LeafDev *leafB, const void *dataA,
                              const void *dataB, const LeafDev *leafC, void *dataC, int *err, cudaStream_t s);
+// one block: a bounded wait on an mbarrier that nothing arrives on (the near field's failure path)
+cudaError_t launch_tc_wait_check(int polls, int *gave_up, cudaStream_t s);
 cudaError_t launch_near_tc(const TargetDev *tg, int ntg, const int2 *blk_terms, const TermDev *terms,
                            const PairDev *pairs, const BlockDev *blocks, const LeafDev *leafA, const LeafDev *leafB,
                            const float *dataA, const float *dataB, const LeafDev *leafC, float *dataC, int *err,

@@ -26,7 +26,7 @@ constexpr int STAGE_ELEMS = 4 * TILE_ELEMS;
 constexpr uint32_t LBO = 128;             // bytes between core matrices along K
 constexpr uint32_t SBO = (KC / 4) * 128;  // bytes between groups of 8 rows
 constexpr uint32_t TMEM_COLS = 2 * TM;    // two accumulators of 64 columns
-constexpr int WAIT_POLLS = 1 << 22;       // bounded mbarrier waits
+constexpr int WAIT_POLLS = 1 << 18;       // bounded mbarrier waits: about 1 s on GB300
 constexpr uint32_t IDESC = tc::idesc_tf32(TM, TM);
 constexpr int FOLD_GROUP = 4;             // contributions summed in TMEM between two folds
 static_assert(NTC == 128 && KC == 32 && TM == 64, "stage_chunk's thread-to-element map assumes these sizes");
@@ -257,7 +257,33 @@ __global__ void __launch_bounds__(NTC, 2)
   if (warp == 0) tc::tmem_free(tmem, TMEM_COLS);
 }
 
+// The failure path of the waits above on its own: TMEM held, a wait on an mbarrier that nothing
+// arrives on, then the same exit (TMEM freed). *gave_up = 1 when the wait gave up.
+__global__ void __launch_bounds__(NTC) k_tc_wait_check(int polls, int *gave_up) {
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tslot;
+  const int warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) tc::mbar_init(&mbar, 1);
+  tc::fence_smem_to_async();
+  if (warp == 0) tc::tmem_alloc(&tslot, 32);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = tslot;
+  const bool ok = tc::mbar_wait(&mbar, 0, polls);
+  const bool failed = __syncthreads_or(!ok) != 0;
+  if (threadIdx.x == 0) *gave_up = failed ? 1 : 0;
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_free(tmem, 32);
+}
+
 }  // namespace
+
+cudaError_t launch_tc_wait_check(int polls, int *gave_up, cudaStream_t s) {
+  k_tc_wait_check<<<1, NTC, 0, s>>>(polls, gave_up);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_near_tc(const TargetDev *tg, int ntg, const int2 *blk_terms, const TermDev *terms,
                            const PairDev *pairs, const BlockDev *blocks, const LeafDev *leafA, const LeafDev *leafB,

@@ -31,7 +31,8 @@ EXPORTS = ["hmat_points", "hmat_build", "hmat_plan_host", "hmat_multiply", "hmat
            "hmat_leaf_get", "hmat_permutation", "hmat_stats", "hmat_sumexpr_counts", "hmat_destroy",
            "hmat_data_bytes", "hmat_data_get", "hmat_rank_features", "hmat_rankmodel_train",
            "hmat_rankmodel_predict", "hmat_rankmodel_get", "hmat_rankmodel_create", "hmat_rankmodel_grad",
-           "hmat_rankmodel_grad_noalloc", "hmat_rankmodel_destroy", "hmat_matvec", "hmat_product_error", "hmat_last_error", "hmat_set_allocator"]
+           "hmat_rankmodel_grad_noalloc", "hmat_rankmodel_destroy", "hmat_matvec", "hmat_product_error", "hmat_last_error", "hmat_set_allocator",
+           "hmat_check_bounded_wait"]
 
 RANK_FEATURES = 12
 RANK_PARAMS = 5057
@@ -132,6 +133,7 @@ def lib():
     L.hmat_rankmodel_grad_noalloc.argtypes = [_P, _PF, _PF, _I64, _PF, _PF, _P]
     L.hmat_matvec.argtypes = [_P, _PD, _PD, _I64, _P]
     L.hmat_product_error.argtypes = [_P, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_uint64, _PD]
+    L.hmat_check_bounded_wait.argtypes = [ctypes.c_int]
     L.hmat_rankmodel_destroy.argtypes = [_P]
     L.hmat_rankmodel_destroy.restype = None
     L.hmat_destroy.argtypes = [_P]
@@ -142,7 +144,8 @@ def lib():
                  "hmat_leaf_info", "hmat_leaf_get", "hmat_permutation", "hmat_stats", "hmat_sumexpr_counts",
                  "hmat_set_allocator", "hmat_data_bytes", "hmat_data_get", "hmat_rank_features",
                  "hmat_rankmodel_train", "hmat_rankmodel_predict", "hmat_rankmodel_get", "hmat_rankmodel_create",
-                 "hmat_rankmodel_grad", "hmat_rankmodel_grad_noalloc", "hmat_matvec", "hmat_product_error"]:
+                 "hmat_rankmodel_grad", "hmat_rankmodel_grad_noalloc", "hmat_matvec", "hmat_product_error",
+                 "hmat_check_bounded_wait"]:
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -327,6 +330,11 @@ def hmat_matvec(Hm: HMatrix, x, stream=None) -> np.ndarray:
     Y = np.zeros_like(X, order="F")
     _check(lib().hmat_matvec(Hm.handle, X.ctypes.data_as(_PD), Y.ctypes.data_as(_PD), X.shape[1], _stream_ptr(stream)))
     return Y[:, 0].copy() if vec else np.ascontiguousarray(Y)
+
+
+def hmat_check_bounded_wait(polls: int) -> int:
+    """Status of the library's bounded-wait check (HMAT_ETIMEOUT when the wait gave up)."""
+    return lib().hmat_check_bounded_wait(polls)
 
 
 def hmat_product_error(A: HMatrix, B: HMatrix, C: HMatrix, iters: int = 10, size: int = 100, seed: int = 0) -> float:

@@ -30,6 +30,7 @@
 namespace hm {
 
 constexpr int NT = 256;     // threads per block
+constexpr int ACA_KMAX = 128;  // largest rank of the input ACA (hmat_build rejects larger aca_kmax)
 constexpr int KC = 32;      // rows staged per chunk in the SIMT contractions
 constexpr int PMAX = 32;    // max right-hand-side columns per contraction call
 constexpr int RMAX = 128;   // max rank / leaf size handled by one contraction call
@@ -290,7 +291,9 @@ __global__ void __launch_bounds__(NT) k_aca(int kernel, const double *pts, int d
   __shared__ double redv[NT / 32];
   __shared__ int64_t redi[NT / 32];
   __shared__ double red[NT / 32];
+  __shared__ double dots[2][ACA_KMAX][NT / 32];  // per warp: L_q . l_k and R_q . r_k, q <= k
   const int f = blockIdx.x;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const LeafDev lf = leaves[ids[f]];
   const int64_t m = lf.m, n = lf.n;
   double *L = scratch + soff[f];
@@ -346,19 +349,35 @@ __global__ void __launch_bounds__(NT) k_aca(int kernel, const double *pts, int d
       L[k * m + i] = v;
     }
     __syncthreads();
-    double pl = 0.0, pu = 0.0;
-    for (int64_t i = threadIdx.x; i < m; i += NT) pl += L[k * m + i] * L[k * m + i];
-    for (int64_t j = threadIdx.x; j < n; j += NT) pu += R[k * n + j] * R[k * n + j];
-    const double nl = block_sum(pl, red), nu = block_sum(pu, red);
-    double cross = 0.0;
-    for (int q = 0; q < k; q++) {
+    // ||L_{k+1} U_{k+1}^T||_F^2 = ||L_k U_k^T||_F^2 + 2 sum_{q<k} (L_q . l_k)(R_q . r_k) + |l_k|^2 |r_k|^2:
+    // every dot of this step (q <= k) reduced within each warp, then across the warps once
+    for (int q = 0; q <= k; q++) {
       double a = 0.0, b = 0.0;
       for (int64_t i = threadIdx.x; i < m; i += NT) a += L[q * m + i] * L[k * m + i];
       for (int64_t j = threadIdx.x; j < n; j += NT) b += R[q * n + j] * R[k * n + j];
-      a = block_sum(a, red);
-      b = block_sum(b, red);
-      cross += a * b;
+      a = warp_sum(a);
+      b = warp_sum(b);
+      if (lane == 0) {
+        dots[0][q][w] = a;
+        dots[1][q][w] = b;
+      }
     }
+    __syncthreads();
+    double nl = 0.0, nu = 0.0;
+    for (int x = 0; x < NT / 32; x++) {
+      nl += dots[0][k][x];
+      nu += dots[1][k][x];
+    }
+    double part = 0.0;
+    for (int q = threadIdx.x; q < k; q += NT) {
+      double a = 0.0, b = 0.0;
+      for (int x = 0; x < NT / 32; x++) {
+        a += dots[0][q][x];
+        b += dots[1][q][x];
+      }
+      part += a * b;
+    }
+    const double cross = block_sum(part, red);  // (its barriers also end this step's reads of dots)
     const double prev = norm2;
     norm2 = prev + 2.0 * cross + nl * nu;
     k++;
@@ -1795,6 +1814,7 @@ cudaError_t launch_aca(int kernel, const double *pts, int dim, const LeafDev *le
                        int nfar, double eps, int kmax, double *scratch, const int64_t *scratch_off, int32_t *ranks,
                        cudaStream_t s) {
   if (nfar == 0) return cudaSuccess;
+  if (kmax < 1 || kmax > ACA_KMAX) return cudaErrorInvalidValue;  // the kernel's dot table holds ACA_KMAX
   k_aca<<<nfar, NT, 0, s>>>(kernel, pts, dim, leaves, far_ids, eps, kmax, scratch, scratch_off, ranks);
   return cudaGetLastError();
 }

@@ -639,13 +639,29 @@ hmat_status hmat_build(const double *xyz, int64_t n, int dim, hmat_kernel kernel
           pos++;
         }
         DevBuf scratch(sizeof(double) * tot, s), d_soff = upload(soff, s), d_ids = upload(ids, s);
+        // the ACA runs leaves of at most 64 x 64 one warp each, the others one block each: its
+        // launch lists the small ones first (the factor layout keeps the batch's own order)
+        std::vector<int32_t> order;
+        for (size_t i = 0; i < ids.size(); i++)
+          if (lv[ids[i]].m <= 64 && lv[ids[i]].n <= 64) order.push_back((int32_t)i);
+        const int nsmall = (int)order.size();
+        for (size_t i = 0; i < ids.size(); i++)
+          if (!(lv[ids[i]].m <= 64 && lv[ids[i]].n <= 64)) order.push_back((int32_t)i);
+        std::vector<int32_t> ids_l(ids.size());
+        std::vector<int64_t> soff_l(ids.size());
+        for (size_t i = 0; i < ids.size(); i++) {
+          ids_l[i] = ids[order[i]];
+          soff_l[i] = soff[order[i]];
+        }
+        DevBuf d_ids_l = upload(ids_l, s), d_soff_l = upload(soff_l, s);
         DevBuf d_rk(sizeof(int32_t) * ids.size(), s);
-        ck(launch_aca(kernel, t.d_pts, dim, d_lv0.as<LeafDev>(), d_ids.as<int32_t>(), (int)ids.size(), opts->aca_eps,
-                      kmax, scratch.as<double>(), d_soff.as<int64_t>(), d_rk.as<int32_t>(), s),
+        ck(launch_aca(kernel, t.d_pts, dim, d_lv0.as<LeafDev>(), d_ids_l.as<int32_t>(), (int)ids.size(), nsmall,
+                      opts->aca_eps, kmax, scratch.as<double>(), d_soff_l.as<int64_t>(), d_rk.as<int32_t>(), s),
            "ACA launch");
-        std::vector<int32_t> rk(ids.size());
-        ck(cudaMemcpyAsync(rk.data(), d_rk.p, sizeof(int32_t) * ids.size(), cudaMemcpyDeviceToHost, s), "ranks");
+        std::vector<int32_t> rk_l(ids.size()), rk(ids.size());
+        ck(cudaMemcpyAsync(rk_l.data(), d_rk.p, sizeof(int32_t) * ids.size(), cudaMemcpyDeviceToHost, s), "ranks");
         ck(cudaStreamSynchronize(s), "ACA");
+        for (size_t i = 0; i < ids.size(); i++) rk[order[i]] = rk_l[i];
         // batch-relative offsets
         std::vector<LeafDev> blv = lv;
         int64_t e = 0;

@@ -169,8 +169,10 @@ struct ApplyArgs {
 cudaError_t launch_kernel_dense(int prec, int kernel, const double *pts, int dim,
                                 const LeafDev *leaves, const int32_t *near_ids, int nnear,
                                 void *data, cudaStream_t s);
+// far_ids[0 .. nsmall) must be leaves of at most 64 x 64 (one warp each), the rest any size
+// (one block each)
 cudaError_t launch_aca(int kernel, const double *pts, int dim, const LeafDev *leaves,
-                       const int32_t *far_ids, int nfar, double eps, int kmax,
+                       const int32_t *far_ids, int nfar, int nsmall, double eps, int kmax,
                        double *scratch, const int64_t *scratch_off, int32_t *ranks,
                        cudaStream_t s);
 cudaError_t launch_aca_compact(int prec, const LeafDev *leaves, const int32_t *far_ids, int nfar,

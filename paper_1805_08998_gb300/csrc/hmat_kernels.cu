@@ -286,13 +286,13 @@ __device__ int64_t block_argmax(double v, int64_t idx, double *redv, int64_t *re
 // when ||l_{k+1}|| ||u_{k+1}|| <= eps ||L_k U_k||_F (eq. (truncaca)), keeping that term.
 // L (m x kmax) and R (n x kmax) live in scratch; `used` flags live after them.
 __global__ void __launch_bounds__(NT) k_aca(int kernel, const double *pts, int dim, const LeafDev *leaves,
-                                            const int32_t *ids, double eps, int kmax, double *scratch,
+                                            const int32_t *ids, int base, double eps, int kmax, double *scratch,
                                             const int64_t *soff, int32_t *ranks) {
   __shared__ double redv[NT / 32];
   __shared__ int64_t redi[NT / 32];
   __shared__ double red[NT / 32];
   __shared__ double dots[2][ACA_KMAX][NT / 32];  // per warp: L_q . l_k and R_q . r_k, q <= k
-  const int f = blockIdx.x;
+  const int f = base + blockIdx.x;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const LeafDev lf = leaves[ids[f]];
   const int64_t m = lf.m, n = lf.n;
@@ -393,6 +393,133 @@ __global__ void __launch_bounds__(NT) k_aca(int kernel, const double *pts, int d
     if (ipiv < 0) break;
   }
   if (threadIdx.x == 0) ranks[f] = k;
+}
+
+// (value, index) of the largest value over the warp, the smallest index on ties; entries without
+// a candidate carry (-1, -1)
+__device__ __forceinline__ void warp_argmax(double &v, int &idx) {
+  for (int off = 16; off > 0; off >>= 1) {
+    const double ov = __shfl_xor_sync(0xffffffffu, v, off);
+    const int oi = __shfl_xor_sync(0xffffffffu, idx, off);
+    if (ov > v || (ov == v && oi >= 0 && (idx < 0 || oi < idx))) {
+      v = ov;
+      idx = oi;
+    }
+  }
+}
+
+// The same Algorithm 6 for far leaves of at most 64 x 64, one warp per leaf (eight leaves per
+// block): each lane owns rows and columns lane and lane + 32, the used rows are one 64-bit mask,
+// and every reduction is a warp exchange, so no step waits at a block barrier. Same pivoting,
+// stop test and scratch layout as k_aca.
+__global__ void __launch_bounds__(NT) k_aca_warp(int kernel, const double *pts, int dim, const LeafDev *leaves,
+                                                 const int32_t *ids, int count, double eps, int kmax,
+                                                 double *scratch, const int64_t *soff, int32_t *ranks) {
+  const int f = blockIdx.x * (NT / 32) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (f >= count) return;  // a whole warp: nothing below waits on the rest of the block
+  const LeafDev lf = leaves[ids[f]];
+  const int m = lf.m, n = lf.n;
+  double *L = scratch + soff[f];
+  double *R = L + (int64_t)m * kmax;
+  const int cap = min(kmax, min(m, n));
+  const uint64_t rows = m == 64 ? ~0ull : ((1ull << m) - 1);
+  uint64_t used = 0;
+  double norm2 = 0.0;
+  int k = 0, ipiv = 0;
+  while (k < cap) {
+    int jpiv = -1;
+    while (true) {
+      if (ipiv < 0 || ((used >> ipiv) & 1ull)) {
+        const uint64_t free_rows = rows & ~used;
+        ipiv = free_rows ? __ffsll((long long)free_rows) - 1 : -1;
+        if (ipiv < 0) break;
+      }
+      const double *x = pts + (lf.row + ipiv) * dim;
+      double bv = -1.0;
+      int bi = -1;
+#pragma unroll
+      for (int h = 0; h < 2; h++) {
+        const int j = lane + 32 * h;
+        if (j < n) {
+          double v = kernel_eval(kernel, x, pts + (lf.col + j) * dim, dim);
+          for (int q = 0; q < k; q++) v -= L[q * m + ipiv] * R[q * n + j];
+          R[k * n + j] = v;
+          const double a = fabs(v);
+          if (a > bv) {
+            bv = a;
+            bi = j;
+          }
+        }
+      }
+      used |= 1ull << ipiv;
+      warp_argmax(bv, bi);
+      jpiv = bi;
+      __syncwarp();
+      const double best = jpiv >= 0 ? fabs(R[k * n + jpiv]) : 0.0;
+      if (best > 0.0) break;
+      ipiv = -1;
+      jpiv = -1;
+    }
+    if (ipiv < 0 || jpiv < 0) break;
+    const double piv = R[k * n + jpiv];
+    __syncwarp();
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+      const int j = lane + 32 * h;
+      if (j < n) R[k * n + j] = R[k * n + j] / piv;
+    }
+    __syncwarp();
+    const double *y = pts + (lf.col + jpiv) * dim;
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+      const int i = lane + 32 * h;
+      if (i < m) {
+        double v = kernel_eval(kernel, pts + (lf.row + i) * dim, y, dim);
+        for (int q = 0; q < k; q++) v -= R[q * n + jpiv] * L[q * m + i];
+        L[k * m + i] = v;
+      }
+    }
+    __syncwarp();
+    // ||L_{k+1} U_{k+1}^T||_F^2 = ||L_k U_k^T||_F^2 + 2 sum_{q<k} (L_q . l_k)(R_q . r_k) + |l_k|^2 |r_k|^2
+    double nl = 0.0, nu = 0.0, cross = 0.0;
+    for (int q = 0; q <= k; q++) {
+      double a = 0.0, b = 0.0;
+#pragma unroll
+      for (int h = 0; h < 2; h++) {
+        const int i = lane + 32 * h;
+        if (i < m) a += L[q * m + i] * L[k * m + i];
+        if (i < n) b += R[q * n + i] * R[k * n + i];
+      }
+      a = warp_sum(a);
+      b = warp_sum(b);
+      if (q < k) cross += a * b;
+      else {
+        nl = a;
+        nu = b;
+      }
+    }
+    const double prev = norm2;
+    norm2 = prev + 2.0 * cross + nl * nu;
+    k++;
+    if (sqrt(nl) * sqrt(nu) <= eps * sqrt(prev)) break;
+    double bv = -1.0;
+    int bi = -1;
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+      const int i = lane + 32 * h;
+      if (i < m && !((used >> i) & 1ull)) {
+        const double a = fabs(L[(k - 1) * m + i]);
+        if (a > bv) {
+          bv = a;
+          bi = i;
+        }
+      }
+    }
+    warp_argmax(bv, bi);
+    ipiv = bi;
+    if (ipiv < 0) break;
+  }
+  if (lane == 0) ranks[f] = k;
 }
 
 template <typename T>
@@ -1811,11 +1938,17 @@ cudaError_t launch_kernel_dense(int prec, int kernel, const double *pts, int dim
 }
 
 cudaError_t launch_aca(int kernel, const double *pts, int dim, const LeafDev *leaves, const int32_t *far_ids,
-                       int nfar, double eps, int kmax, double *scratch, const int64_t *scratch_off, int32_t *ranks,
-                       cudaStream_t s) {
+                       int nfar, int nsmall, double eps, int kmax, double *scratch, const int64_t *scratch_off,
+                       int32_t *ranks, cudaStream_t s) {
   if (nfar == 0) return cudaSuccess;
   if (kmax < 1 || kmax > ACA_KMAX) return cudaErrorInvalidValue;  // the kernel's dot table holds ACA_KMAX
-  k_aca<<<nfar, NT, 0, s>>>(kernel, pts, dim, leaves, far_ids, eps, kmax, scratch, scratch_off, ranks);
+  if (nsmall < 0 || nsmall > nfar) return cudaErrorInvalidValue;
+  if (nsmall > 0)
+    k_aca_warp<<<(nsmall + NT / 32 - 1) / (NT / 32), NT, 0, s>>>(kernel, pts, dim, leaves, far_ids, nsmall, eps, kmax,
+                                                               scratch, scratch_off, ranks);
+  if (nfar > nsmall)
+    k_aca<<<nfar - nsmall, NT, 0, s>>>(kernel, pts, dim, leaves, far_ids, nsmall, eps, kmax, scratch, scratch_off,
+                                       ranks);
   return cudaGetLastError();
 }
 

@@ -1579,13 +1579,22 @@ void Product::run() {
 
   // FP32 far x far products with both ranks <= 32 and at most 2048 inner rows run one warp per
   // job (listed first), the others (and all FP64 ones) one block per job.
+  // The warp jobs are listed by rank bucket (both ranks <= 8, <= 16, <= 32), each run by a
+  // kernel sized for its bucket; the order within a bucket is the plan's.
   int n_ff_warp = 0;
+  int ff_bucket[3] = {0, 0, 0};
   if (cprec == 32) {
-    std::vector<int32_t> big;
+    std::vector<int32_t> bk[3], big;
     for (int32_t i : ff_ids) {
       const LeafDev &la = A->leaves[jobs[i].a], &lb = B->leaves[jobs[i].b];
-      if (la.rank <= 32 && lb.rank <= 32 && la.n <= 2048) ff_ids[n_ff_warp++] = i;
+      const int r = std::max(la.rank, lb.rank);
+      if (r <= 32 && la.n <= 2048) bk[r <= 8 ? 0 : r <= 16 ? 1 : 2].push_back(i);
       else big.push_back(i);
+    }
+    for (int b = 0; b < 3; b++) {
+      std::copy(bk[b].begin(), bk[b].end(), ff_ids.begin() + n_ff_warp);
+      n_ff_warp += (int)bk[b].size();
+      ff_bucket[b] = (int)bk[b].size();
     }
     std::copy(big.begin(), big.end(), ff_ids.begin() + n_ff_warp);
   }
@@ -1629,14 +1638,15 @@ void Product::run() {
     cudaEventRecord(a2ev.back().second[which], s);
   };
   a2mark(-1, 0);
-  ck(launch_ff_warp(cprec, d_jobs.as<TermJob>(), d_ffids.as<int32_t>(), n_ff_warp, A->d_leaves.as<LeafDev>(),
+  ck(launch_ff_warp(cprec, d_jobs.as<TermJob>(), d_ffids.as<int32_t>(), ff_bucket, A->d_leaves.as<LeafDev>(),
                     B->d_leaves.as<LeafDev>(), dataA, dataB, d_termbuf.p, s),
      "far x far products (warp)");
   ck(launch_term_jobs(cprec, d_jobs.as<TermJob>(), d_ffids.as<int32_t>() + n_ff_warp, (int)ff_ids.size() - n_ff_warp,
                       A->d_leaves.as<LeafDev>(), B->d_leaves.as<LeafDev>(), t.d_blocks, dataA, dataB, d_termbuf.p, s),
      "far x far products");
   a2mark(-1, 1);
-  int64_t launches = 1 + (n_ff_warp > 0 ? 1 : 0) + ((int)ff_ids.size() > n_ff_warp ? 1 : 0);
+  int64_t launches = 1 + (ff_bucket[0] > 0 ? 1 : 0) + (ff_bucket[1] > 0 ? 1 : 0) + (ff_bucket[2] > 0 ? 1 : 0) +
+                     ((int)ff_ids.size() > n_ff_warp ? 1 : 0);
   const int64_t pstride = (int64_t)2 * pdim[NB + 1] * panel_row_stride(PW);
   // one staging slot per thread block of the global-staging launch (it loops over its panels)
   const int64_t pslots = std::min<int64_t>((int64_t)pk[NB + 1].size(), PANEL_GSTAGE_SLOTS);

@@ -179,8 +179,11 @@ cudaError_t launch_aca_compact(int prec, const LeafDev *leaves, const int32_t *f
                                const double *scratch, const int64_t *scratch_off, int kmax,
                                void *data, cudaStream_t s);
 // far x far products ids[0..n) with both ranks <= 32, one warp per job (the others: launch_term_jobs)
-cudaError_t launch_ff_warp(int prec, const TermJob *jobs, const int32_t *ids, int n, const LeafDev *leafA,
-                           const LeafDev *leafB, const void *dataA, const void *dataB, void *terms, cudaStream_t s);
+// far x far products one warp each: ids lists nbucket[0] jobs with both ranks <= 8, then
+// nbucket[1] with both <= 16, then nbucket[2] with both <= 32
+cudaError_t launch_ff_warp(int prec, const TermJob *jobs, const int32_t *ids, const int *nbucket,
+                           const LeafDev *leafA, const LeafDev *leafB, const void *dataA, const void *dataB,
+                           void *terms, cudaStream_t s);
 cudaError_t launch_term_jobs(int prec, const TermJob *jobs, const int32_t *ids, int njobs, const LeafDev *leafA,
                              const LeafDev *leafB, const BlockDev *blocks, const void *dataA,
                              const void *dataB, void *terms, cudaStream_t s);

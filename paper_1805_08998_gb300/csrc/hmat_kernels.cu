@@ -1969,108 +1969,121 @@ cudaError_t launch_aca_compact(int prec, const LeafDev *leaves, const int32_t *f
 // L_new = U_a M (lanes over rows, a row of M broadcast per step) and FF_R writes R_new = V_b M^T.
 constexpr int FF_CH = 16;  // rows of V_a and U_b staged per step
 constexpr int FF_K = 32;   // max rank of either factor
-template <typename T>
+
+// K: the job's rank bucket (8, 16 or 32, at least both ranks); ranks below K read as zeros
+template <typename T, int K>
 struct FfSmem {
-  T va[FF_CH][FF_K + 1], ub[FF_CH][FF_K + 1];
-  T M[FF_K][FF_K + 1];
+  T va[FF_CH][K + 1], ub[FF_CH][K + 1];
+  T M[K][K + 1];
 };
 
-template <typename T>
+template <typename T, int K>
 __global__ void __launch_bounds__(NT) k_ff_warp(const TermJob *jobs, const int32_t *ids, int n, const LeafDev *leafA,
                                                 const LeafDev *leafB, const T *dataA, const T *dataB, T *terms) {
+  static_assert(K == 8 || K == 16 || K == 32, "rank bucket");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ji = blockIdx.x * (NT / 32) + w;
   if (ji >= n) return;  // whole warps only; no block barrier below
-  FfSmem<T> &S = ((FfSmem<T> *)smem_raw)[w];
+  FfSmem<T, K> &S = ((FfSmem<T, K> *)smem_raw)[w];
   const TermJob jb = jobs[ids[ji]];
   const LeafDev a = leafA[jb.a], b = leafB[jb.b];
   const int ka = a.rank, kb = b.rank, rho = a.n;
   const T *Ua = dataA + a.off_u, *Va = dataA + a.off_v;
   const T *Ub = dataB + b.off_u, *Vb = dataB + b.off_v;
-  // M = V_a^T U_b; lane owns rows q0..q0+3 and columns c0..c0+7 of M
-  const int q0 = (lane >> 2) * 4, c0 = (lane & 3) * 8;
-  T acc[4][8];
+  // M = V_a^T U_b; lane owns rows q0 .. q0 + TQ - 1 and columns c0 .. c0 + TC - 1 of M
+  constexpr int TQ = K / 8, TC = K / 4;
+  const int q0 = (lane >> 2) * TQ, c0 = (lane & 3) * TC;
+  T acc[TQ][TC];
 #pragma unroll
-  for (int u = 0; u < 4; u++)
+  for (int u = 0; u < TQ; u++)
 #pragma unroll
-    for (int v = 0; v < 8; v++) acc[u][v] = T(0);
+    for (int v = 0; v < TC; v++) acc[u][v] = T(0);
   for (int i0 = 0; i0 < rho; i0 += FF_CH) {
     const int ni = min(FF_CH, rho - i0);
-    for (int o = lane; o < FF_CH * FF_K; o += 32) {
+    for (int o = lane; o < FF_CH * K; o += 32) {
       const int i = o % FF_CH, q = o / FF_CH;
       S.va[i][q] = (i < ni && q < ka) ? Va[(i0 + i) + (int64_t)q * rho] : T(0);
       S.ub[i][q] = (i < ni && q < kb) ? Ub[(i0 + i) + (int64_t)q * rho] : T(0);
     }
     __syncwarp();
     for (int i = 0; i < ni; i++) {
-      T x[4], y[8];
+      T x[TQ], y[TC];
 #pragma unroll
-      for (int u = 0; u < 4; u++) x[u] = S.va[i][q0 + u];
+      for (int u = 0; u < TQ; u++) x[u] = S.va[i][q0 + u];
 #pragma unroll
-      for (int v = 0; v < 8; v++) y[v] = S.ub[i][c0 + v];
+      for (int v = 0; v < TC; v++) y[v] = S.ub[i][c0 + v];
 #pragma unroll
-      for (int u = 0; u < 4; u++)
+      for (int u = 0; u < TQ; u++)
 #pragma unroll
-        for (int v = 0; v < 8; v++) acc[u][v] += x[u] * y[v];
+        for (int v = 0; v < TC; v++) acc[u][v] += x[u] * y[v];
     }
     __syncwarp();
   }
 #pragma unroll
-  for (int u = 0; u < 4; u++)
+  for (int u = 0; u < TQ; u++)
 #pragma unroll
-    for (int v = 0; v < 8; v++) S.M[q0 + u][c0 + v] = acc[u][v];
+    for (int v = 0; v < TC; v++) S.M[q0 + u][c0 + v] = acc[u][v];
   __syncwarp();
   T *out = terms + jb.out;
   const int rows = (int)jb.rows;
   if (jb.type == JOB_FF_L) {  // out (rows x kb) = U_a M
     for (int i = lane; i < rows; i += 32) {
-      T o[FF_K];
+      T o[K];
 #pragma unroll
-      for (int c = 0; c < FF_K; c++) o[c] = T(0);
+      for (int c = 0; c < K; c++) o[c] = T(0);
       for (int q = 0; q < ka; q++) {
         const T u = Ua[i + (int64_t)q * rows];
 #pragma unroll
-        for (int c = 0; c < FF_K; c++) o[c] += u * S.M[q][c];
+        for (int c = 0; c < K; c++) o[c] += u * S.M[q][c];
       }
 #pragma unroll
-      for (int c = 0; c < FF_K; c++)
+      for (int c = 0; c < K; c++)
         if (c < kb) out[i + (int64_t)c * rows] = o[c];
     }
   } else {  // FF_R: out (rows x ka) = V_b M^T
     for (int i = lane; i < rows; i += 32) {
-      T o[FF_K];
+      T o[K];
 #pragma unroll
-      for (int q = 0; q < FF_K; q++) o[q] = T(0);
+      for (int q = 0; q < K; q++) o[q] = T(0);
       for (int c = 0; c < kb; c++) {
         const T v = Vb[i + (int64_t)c * rows];
 #pragma unroll
-        for (int q = 0; q < FF_K; q++) o[q] += v * S.M[q][c];
+        for (int q = 0; q < K; q++) o[q] += v * S.M[q][c];
       }
 #pragma unroll
-      for (int q = 0; q < FF_K; q++)
+      for (int q = 0; q < K; q++)
         if (q < ka) out[i + (int64_t)q * rows] = o[q];
     }
   }
 }
 
-cudaError_t launch_ff_warp(int prec, const TermJob *jobs, const int32_t *ids, int n, const LeafDev *leafA,
-                           const LeafDev *leafB, const void *dataA, const void *dataB, void *terms, cudaStream_t s) {
+template <typename T, int K>
+static cudaError_t launch_ff_bucket(const TermJob *jobs, const int32_t *ids, int n, const LeafDev *leafA,
+                                    const LeafDev *leafB, const void *dataA, const void *dataB, void *terms,
+                                    cudaStream_t s) {
   if (n == 0) return cudaSuccess;
-  const int grid = (n + NT / 32 - 1) / (NT / 32);
+  const size_t sm = sizeof(FfSmem<T, K>) * (NT / 32);
   cudaError_t e;
-  if (prec == 64) {
-    const size_t sm = sizeof(FfSmem<double>) * (NT / 32);
-    if ((e = set_smem(k_ff_warp<double>, sm)) != cudaSuccess) return e;
-    k_ff_warp<double><<<grid, NT, sm, s>>>(jobs, ids, n, leafA, leafB, (const double *)dataA, (const double *)dataB,
-                                           (double *)terms);
-  } else {
-    const size_t sm = sizeof(FfSmem<float>) * (NT / 32);
-    if ((e = set_smem(k_ff_warp<float>, sm)) != cudaSuccess) return e;
-    k_ff_warp<float><<<grid, NT, sm, s>>>(jobs, ids, n, leafA, leafB, (const float *)dataA, (const float *)dataB,
-                                          (float *)terms);
-  }
+  if ((e = set_smem(k_ff_warp<T, K>, sm)) != cudaSuccess) return e;
+  k_ff_warp<T, K><<<(n + NT / 32 - 1) / (NT / 32), NT, sm, s>>>(jobs, ids, n, leafA, leafB, (const T *)dataA,
+                                                               (const T *)dataB, (T *)terms);
   return cudaGetLastError();
+}
+
+cudaError_t launch_ff_warp(int prec, const TermJob *jobs, const int32_t *ids, const int *nbucket,
+                           const LeafDev *leafA, const LeafDev *leafB, const void *dataA, const void *dataB,
+                           void *terms, cudaStream_t s) {
+  cudaError_t e;
+  const int n8 = nbucket[0], n16 = nbucket[1], n32 = nbucket[2];
+  if (prec == 64) {
+    if ((e = launch_ff_bucket<double, 8>(jobs, ids, n8, leafA, leafB, dataA, dataB, terms, s))) return e;
+    if ((e = launch_ff_bucket<double, 16>(jobs, ids + n8, n16, leafA, leafB, dataA, dataB, terms, s))) return e;
+    return launch_ff_bucket<double, 32>(jobs, ids + n8 + n16, n32, leafA, leafB, dataA, dataB, terms, s);
+  }
+  if ((e = launch_ff_bucket<float, 8>(jobs, ids, n8, leafA, leafB, dataA, dataB, terms, s))) return e;
+  if ((e = launch_ff_bucket<float, 16>(jobs, ids + n8, n16, leafA, leafB, dataA, dataB, terms, s))) return e;
+  return launch_ff_bucket<float, 32>(jobs, ids + n8 + n16, n32, leafA, leafB, dataA, dataB, terms, s);
 }
 
 cudaError_t launch_term_jobs(int prec, const TermJob *jobs, const int32_t *ids, int njobs, const LeafDev *leafA,

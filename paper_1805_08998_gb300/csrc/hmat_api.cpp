@@ -1678,8 +1678,10 @@ void Product::run() {
   S.n_panels += (int64_t)panels.size();
   check_finite(cprec, d_termbuf.p, term_elems, "low-rank products", s);
   tr.mark("a2 launched");
-  if (tr.on) {
-    cudaStreamSynchronize(s);
+  // (trace) the a2 launches' device times, read once the product has synchronised, so that the
+  // trace does not serialise the host work below behind them
+  auto a2_report = [&]() {
+    if (!tr.on) return;
     for (auto &e : a2ev) {
       float x = 0.f;
       cudaEventElapsedTime(&x, e.second[0], e.second[1]);
@@ -1693,7 +1695,7 @@ void Product::run() {
       cudaEventDestroy(e.second[0]);
       cudaEventDestroy(e.second[1]);
     }
-  }
+  };
   ck(cudaEventRecord(ev[1], s), "event");
 
   // host work below overlaps the low-rank products on the GPU
@@ -2330,6 +2332,7 @@ void Product::run() {
   int near_err = 0;
   ck(cudaMemcpyAsync(&near_err, d_nerr.p, sizeof(int), cudaMemcpyDeviceToHost, s), "near status");
   ck(cudaStreamSynchronize(s), "product");
+  a2_report();
   {
     float nms = 0;
     cudaEventElapsedTime(&nms, ne.e[0], ne.e[1]);

@@ -1932,8 +1932,6 @@ void Product::run() {
   DevBuf d_ntg = upload(ntg, s2.st), d_npairs = upload(npairs, s2.st);
   DevBuf d_nerr(sizeof(int), s2.st);
   ck(cudaMemsetAsync(d_nerr.p, 0, sizeof(int), s2.st), "memset");
-  ck(cudaEventRecord(s2.e0, s), "event");
-  ck(cudaStreamWaitEvent(s2.st, s2.e0, 0), "stream wait");
   // the near field's own device time, on its stream
   struct NearEvents {
     cudaEvent_t e[2] = {nullptr, nullptr};
@@ -1944,15 +1942,20 @@ void Product::run() {
   } ne;
   ck(cudaEventCreate(&ne.e[0]), "event");
   ck(cudaEventCreate(&ne.e[1]), "event");
-  ck(cudaEventRecord(ne.e[0], s2.st), "event");
-  ck(launch_near_eval(cprec, d_ntg.as<TargetDev>(), (int)ntg.size(), d_blkterms.as<int2>(), d_terms.as<TermDev>(),
-                      d_npairs.as<PairDev>(), t.d_blocks, A->d_leaves.as<LeafDev>(), B->d_leaves.as<LeafDev>(), dataA,
-                      dataB, d_near_leaves.as<LeafDev>(), d_near.p, d_nerr.as<int>(), s2.st),
-     "near field");
-  ck(cudaEventRecord(ne.e[1], s2.st), "event");
-  ck(cudaEventRecord(s2.e1, s2.st), "event");
-
-  tr.mark("near field launched");
+  // the near field needs the low-rank products: its stream waits for them, then runs beside the
+  // sampling rounds
+  {
+    ck(cudaEventRecord(s2.e0, s), "event");
+    ck(cudaStreamWaitEvent(s2.st, s2.e0, 0), "stream wait");
+    ck(cudaEventRecord(ne.e[0], s2.st), "event");
+    ck(launch_near_eval(cprec, d_ntg.as<TargetDev>(), (int)ntg.size(), d_blkterms.as<int2>(), d_terms.as<TermDev>(),
+                        d_npairs.as<PairDev>(), t.d_blocks, A->d_leaves.as<LeafDev>(), B->d_leaves.as<LeafDev>(),
+                        dataA, dataB, d_near_leaves.as<LeafDev>(), d_near.p, d_nerr.as<int>(), s2.st),
+       "near field");
+    ck(cudaEventRecord(ne.e[1], s2.st), "event");
+    ck(cudaEventRecord(s2.e1, s2.st), "event");
+    tr.mark("near field launched");
+  }
   // ---- a3..a7: adaptive randomized truncation of all far targets
   const int nf = (int)ftg.size();
   DevBuf d_ftg = upload(ftg, s), d_fpairs = upload(fpairs, s);
@@ -2159,11 +2162,21 @@ void Product::run() {
       launches += 2;
     }
   }
+  double host_t = now_ms();
+  int32_t act_prev = nf;
   for (int round = 0; round < max_rounds && nf > 0 && fixed_k == 0 && !single; round++) {
     rounds++;
     const int pr = round == 0 ? pmax : p;  // widest panel this round (round 0: each target's p0)
     aa.p = pr;
     aa.round = round;
+    cudaEvent_t rev[2] = {nullptr, nullptr};  // (trace) the round's span on the device
+    if (tr.on) {
+      std::fprintf(stderr, "hmat trace: round %d: %d active targets, host %.3f ms since the last round's result\n",
+                   round, act_prev, now_ms() - host_t);
+      cudaEventCreate(&rev[0]);
+      cudaEventCreate(&rev[1]);
+      cudaEventRecord(rev[0], s);
+    }
     kmark(0, 0);
     ck(launch_gaussian(cprec, aa.tg, aa.state, nf, pr, o->seed, round, d_x.p, s), "gaussian");
     kmark(0, 1);
@@ -2184,9 +2197,19 @@ void Product::run() {
                        d_cnt.as<int32_t>(), s),
        "stop test");
     kmark(2, 1);
+    if (tr.on) cudaEventRecord(rev[1], s);
     int32_t act = 0;
     ck(cudaMemcpyAsync(&act, d_cnt.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s), "count");
     ck(cudaStreamSynchronize(s), "round");
+    host_t = now_ms();
+    act_prev = act;
+    if (tr.on) {
+      float x = 0.f;
+      cudaEventElapsedTime(&x, rev[0], rev[1]);
+      std::fprintf(stderr, "hmat trace: round %d: %.3f ms on the device\n", round, x);
+      cudaEventDestroy(rev[0]);
+      cudaEventDestroy(rev[1]);
+    }
     if (act == 0) break;
   }
   tr.mark("sampling rounds done");

@@ -41,16 +41,21 @@ struct Builder {
   // the floor(size/2) smallest keys, since each child orders its own points again by its own
   // axis and its bounding box does not depend on their order. The keys are a strict total order,
   // so the selected sets, and hence the permutation, equal those of a full sort at every level.
-  std::vector<std::pair<double, int64_t>> keys;
-  int cluster(int64_t begin, int64_t size, int level) {
-    const int id = (int)t.cl.size();
-    t.cl.emplace_back();
+  //
+  // The tree is complete, so a cluster's depth-first (preorder) id follows from its parent's: the
+  // first child is id + 1, the second id + 2^(D - level) (after the first child's 2^(D - level) - 1
+  // clusters). Clusters therefore fill their own slots and their own ranges of the permutation,
+  // and disjoint subtrees are built on different threads with the same result as one thread.
+  using Keys = std::vector<std::pair<double, int64_t>>;
+  // fills cluster id; above depth D also orders its points for the split and records its
+  // children's ids; returns the size of the first child (0 at a leaf)
+  int64_t make(int id, int64_t begin, int64_t size, int level, Keys &keys) {
     Cluster c;
     c.level = level;
     c.begin = begin;
     c.size = size;
     bbox(begin, size, c.lo, c.hi);
-    t.cl[id] = c;
+    int64_t h = 0;
     if (level < t.depth) {
       int axis = 0;
       double best = c.hi[0] - c.lo[0];
@@ -70,16 +75,50 @@ struct Builder {
         if (a.first > b.first) return false;
         return a.second < b.second;
       };
-      const int64_t h = size / 2;
+      h = size / 2;
       if (level + 1 < t.depth) std::nth_element(keys.begin(), keys.begin() + h, keys.end(), less);
       else std::sort(keys.begin(), keys.end(), less);
       for (int64_t i = 0; i < size; i++) t.perm[begin + i] = keys[i].second;
-      const int c0 = cluster(begin, h, level + 1);
-      const int c1 = cluster(begin + h, size - h, level + 1);
-      t.cl[id].child[0] = c0;
-      t.cl[id].child[1] = c1;
+      c.child[0] = id + 1;
+      c.child[1] = id + (1 << (t.depth - level));
     }
-    return id;
+    t.cl[id] = c;
+    return h;
+  }
+  void subtree(int id, int64_t begin, int64_t size, int level, Keys &keys) {
+    const int64_t h = make(id, begin, size, level, keys);
+    if (level < t.depth) {
+      subtree(id + 1, begin, h, level + 1, keys);
+      subtree(id + (1 << (t.depth - level)), begin + h, size - h, level + 1, keys);
+    }
+  }
+  // the whole cluster tree: the top levels one level at a time (the clusters of a level in
+  // parallel), then the subtrees below them in parallel
+  void clusters() {
+    t.cl.assign(((size_t)2 << t.depth) - 1, Cluster{});
+    struct Item {
+      int id;
+      int64_t begin, size;
+    };
+    std::vector<Item> cur{Item{0, 0, t.n}};
+    const int top = std::min(t.depth, 4);
+    for (int level = 0; level < top; level++) {
+      std::vector<int64_t> h(cur.size());
+      parallel_for(cur.size(), [&](size_t i) {
+        Keys keys;
+        h[i] = make(cur[i].id, cur[i].begin, cur[i].size, level, keys);
+      });
+      std::vector<Item> nxt;
+      for (size_t i = 0; i < cur.size(); i++) {
+        nxt.push_back(Item{cur[i].id + 1, cur[i].begin, h[i]});
+        nxt.push_back(Item{cur[i].id + (1 << (t.depth - level)), cur[i].begin + h[i], cur[i].size - h[i]});
+      }
+      cur.swap(nxt);
+    }
+    parallel_for(cur.size(), [&](size_t i) {
+      Keys keys;
+      subtree(cur[i].id, cur[i].begin, cur[i].size, top, keys);
+    });
   }
   // eta-admissibility: max(diam tau, diam sigma) <= eta * dist(tau, sigma) with bounding-box
   // diagonals and the Euclidean distance of the boxes; distance zero is never admissible.
@@ -157,9 +196,8 @@ std::shared_ptr<Tree> build_tree(const double *xyz, int64_t n, int dim, int leaf
   t->depth = depth;
   t->perm.resize(n);
   for (int64_t i = 0; i < n; i++) t->perm[i] = i;
-  t->cl.reserve(((size_t)2 << depth));
   Builder bd{*t};
-  bd.cluster(0, n, 0);
+  bd.clusters();
   t->pts.resize(n * dim);
   for (int64_t i = 0; i < n; i++)
     for (int d = 0; d < dim; d++) t->pts[i * dim + d] = t->orig[t->perm[i] * dim + d];

@@ -1628,6 +1628,14 @@ void Product::run() {
                        B->d_leaves.as<LeafDev>(), dataA, dataB, d_termbuf.p, d_terms.as<TermDev>(), s),
      "term table");
   std::vector<std::pair<int, std::array<cudaEvent_t, 2>>> a2ev;  // HMAT_TRACE only: -1 = far x far
+  struct A2EvGuard {  // events not yet read when the product fails
+    std::vector<std::pair<int, std::array<cudaEvent_t, 2>>> &v;
+    ~A2EvGuard() {
+      for (auto &e : v)
+        for (cudaEvent_t x : e.second)
+          if (x) cudaEventDestroy(x);
+    }
+  } a2evg{a2ev};
   auto a2mark = [&](int kind, int which) {
     if (!tr.on) return;
     if (which == 0) {
@@ -1695,6 +1703,7 @@ void Product::run() {
       cudaEventDestroy(e.second[0]);
       cudaEventDestroy(e.second[1]);
     }
+    a2ev.clear();
   };
   ck(cudaEventRecord(ev[1], s), "event");
 

@@ -251,6 +251,8 @@ __global__ void __launch_bounds__(NTC, 2)
           if (j < nt) C[(i0 + row) + (int64_t)(j0 + j) * t.m] = acc[j] + cmp[j];
       }
     }
+  // A block whose wait gave up may still have MMAs in flight when it frees its TMEM below; their
+  // results are lost with the product, which then reports HMAT_ETIMEOUT and returns no output.
   if (failed && threadIdx.x == 0) atomicOr(err, 1);  // (already set when the block skipped its work)
   tc::fence_before_sync();
   __syncthreads();

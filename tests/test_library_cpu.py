@@ -287,6 +287,13 @@ def test_plan_host_arguments(H):
     assert nl.value == len(full.n_lowrank) and np.array_equal(lr[:3], full.n_lowrank[:3]) and np.all(lr[3:] == -7)
 
 
+def test_bounded_wait_check_arguments(H):
+    """The bounded-wait check rejects poll counts outside 1..2^22 before it touches a device."""
+    for bad in (0, -1, (1 << 22) + 1):
+        assert H.hmat_check_bounded_wait(bad) == H.HMAT_EINVAL
+        assert b"polls" in H.lib().hmat_last_error()
+
+
 def test_plan_host_matches_hand_derived_example(H):
     """The library's trees and restriction plan against the worked example derived by hand in
     tests/golden/tree_1d_n16_leaf2_eta1.txt (Def. 2.2, Def. 2.3, Algorithms 1 and 3)."""
